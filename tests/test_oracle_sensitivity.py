@@ -1,0 +1,33 @@
+"""Sensitivity of the model itself, measured with the FP64 oracle alone.
+
+With both edge vortices shed every step (the 1000-particle MPPI workload), a relative
+perturbation of 1e-7 of the initial positions (the size of binary32 rounding) grows to
+O(0.1-1) chords within 100 steps, while the variant that sheds the LEV only above the
+critical incidence stays within ~1e-4. Pointwise 100-step position parity at 1e-4 chords
+is therefore a property a binary64 path can have on the ungated workload, and a binary32
+path only on the gated variant; the GPU tests are arranged accordingly.
+"""
+import numpy as np
+
+import workloads as W
+
+
+def _spread(ora, p, field, xg0, u, rel, seed=1):
+    a = ora.rollout(p, field, xg0, u, want_field=True)
+    f2 = field.copy()
+    f2[:, :2] += np.random.default_rng(seed).normal(0, rel, f2[:, :2].shape) * np.abs(f2[:, :2])
+    b = ora.rollout(p, f2, xg0, u, want_field=True)
+    return np.linalg.norm(a["field"][:, :2] - b["field"][:, :2], axis=1).max()
+
+
+def test_ungated_workload_amplifies_rounding(ora):
+    p, field, xg0, eps = W.mppi_c2(0, K=1, H=100, n=1000)
+    u = eps[0].astype(np.float64)
+    assert _spread(ora, p, field, xg0, u, 1e-7) > 1e-2
+    assert _spread(ora, p, field, xg0, u, 1e-13) < 1e-3
+
+
+def test_lev_gated_variant_is_mildly_sensitive(ora):
+    p, field, xg0, eps = W.mppi_c2(0, K=1, H=100, n=1000)
+    p = dict(p, shed_gate=2)
+    assert _spread(ora, p, field, xg0, eps[0].astype(np.float64), 1e-7) < 1e-4
