@@ -1,0 +1,222 @@
+/*
+ * vpm.h - C ABI of the B300 vortex-particle-model (VPM) rollout library.
+ *
+ * The library advances batches of 2-D VPM models of a flat-plate glider, each carrying its own
+ * field of regularised point vortices, and reduces rollout costs to MPPI weights, as defined in
+ * "Real-Time Maneuver Planning for Fixed-Wing UAVs in Unsteady Flows Using a GPU-Accelerated
+ * Vortex Particle Model": the model of §III-A (Eqs. 2-17), the glider of §III-B (Eqs. 18-22),
+ * the terminal cost of §IV-A (Eq. 24) and the MPPI reweighting of §IV-A (Eq. 25).
+ *
+ * Conventions shared by every call
+ *  - Coordinates are (x, z) in chord units, z up. Positive circulation and positive pitch are
+ *    counter-clockwise (nose up). A particle is (x, z, Gamma).
+ *  - Pointers named d_* are device pointers (for example from torch tensors); h_* are host
+ *    pointers. The caller owns every buffer it passes. The library owns vpm_state handles.
+ *  - Every call that takes a cudaStream_t enqueues its work on that stream and returns without
+ *    waiting, unless it says otherwise. Calls on one state must not overlap on the device.
+ *  - Every call returns a vpm_status. VPM_OK is 0. vpm_last_error() gives a message for the
+ *    last failing call of the calling host thread. Invalid arguments are rejected on the host
+ *    before anything is enqueued; device-side failures (non-finite values) latch into the
+ *    state's error word, which vpm_state_status() reads.
+ *  - The library builds for sm_103a only and keeps no CPU fallback: without a CUDA device every
+ *    call that needs one returns VPM_ERR_CUDA.
+ */
+#ifndef VPM_H
+#define VPM_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VPM_OK = 0,
+    VPM_ERR_INVALID = 1,     /* bad argument (null, negative size, non-finite parameter)   */
+    VPM_ERR_OOM = 2,         /* device allocation failed                                    */
+    VPM_ERR_CAPACITY = 3,    /* particles would exceed the state's capacity or shared memory */
+    VPM_ERR_NONFINITE = 4,   /* a NaN or Inf appeared in a model quantity                   */
+    VPM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                               */
+    VPM_ERR_CUDA = 6,        /* a CUDA runtime call failed (message in vpm_last_error)       */
+    VPM_ERR_BUSY = 7,        /* resource in use                                             */
+    VPM_ERR_SINGULAR = 8     /* the surface-circulation system is singular                  */
+} vpm_status;
+
+/* Kernel applied by wake and shed vortices. Bound vortices always use the singular kernel
+ * (§III-A: Eq. 4 for bound vortices, Eq. 5 for wake vortices). */
+typedef enum {
+    VPM_KERNEL_SINGULAR = 0, /* Eq. 4: K = -1/(2 pi r^2) [[0,1],[-1,0]] dr                   */
+    VPM_KERNEL_VATISTAS = 1, /* Eq. 5: Eq. 4 times (r/r_core)^2 / sqrt(1 + (r/r_core)^4)     */
+    VPM_KERNEL_GAUSSIAN = 2  /* Eq. 4 times 1 - exp(-r^2 / r_core^2)                          */
+} vpm_kernel;
+
+/* Arithmetic of the particle sums and positions. VPM_FP32: binary32 pair sums with
+ * compensated accumulation across source tiles and double-length (hi + lo) positions;
+ * the surface solve, Kelvin sum, loads and glider stay binary64. VPM_FP64: binary64
+ * throughout. */
+typedef enum { VPM_FP32 = 0, VPM_FP64 = 1 } vpm_precision;
+
+/* Separation gate of §III-A. */
+typedef enum {
+    VPM_GATE_OFF = 0,        /* LEV and TEV shed every step                                 */
+    VPM_GATE_BOTH = 1,       /* nothing is shed while |alpha| <= alpha_crit                  */
+    VPM_GATE_LEV = 2         /* TEV every step, LEV only while |alpha| > alpha_crit          */
+} vpm_gate;
+
+/* Model parameters. Field meanings follow §III-A and §III-B. */
+typedef struct {
+    int n_b;                 /* bound vortices N_b (collocation points N_c = N_b + 1), 2..32  */
+    double chord, span, rho; /* chord c, span s, air density                                 */
+    int wake_kernel;         /* vpm_kernel of wake and shed vortices                         */
+    double r_core;           /* core radius of the wake kernel                               */
+    double shed_offset;      /* delta_s / c: LEV at LE - delta_s e_t, TEV at TE + delta_s e_t  */
+    double gamma_decay;      /* gamma of Eq. 17; Gamma <- Gamma exp(-gamma dt) each step      */
+    int shed_gate;           /* vpm_gate                                                     */
+    double alpha_crit;       /* critical angle of attack (rad)                               */
+    int n_wake_max;          /* merge the two oldest particles while N > n_wake_max; 0 = off  */
+    double u_inf[2];         /* uniform free stream (0 in still air)                         */
+    double dt;               /* time step (explicit Euler)                                   */
+    int fixed_plate;         /* 1: the plate is held at the initial glider pose, never moves  */
+    double mass, inertia, g; /* glider mass, pitch inertia, gravity                          */
+    double l, l_w, l_e, s_e; /* body length, wing offset, elevator length and area (Eq. 18)   */
+    double q[7];             /* diagonal of Q (Eq. 24)                                        */
+    double x_d[7];           /* desired final state x_d (Eq. 24)                              */
+    int precision;           /* vpm_precision                                                */
+} vpm_params;
+
+typedef struct vpm_state vpm_state;
+
+/* Message describing the last failure of the calling host thread ("" if none). */
+const char *vpm_last_error(void);
+
+/* Library version string. */
+const char *vpm_version(void);
+
+/*
+ * Creates a resident model: glider state x_g = [x, z, theta, phi, xdot, zdot, thetadot]
+ * (§III-B, Eq. 23) and n wake particles, with room for `capacity` particles. h_particles is
+ * n x 3 row-major binary64 (x, z, Gamma). The previous-step circulations used by the time
+ * derivatives of Eq. 13 start unset (the first step's derivatives are zero). Synchronises
+ * `stream` before returning.
+ * Errors: VPM_ERR_INVALID (null pointers, n < 0, capacity < n, bad parameters),
+ * VPM_ERR_NONFINITE (non-finite input), VPM_ERR_CAPACITY (capacity beyond the shared memory
+ * of one block), VPM_ERR_OOM, VPM_ERR_SINGULAR (surface system singular for these
+ * parameters), VPM_ERR_CUDA (no device).
+ */
+vpm_status vpm_state_create(const vpm_params *params, const double *h_particles, int n,
+                            int capacity, const double *h_glider7, vpm_state **out,
+                            cudaStream_t stream);
+
+/* Frees the state's device memory (synchronises the device first). */
+vpm_status vpm_state_destroy(vpm_state *state);
+
+/*
+ * Sets the previous-step bound circulations h_gb_prev[n_b], the previous LEV circulation and
+ * whether they are valid (has_prev = 0 makes the next step's derivatives zero). Synchronises
+ * `stream`.
+ */
+vpm_status vpm_state_set_history(vpm_state *state, const double *h_gb_prev, double glev_prev,
+                                 int has_prev, cudaStream_t stream);
+
+/*
+ * Copies the state to the host and synchronises `stream`: *n_out particles into
+ * h_particles (capacity x 3 binary64; on the binary32 path x and z are hi + lo), the glider
+ * state h_glider7, and optionally (if non-null) h_hist[n_b + 2] = [Gamma_b of the previous
+ * step (n_b), Gamma_LEV of the previous step, has_prev]. Returns the latched device error.
+ */
+vpm_status vpm_state_read(const vpm_state *state, double *h_particles, int *n_out,
+                          double *h_glider7, double *h_hist, cudaStream_t stream);
+
+/* Reads and clears the state's latched device error word (synchronises `stream`). */
+vpm_status vpm_state_status(vpm_state *state, cudaStream_t stream);
+
+/* Serialises the complete state into a host buffer (synchronises `stream`). With h_buf null,
+ * *bytes receives the size needed. */
+vpm_status vpm_state_save(const vpm_state *state, void *h_buf, size_t *bytes,
+                          cudaStream_t stream);
+
+/* Restores a state saved by vpm_state_save into a state created with the same precision,
+ * n_b and capacity (synchronises `stream`). */
+vpm_status vpm_state_load(vpm_state *state, const void *h_buf, size_t bytes,
+                          cudaStream_t stream);
+
+/*
+ * Advances the resident model by one step under elevator rate u (the tracking instance of
+ * §IV-C), in the order: geometry, relative velocity at the plate (Eq. 12), surface solve
+ * (Eq. 11), pressure and loads (Eqs. 13-15), glider update, shedding, convection (Eq. 16),
+ * Euler advection, decay (Eq. 17), merging. Optional device outputs (null to skip):
+ *   d_fm[3]              wing load F_w,x, F_w,z, M_w of this step
+ *   d_gamma_s[n_b+2]     surface circulations [Gamma_b, Gamma_LEV, Gamma_TEV] (0 if not shed)
+ *   d_vel[2*(n+2)]       convection velocity (u, w) of every particle of the enlarged wake
+ *   d_vtilde[2*(2n_b+1)] relative velocity of Eq. 12 at the collocation then bound points
+ * Errors: VPM_ERR_CAPACITY if the step could overflow the capacity, VPM_ERR_CUDA.
+ */
+vpm_status vpm_step(vpm_state *state, double u, double *d_fm, double *d_gamma_s, double *d_vel,
+                    double *d_vtilde, cudaStream_t stream);
+
+/*
+ * K independent rollouts of H steps from the root model, which is not modified. Rollout i
+ * applies elevator rates d_controls[i*H + k] (binary32, K x H row-major). One thread block
+ * holds one rollout's field in shared memory for the whole horizon. Outputs (device):
+ *   d_costs[K]               terminal cost J_i of Eq. 24 (computed in binary64, stored binary32;
+ *                            NaN if the rollout produced a non-finite value)
+ *   d_final_glider[K*7]      final glider states (binary64), or null
+ *   d_traj[K*H*7]            glider state after every step (binary64), or null
+ *   d_field[K*capacity*3]    final wake (x, z, Gamma) per rollout (binary64), or null
+ *   d_count[K]               final particle count per rollout, or null
+ * Errors: VPM_ERR_INVALID (K, H < 1, null controls/costs), VPM_ERR_CAPACITY (the count could
+ * exceed the capacity within H steps), VPM_ERR_CUDA.
+ */
+vpm_status vpm_rollout_batch(const vpm_state *root, int K, int H, const float *d_controls,
+                             float *d_costs, double *d_final_glider, double *d_traj,
+                             double *d_field, int *d_count, cudaStream_t stream);
+
+/*
+ * Same results as vpm_rollout_batch computed in the plain one-rollout-per-launch form: every
+ * step of every rollout is its own single-block launch (H x K launches) and each rollout's
+ * field lives in global memory between launches. Kept as the comparison baseline for the
+ * persistent form. Uses library-allocated scratch (stream-ordered allocation).
+ */
+vpm_status vpm_rollout_batch_per_launch(const vpm_state *root, int K, int H,
+                                        const float *d_controls, float *d_costs,
+                                        double *d_final_glider, cudaStream_t stream);
+
+/*
+ * MPPI weights of §IV-A, Eq. 25: w_i = eta exp(-(J_i - J_min) / lambda), eta normalising the
+ * sum to 1. d_costs[K] binary32 in, d_weights[K] binary32 out; exponentials and sums in
+ * binary64 in a fixed order (deterministic). Errors: VPM_ERR_INVALID (K < 1, lambda <= 0).
+ */
+vpm_status mppi_weights(const float *d_costs, int K, float lambda, float *d_weights,
+                        cudaStream_t stream);
+
+/* Reweighted control sequence of Eq. 25: d_mu[k] = sum_i d_weights[i] d_controls[i*H + k]
+ * (binary64 sums, fixed order). */
+vpm_status mppi_update(const float *d_weights, const float *d_controls, int K, int H,
+                       float *d_mu, cudaStream_t stream);
+
+/* Sampled control sequences xi_i = mu + eps_i (§IV-A): d_controls[i*H + k] =
+ * d_mu[k] + d_eps[i*H + k]. The noise is an input so that it can be drawn anywhere. */
+vpm_status mppi_perturb(const float *d_mu, const float *d_eps, int K, int H,
+                        float *d_controls, cudaStream_t stream);
+
+/*
+ * Free-field velocities (Eq. 3 with the chosen kernel, self term excluded) of n particles
+ * d_particles[n*4] = (x, z, Gamma, unused) binary32; d_vel[n*2] receives (u, w). Binary32
+ * pair sums, compensated across source tiles.
+ */
+vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel, double r_core,
+                                  float *d_vel, cudaStream_t stream);
+
+/*
+ * `steps` Heun (explicit trapezoidal RK2) steps of a free field in place:
+ * v1 = V(r), r* = r + dt v1, v2 = V(r*), r <- r + dt (v1 + v2) / 2. d_particles as above.
+ * Uses 24 n bytes of library-allocated scratch (stream-ordered allocation).
+ */
+vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, double r_core, double dt,
+                              int steps, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VPM_H */

@@ -1,0 +1,284 @@
+"""Python binding of the B300 VPM rollout library (libvpm.so, C ABI in include/vpm.h).
+
+The binding only marshals arguments: every step of the model runs in the library's CUDA
+kernels. PyTorch provides device memory (tensors) and streams (the current stream of the
+current device). If libvpm.so is missing, the first call raises; there is no CPU fallback.
+
+Build the library with `python -m paper_2509_16079_b300.build`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvpm.so")
+
+VPM_OK, VPM_ERR_INVALID, VPM_ERR_OOM, VPM_ERR_CAPACITY, VPM_ERR_NONFINITE, VPM_ERR_TIMEOUT, \
+    VPM_ERR_CUDA, VPM_ERR_BUSY, VPM_ERR_SINGULAR = range(9)
+KERNEL_SINGULAR, KERNEL_VATISTAS, KERNEL_GAUSSIAN = 0, 1, 2
+FP32, FP64 = 0, 1
+GATE_OFF, GATE_BOTH, GATE_LEV = 0, 1, 2
+N_B_MAX = 32
+
+_STATUS_NAMES = {0: "VPM_OK", 1: "VPM_ERR_INVALID", 2: "VPM_ERR_OOM", 3: "VPM_ERR_CAPACITY",
+                 4: "VPM_ERR_NONFINITE", 5: "VPM_ERR_TIMEOUT", 6: "VPM_ERR_CUDA",
+                 7: "VPM_ERR_BUSY", 8: "VPM_ERR_SINGULAR"}
+
+
+class VpmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class Params(C.Structure):
+    """Mirror of vpm_params."""
+    _fields_ = [
+        ("n_b", C.c_int), ("chord", C.c_double), ("span", C.c_double), ("rho", C.c_double),
+        ("wake_kernel", C.c_int), ("r_core", C.c_double), ("shed_offset", C.c_double),
+        ("gamma_decay", C.c_double), ("shed_gate", C.c_int), ("alpha_crit", C.c_double),
+        ("n_wake_max", C.c_int), ("u_inf", C.c_double * 2), ("dt", C.c_double),
+        ("fixed_plate", C.c_int), ("mass", C.c_double), ("inertia", C.c_double),
+        ("g", C.c_double), ("l", C.c_double), ("l_w", C.c_double), ("l_e", C.c_double),
+        ("s_e", C.c_double), ("q", C.c_double * 7), ("x_d", C.c_double * 7),
+        ("precision", C.c_int),
+    ]
+
+
+def make_params(d: dict, precision: int = FP32) -> Params:
+    p = Params()
+    for k in ("n_b", "wake_kernel", "shed_gate", "n_wake_max", "fixed_plate"):
+        setattr(p, k, int(d[k]))
+    for k in ("chord", "span", "rho", "r_core", "shed_offset", "gamma_decay", "alpha_crit",
+              "dt", "mass", "inertia", "g", "l", "l_w", "l_e", "s_e"):
+        setattr(p, k, float(d[k]))
+    p.u_inf[0], p.u_inf[1] = (float(v) for v in d["u_inf"])
+    for i in range(7):
+        p.q[i] = float(d["q"][i])
+        p.x_d[i] = float(d["x_d"][i])
+    p.precision = int(precision)
+    return p
+
+
+_VP, _I, _D, _F = C.c_void_p, C.c_int, C.c_double, C.c_float
+_SIGNATURES = {
+    "vpm_last_error": ([], C.c_char_p),
+    "vpm_version": ([], C.c_char_p),
+    "vpm_state_create": ([C.POINTER(Params), _VP, _I, _I, _VP, C.POINTER(_VP), _VP], _I),
+    "vpm_state_destroy": ([_VP], _I),
+    "vpm_state_set_history": ([_VP, _VP, _D, _I, _VP], _I),
+    "vpm_state_read": ([_VP, _VP, C.POINTER(_I), _VP, _VP, _VP], _I),
+    "vpm_state_status": ([_VP, _VP], _I),
+    "vpm_state_save": ([_VP, _VP, C.POINTER(C.c_size_t), _VP], _I),
+    "vpm_state_load": ([_VP, _VP, C.c_size_t, _VP], _I),
+    "vpm_step": ([_VP, _D, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_rollout_batch": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_rollout_batch_per_launch": ([_VP, _I, _I, _VP, _VP, _VP, _VP], _I),
+    "mppi_weights": ([_VP, _I, _F, _VP, _VP], _I),
+    "mppi_update": ([_VP, _VP, _I, _I, _VP, _VP], _I),
+    "mppi_perturb": ([_VP, _VP, _I, _I, _VP, _VP], _I),
+    "vpm_freefield_velocity": ([_VP, _I, _I, _D, _VP, _VP], _I),
+    "vpm_freefield_heun": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libvpm.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libvpm.so is not built (run python -m paper_2509_16079_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def check(status: int):
+    """Raises VpmError carrying vpm_last_error() for a non-zero status."""
+    if status != VPM_OK:
+        raise VpmError(status, lib().vpm_last_error().decode())
+
+
+def stream_handle(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev_tensor(t, dtype, shape=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor of %s" % dtype)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+    return t
+
+
+class State:
+    """A resident model (glider + wake) on the current CUDA device."""
+
+    def __init__(self, params: dict, particles, glider7, capacity: int, precision: int = FP32,
+                 stream=None):
+        self.params = dict(params)
+        self.precision = precision
+        self._P = make_params(params, precision)
+        parts = np.ascontiguousarray(np.asarray(particles, dtype=np.float64).reshape(-1, 3))
+        xg = np.ascontiguousarray(np.asarray(glider7, dtype=np.float64))
+        self.capacity = int(capacity)
+        h = C.c_void_p()
+        check(lib().vpm_state_create(C.byref(self._P), parts.ctypes.data_as(_VP), len(parts),
+                                     self.capacity, xg.ctypes.data_as(_VP), C.byref(h),
+                                     stream_handle(stream)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vpm_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_history(self, gb_prev, glev_prev: float, has_prev: bool, stream=None):
+        gb = np.ascontiguousarray(np.asarray(gb_prev, dtype=np.float64))
+        check(lib().vpm_state_set_history(self._h, gb.ctypes.data_as(_VP), float(glev_prev),
+                                          int(has_prev), stream_handle(stream)))
+
+    def read(self, stream=None):
+        """Returns (particles (n, 3) float64, glider (7,), hist (n_b + 2,))."""
+        parts = np.zeros((self.capacity, 3))
+        xg = np.zeros(7)
+        hist = np.zeros(int(self.params["n_b"]) + 2)
+        n = C.c_int()
+        check(lib().vpm_state_read(self._h, parts.ctypes.data_as(_VP), C.byref(n),
+                                   xg.ctypes.data_as(_VP), hist.ctypes.data_as(_VP),
+                                   stream_handle(stream)))
+        return parts[:n.value].copy(), xg, hist
+
+    def status(self, stream=None):
+        check(lib().vpm_state_status(self._h, stream_handle(stream)))
+
+    def save(self, stream=None) -> bytes:
+        size = C.c_size_t()
+        check(lib().vpm_state_save(self._h, None, C.byref(size), stream_handle(stream)))
+        buf = C.create_string_buffer(size.value)
+        check(lib().vpm_state_save(self._h, C.cast(buf, _VP), C.byref(size), stream_handle(stream)))
+        return buf.raw[:size.value]
+
+    def load(self, blob: bytes, stream=None):
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib().vpm_state_load(self._h, C.cast(buf, _VP), len(blob), stream_handle(stream)))
+
+    def step(self, u: float = 0.0, probe: bool = False, stream=None):
+        """One committed step; with probe=True returns the step's quantities as tensors."""
+        import torch
+        out = {}
+        if probe:
+            nb = int(self.params["n_b"])
+            dev = torch.device("cuda", torch.cuda.current_device())
+            out = dict(fm=torch.zeros(3, dtype=torch.float64, device=dev),
+                       gamma_s=torch.zeros(nb + 2, dtype=torch.float64, device=dev),
+                       vel=torch.zeros(2 * self.capacity, dtype=torch.float64, device=dev),
+                       vtilde=torch.zeros(2 * (2 * nb + 1), dtype=torch.float64, device=dev))
+        check(lib().vpm_step(self._h, float(u), ptr(out.get("fm")), ptr(out.get("gamma_s")),
+                             ptr(out.get("vel")), ptr(out.get("vtilde")), stream_handle(stream)))
+        return out
+
+    def rollout_batch(self, controls, want_final: bool = True, want_traj: bool = False,
+                      want_field: bool = False, costs=None, stream=None):
+        """K rollouts of H steps under controls (K, H) float32 CUDA tensor."""
+        import torch
+        controls = _dev_tensor(controls, torch.float32)
+        K, H = controls.shape
+        dev = controls.device
+        out = dict(costs=costs if costs is not None else torch.empty(K, dtype=torch.float32, device=dev))
+        if want_final:
+            out["final_glider"] = torch.empty((K, 7), dtype=torch.float64, device=dev)
+        if want_traj:
+            out["traj"] = torch.empty((K, H, 7), dtype=torch.float64, device=dev)
+        if want_field:
+            out["field"] = torch.zeros((K, self.capacity, 3), dtype=torch.float64, device=dev)
+            out["count"] = torch.zeros(K, dtype=torch.int32, device=dev)
+        check(lib().vpm_rollout_batch(self._h, K, H, ptr(controls), ptr(out["costs"]),
+                                      ptr(out.get("final_glider")), ptr(out.get("traj")),
+                                      ptr(out.get("field")), ptr(out.get("count")),
+                                      stream_handle(stream)))
+        return out
+
+    def rollout_batch_per_launch(self, controls, stream=None):
+        import torch
+        controls = _dev_tensor(controls, torch.float32)
+        K, H = controls.shape
+        costs = torch.empty(K, dtype=torch.float32, device=controls.device)
+        fin = torch.empty((K, 7), dtype=torch.float64, device=controls.device)
+        check(lib().vpm_rollout_batch_per_launch(self._h, K, H, ptr(controls), ptr(costs),
+                                                 ptr(fin), stream_handle(stream)))
+        return dict(costs=costs, final_glider=fin)
+
+
+def mppi_weights(costs, lam: float, out=None, stream=None):
+    import torch
+    costs = _dev_tensor(costs, torch.float32)
+    w = out if out is not None else torch.empty_like(costs)
+    check(lib().mppi_weights(ptr(costs), costs.numel(), float(lam), ptr(w), stream_handle(stream)))
+    return w
+
+
+def mppi_update(weights, controls, out=None, stream=None):
+    import torch
+    weights = _dev_tensor(weights, torch.float32)
+    controls = _dev_tensor(controls, torch.float32)
+    K, H = controls.shape
+    mu = out if out is not None else torch.empty(H, dtype=torch.float32, device=controls.device)
+    check(lib().mppi_update(ptr(weights), ptr(controls), K, H, ptr(mu), stream_handle(stream)))
+    return mu
+
+
+def mppi_perturb(mu, eps, out=None, stream=None):
+    import torch
+    mu = _dev_tensor(mu, torch.float32)
+    eps = _dev_tensor(eps, torch.float32)
+    K, H = eps.shape
+    c = out if out is not None else torch.empty_like(eps)
+    check(lib().mppi_perturb(ptr(mu), ptr(eps), K, H, ptr(c), stream_handle(stream)))
+    return c
+
+
+def freefield_velocity(particles, kernel: int, r_core: float, out=None, stream=None):
+    """particles: (n, 4) float32 CUDA tensor (x, z, Gamma, unused) -> (n, 2) velocities."""
+    import torch
+    particles = _dev_tensor(particles, torch.float32)
+    n = particles.shape[0]
+    v = out if out is not None else torch.empty((n, 2), dtype=torch.float32, device=particles.device)
+    check(lib().vpm_freefield_velocity(ptr(particles), n, int(kernel), float(r_core), ptr(v),
+                                       stream_handle(stream)))
+    return v
+
+
+def freefield_heun(particles, kernel: int, r_core: float, dt: float, steps: int, stream=None):
+    """In-place Heun steps of a free field (n, 4) float32 CUDA tensor."""
+    import torch
+    particles = _dev_tensor(particles, torch.float32)
+    check(lib().vpm_freefield_heun(ptr(particles), particles.shape[0], int(kernel),
+                                   float(r_core), float(dt), int(steps), stream_handle(stream)))
+    return particles

@@ -1,0 +1,576 @@
+// Persistent rollout kernel: one 128-thread block advances one rollout of the coupled
+// glider + VPM model (§III-A, §III-B) for the whole horizon with the field resident in shared
+// memory, then writes the terminal cost (Eq. 24). The same step code serves vpm_step (one
+// block, one step, state written back) and the one-rollout-per-launch comparison form.
+//
+// One step, in the order of §III-A: plate geometry from the glider state; relative velocity of
+// Eq. 12 at the collocation and bound points from the wake before shedding; the surface
+// circulation Gamma_S = K^-1 b of Eq. 11 with the body-frame inverse (K is constant in the
+// body frame, so its inverse is formed once on the host); unsteady Bernoulli loads (Eqs.
+// 13-15); the glider's explicit Euler update (Eqs. 18-22); LEV/TEV appended to the wake;
+// convection velocities of Eq. 16 for every wake particle; explicit Euler advection and the
+// decay of Eq. 17; merging of the two oldest particles while N > N_w,max.
+#include "vpm_rollout.cuh"
+
+namespace vpm {
+
+struct Geo {
+    double xw, zw, tx, tz, nx, nz, vx, vz, om;
+    int lev, tev;
+};
+
+// Shared-memory workspace of one rollout block (besides the particle and velocity arrays).
+struct Work {
+    double xg[7];
+    double hist[kMaxB + 2];          // previous Gamma_b, previous Gamma_LEV, has_prev flag
+    double vt[2 * (2 * kMaxB + 1)];  // relative velocity at collocation then bound points
+    double gs[kMaxS];                // Gamma_b, Gamma_LEV, Gamma_TEV of this step
+    double fm[3];
+    double red[kThreads / 32];
+    float bnd_f[4 * kMaxB];          // bound positions as (x_hi, x_lo, z_hi, z_lo)
+    float gb_f[kMaxB];               // bound circulations (binary32 copy)
+    Geo geo;
+    int n;
+    int flag;
+};
+
+// ------------------------------------------------------------------ geometry (thread 0)
+
+__device__ void plate_geometry(const DevParams &p, Work &w)
+{
+    const double *xg = w.xg;
+    double th = xg[2], c = cos(th), s = sin(th);
+    Geo &G = w.geo;
+    G.xw = xg[0] - p.l_w * c;
+    G.zw = xg[1] - p.l_w * s;
+    G.tx = -c; G.tz = -s;        // leading edge -> trailing edge
+    G.nx = -s; G.nz = c;         // body-up normal
+    if (p.fixed_plate) {
+        G.vx = 0.0; G.vz = 0.0; G.om = 0.0;
+    } else {
+        G.vx = xg[4] + p.l_w * xg[6] * s;
+        G.vz = xg[5] - p.l_w * xg[6] * c;
+        G.om = xg[6];
+    }
+    double alpha = th - atan2(G.vz - p.u_inf_z, G.vx - p.u_inf_x);
+    alpha = atan2(sin(alpha), cos(alpha));
+    int open = fabs(alpha) > p.alpha_crit;
+    G.lev = (p.shed_gate == VPM_GATE_OFF) || open;
+    G.tev = (p.shed_gate != VPM_GATE_BOTH) || open;
+    for (int j = 0; j < p.n_b; ++j) {
+        double sj = -0.5 * p.chord + (j + 0.5) * p.lb;
+        double bx = G.xw + sj * G.tx, bz = G.zw + sj * G.tz;
+        float bxh = (float)bx, bzh = (float)bz;
+        w.bnd_f[4 * j + 0] = bxh;
+        w.bnd_f[4 * j + 1] = (float)(bx - (double)bxh);
+        w.bnd_f[4 * j + 2] = bzh;
+        w.bnd_f[4 * j + 3] = (float)(bz - (double)bzh);
+    }
+}
+
+// Target point t of the plate: collocation points 0..n_c-1, then bound points.
+__device__ __forceinline__ void plate_point(const DevParams &p, const Geo &G, int t, double &x,
+                                            double &z)
+{
+    double s = (t < p.n_c) ? (-0.5 * p.chord + t * p.lb)
+                           : (-0.5 * p.chord + (t - p.n_c + 0.5) * p.lb);
+    x = G.xw + s * G.tx;
+    z = G.zw + s * G.tz;
+}
+
+// ------------------------------------------------------------------ glider (§III-B)
+
+__device__ void glider_rhs(const DevParams &p, const double *xg, double fwx, double fwz,
+                           double mw, double u, double *f)
+{
+    double th = xg[2], ph = xg[3], xd = xg[4], zd = xg[5], thd = xg[6];
+    double ct = cos(th), st = sin(th), cp = cos(th + ph), sp = sin(th + ph);
+    // elevator velocity (Eq. 18) with phidot = u
+    double exd = xd + p.l * thd * st + p.l_e * (thd + u) * sp;
+    double ezd = zd - p.l * thd * ct - p.l_e * (thd + u) * cp;
+    // flat-plate elevator (Eqs. 19-20): C_n = 2 sin(alpha_e) along n_e = (-sin, cos)(th + ph)
+    double alpha_e = th + ph - atan2(ezd, exd);
+    double fe = 0.5 * p.rho * (exd * exd + ezd * ezd) * p.s_e * 2.0 * sin(alpha_e);
+    double fex = -fe * sp, fez = fe * cp;
+    // pitch moment about the centre of gravity with world-frame arms of x_w and x_e
+    double wx = -p.l_w * ct, wz = -p.l_w * st;
+    double ex = -p.l * ct - p.l_e * cp, ez = -p.l * st - p.l_e * sp;
+    double tq = (wx * fwz - wz * fwx) + (ex * fez - ez * fex) + mw;
+    f[0] = xd; f[1] = zd; f[2] = thd; f[3] = u;
+    f[4] = (fwx + fex) / p.mass;
+    f[5] = (fwz + fez) / p.mass - p.g;
+    f[6] = tq / p.inertia;
+}
+
+// ------------------------------------------------------------------ step phases
+
+// Phase A: wake-induced velocity at the plate points (Eq. 12's sum) and the Kelvin sum.
+// Each warp takes plate points in turn; its lanes split the sources and the partial sums
+// are reduced in binary64.
+template <class R, int KER>
+__device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>::P *part, int n)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int M = p.n_c + p.n_b;
+    for (int t = warp; t < M; t += kThreads / 32) {
+        double tx, tz;
+        plate_point(p, w.geo, t, tx, tz);
+        double su = 0.0, sw = 0.0;
+        if constexpr (sizeof(R) == 4) {
+            const float txf = (float)tx, tzf = (float)tz;
+            const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
+            float u = 0.f, v = 0.f;
+            for (int j = lane; j < n; j += 32) {
+                float4 s = part[j];
+                float dx = txf - s.x, dz = tzf - s.y;
+                float r2 = fmaf(dx, dx, dz * dz);
+                float g = s.z * PairF32<KER>::q(r2, rc4, irc2);
+                u = fmaf(-dz, g, u);
+                v = fmaf(dx, g, v);
+            }
+            su = u; sw = v;
+        } else {
+            for (int j = lane; j < n; j += 32) {
+                Part64 s = part[j];
+                double dx = tx - s.x, dz = tz - s.z;
+                double r2 = fma(dx, dx, dz * dz);
+                double g = s.g * PairF64<KER>::q(r2, p.rc4, p.inv_rc2);
+                su = fma(-dz, g, su);
+                sw = fma(dx, g, sw);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        }
+        if (lane == 0) {
+            w.vt[2 * t] = su * kInv2Pi;
+            w.vt[2 * t + 1] = sw * kInv2Pi;
+        }
+    }
+    double gsum = 0.0;
+    for (int j = tid; j < n; j += kThreads) gsum += Store<R>::gam(part[j]);
+    for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+    if (lane == 0) w.red[warp] = gsum;
+}
+
+// Phase B (thread 0): surface solve, loads, glider update, shedding. Returns the new count.
+template <class R>
+__device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *part, int n,
+                           double u_ctrl)
+{
+    const Geo &G = w.geo;
+    const int nb = p.n_b, nc = p.n_c, M = nc + nb;
+    // complete Eq. 12: free stream, minus plate translation and rotation e_z x (r_s - r_g)
+    for (int t = 0; t < M; ++t) {
+        double x, z;
+        plate_point(p, G, t, x, z);
+        double rx = x - G.xw, rz = z - G.zw;
+        w.vt[2 * t] += p.u_inf_x - G.vx + G.om * rz;
+        w.vt[2 * t + 1] += p.u_inf_z - G.vz - G.om * rx;
+    }
+    double gw = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) gw += w.red[i];
+    // right-hand side of Eq. 10 for the active rows, Gamma_S = K^-1 b (Eq. 11)
+    const int lev = G.lev, tev = G.tev, m = nb + lev + tev;
+    double b[kMaxS];
+    int r = 0;
+    for (int i = 0; i < nc; ++i) {
+        if ((i == 0 && !lev) || (i == nc - 1 && !tev)) continue;
+        b[r++] = -(w.vt[2 * i] * G.nx + w.vt[2 * i + 1] * G.nz);
+    }
+    b[r] = -gw;
+    const double *ki = p.kinv + (size_t)(lev * 2 + tev) * kMaxS * kMaxS;
+    double gs[kMaxS];
+    for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s = fma(__ldg(ki + i * kMaxS + j), b[j], s);
+        gs[i] = s;
+    }
+    for (int j = 0; j < nb; ++j) w.gs[j] = gs[j];
+    w.gs[nb] = lev ? gs[nb] : 0.0;
+    w.gs[nb + 1] = tev ? gs[nb + lev] : 0.0;
+    // unsteady Bernoulli pressure (Eq. 13) and wing load (Eqs. 14-15)
+    const bool hp = w.hist[nb + 1] != 0.0;
+    double cum = 0.0, cum_prev = 0.0, fwx = 0.0, fwz = 0.0, mw = 0.0;
+    const double dlev = hp ? (w.gs[nb] - w.hist[nb]) / p.dt : 0.0;
+    for (int i = 0; i < nb; ++i) {
+        cum += w.gs[i];
+        cum_prev += w.hist[i];
+        const double *vb = &w.vt[2 * (nc + i)];
+        double tang = (w.gs[i] / p.lb) * (vb[0] * G.tx + vb[1] * G.tz);
+        double dsum = hp ? (cum - cum_prev) / p.dt : 0.0;
+        double dp = p.rho * (tang + dsum + dlev);
+        double fx = p.lb * p.span * dp * G.nx, fz = p.lb * p.span * dp * G.nz;
+        fwx += fx;
+        fwz += fz;
+        double si = -0.5 * p.chord + (i + 0.5) * p.lb;
+        mw += (si * G.tx) * fz - (si * G.tz) * fx;
+    }
+    w.fm[0] = fwx; w.fm[1] = fwz; w.fm[2] = mw;
+    // glider explicit Euler update with this step's loads
+    if (!p.fixed_plate) {
+        double f[7];
+        glider_rhs(p, w.xg, fwx, fwz, mw, u_ctrl, f);
+        for (int c = 0; c < 7; ++c) w.xg[c] += p.dt * f[c];
+    }
+    for (int j = 0; j < nb; ++j) {
+        w.hist[j] = w.gs[j];
+        w.gb_f[j] = (float)w.gs[j];
+    }
+    w.hist[nb] = w.gs[nb];
+    w.hist[nb + 1] = 1.0;
+    bool finite = isfinite(fwx) && isfinite(fwz) && isfinite(mw);
+    for (int c = 0; c < 7; ++c) finite = finite && isfinite(w.xg[c]);
+    if (!finite) w.flag |= kStNonFinite;
+    // W <- W u E (LEV first, then TEV)
+    const double ds = p.shed_dist;
+    if (lev) {
+        double x, z;
+        plate_point(p, G, 0, x, z);
+        part[n++] = Store<R>::make(x - ds * G.tx, z - ds * G.tz, w.gs[nb]);
+    }
+    if (tev) {
+        double x, z;
+        plate_point(p, G, nc - 1, x, z);
+        part[n++] = Store<R>::make(x + ds * G.tx, z + ds * G.tz, w.gs[nb + 1]);
+    }
+    return n;
+}
+
+// Phase C: convection velocity of every wake particle (Eq. 16) plus the free stream.
+// Binary32: each lane holds two targets; sources stream from shared memory (broadcast loads)
+// in tiles of kTile whose plain sums are added into Kahan-compensated totals.
+constexpr int kTile = 64;
+
+template <int KER>
+__device__ void convect_f32(const DevParams &p, const Work &w, const float4 *part, float2 *vel,
+                            int n, double *probe_vel)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    const float inv2pi = (float)kInv2Pi;
+    const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
+    for (int base = warp * 64; base < n; base += kThreads * 2) {
+        const int ia = base + lane, ib = base + 32 + lane;
+        const float4 pa = part[ia < n ? ia : 0], pb = part[ib < n ? ib : 0];
+        const float xa = pa.x, za = pa.y, xb = pb.x, zb = pb.y;
+        float sua = 0.f, cua = 0.f, swa = 0.f, cwa = 0.f;
+        float sub = 0.f, cub = 0.f, swb = 0.f, cwb = 0.f;
+        for (int j0 = 0; j0 < n; j0 += kTile) {
+            const int je = min(n, j0 + kTile);
+            float ua = 0.f, wa = 0.f, ub = 0.f, wb = 0.f;
+#pragma unroll 4
+            for (int j = j0; j < je; ++j) {
+                const float4 s = part[j];
+                const float dxa = xa - s.x, dza = za - s.y;
+                const float dxb = xb - s.x, dzb = zb - s.y;
+                const float ga = s.z * PairF32<KER>::q(fmaf(dxa, dxa, dza * dza), rc4, irc2);
+                const float gb = s.z * PairF32<KER>::q(fmaf(dxb, dxb, dzb * dzb), rc4, irc2);
+                ua = fmaf(-dza, ga, ua);
+                wa = fmaf(dxa, ga, wa);
+                ub = fmaf(-dzb, gb, ub);
+                wb = fmaf(dxb, gb, wb);
+            }
+            kahan_add(sua, cua, ua);
+            kahan_add(swa, cwa, wa);
+            kahan_add(sub, cub, ub);
+            kahan_add(swb, cwb, wb);
+        }
+        // bound vortices: singular kernel (Eq. 4) with double-length displacements
+        float xla, zla, xlb, zlb;
+        unpack_lo(pa.w, xla, zla);
+        unpack_lo(pb.w, xlb, zlb);
+        float bua = 0.f, bwa = 0.f, bub = 0.f, bwb = 0.f;
+        for (int j = 0; j < p.n_b; ++j) {
+            const float bxh = w.bnd_f[4 * j], bxl = w.bnd_f[4 * j + 1];
+            const float bzh = w.bnd_f[4 * j + 2], bzl = w.bnd_f[4 * j + 3];
+            const float g = w.gb_f[j];
+            float dx = (xa - bxh) + (xla - bxl), dz = (za - bzh) + (zla - bzl);
+            float r2 = fmaf(dx, dx, dz * dz);
+            float q = r2 > 0.f ? g / r2 : 0.f;
+            bua = fmaf(-dz, q, bua);
+            bwa = fmaf(dx, q, bwa);
+            dx = (xb - bxh) + (xlb - bxl);
+            dz = (zb - bzh) + (zlb - bzl);
+            r2 = fmaf(dx, dx, dz * dz);
+            q = r2 > 0.f ? g / r2 : 0.f;
+            bub = fmaf(-dz, q, bub);
+            bwb = fmaf(dx, q, bwb);
+        }
+        const float ua = fmaf(((sua - cua) + bua), inv2pi, uix);
+        const float wa = fmaf(((swa - cwa) + bwa), inv2pi, uiz);
+        const float ub = fmaf(((sub - cub) + bub), inv2pi, uix);
+        const float wb = fmaf(((swb - cwb) + bwb), inv2pi, uiz);
+        if (ia < n) {
+            vel[ia] = make_float2(ua, wa);
+            if (probe_vel) { probe_vel[2 * ia] = ua; probe_vel[2 * ia + 1] = wa; }
+        }
+        if (ib < n) {
+            vel[ib] = make_float2(ub, wb);
+            if (probe_vel) { probe_vel[2 * ib] = ub; probe_vel[2 * ib + 1] = wb; }
+        }
+    }
+}
+
+template <int KER>
+__device__ void convect_f64(const DevParams &p, const Work &w, const Part64 *part, double2 *vel,
+                            int n, double *probe_vel)
+{
+    const Geo &G = w.geo;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        const Part64 pi = part[i];
+        double su = 0.0, sw = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const Part64 s = part[j];
+            double dx = pi.x - s.x, dz = pi.z - s.z;
+            double g = s.g * PairF64<KER>::q(fma(dx, dx, dz * dz), p.rc4, p.inv_rc2);
+            su = fma(-dz, g, su);
+            sw = fma(dx, g, sw);
+        }
+        for (int j = 0; j < p.n_b; ++j) {
+            double sj = -0.5 * p.chord + (j + 0.5) * p.lb;
+            double dx = pi.x - (G.xw + sj * G.tx), dz = pi.z - (G.zw + sj * G.tz);
+            double r2 = fma(dx, dx, dz * dz);
+            double q = r2 > 0.0 ? w.gs[j] / r2 : 0.0;
+            su = fma(-dz, q, su);
+            sw = fma(dx, q, sw);
+        }
+        double u = su * kInv2Pi + p.u_inf_x, v = sw * kInv2Pi + p.u_inf_z;
+        vel[i] = make_double2(u, v);
+        if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
+    }
+}
+
+// Phase D: explicit Euler advection (double-length positions on the binary32 path) and the
+// exact decay Gamma <- Gamma exp(-gamma dt) of Eq. 17.
+__device__ void advect_f32(const DevParams &p, Work &w, float4 *part, const float2 *vel, int n)
+{
+    const float dth = (float)p.dt, dtl = (float)(p.dt - (double)dth);
+    const float dch = (float)p.decay, dcl = (float)(p.decay - (double)dch);
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        float4 q = part[i];
+        const float2 v = vel[i];
+        bad |= !(isfinite(v.x) && isfinite(v.y));
+        float xl, zl;
+        unpack_lo(q.w, xl, zl);
+        const float ddx = fmaf(v.x, dth, fmaf(v.x, dtl, xl));
+        const float ddz = fmaf(v.y, dth, fmaf(v.y, dtl, zl));
+        float sx, ex, sz, ez;
+        two_sum(q.x, ddx, sx, ex);
+        two_sum(q.y, ddz, sz, ez);
+        q.x = sx;
+        q.y = sz;
+        q.z = fmaf(q.z, dcl, q.z * dch);
+        q.w = pack_lo(ex, ez);
+        part[i] = q;
+    }
+    if (bad) atomicOr(&w.flag, (int)kStNonFinite);
+}
+
+__device__ void advect_f64(const DevParams &p, Work &w, Part64 *part, const double2 *vel, int n)
+{
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        Part64 q = part[i];
+        const double2 v = vel[i];
+        bad |= !(isfinite(v.x) && isfinite(v.y));
+        q.x += p.dt * v.x;
+        q.z += p.dt * v.y;
+        q.g *= p.decay;
+        part[i] = q;
+    }
+    if (bad) atomicOr(&w.flag, (int)kStNonFinite);
+}
+
+// Merging (§III-A): while N > N_w,max the two oldest particles become one at their mean
+// position with the summed circulation; the merged particle stays the oldest. Applying it
+// m = N - N_w,max times merges records 0..m in order and shifts the rest down by m.
+template <class R>
+__device__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int n)
+{
+    using P = typename Store<R>::P;
+    if (p.n_wake_max <= 0 || n <= p.n_wake_max) return n;
+    const int m = n - p.n_wake_max;
+    __shared__ P s_merged;
+    if (threadIdx.x == 0) {
+        double x, z;
+        Store<R>::xz(part[0], x, z);
+        double g = Store<R>::gam(part[0]);
+        for (int q = 1; q <= m; ++q) {
+            double x2, z2;
+            Store<R>::xz(part[q], x2, z2);
+            x = 0.5 * (x + x2);
+            z = 0.5 * (z + z2);
+            g = g + Store<R>::gam(part[q]);
+        }
+        s_merged = Store<R>::make(x, z, g);
+    }
+    __syncthreads();
+    const int nn = n - m;
+    for (int base = 1; base < nn; base += kThreads) {
+        const int i = base + threadIdx.x;
+        P tmp;
+        if (i < nn) tmp = part[i + m];
+        __syncthreads();
+        if (i < nn) part[i] = tmp;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[0] = s_merged;
+    __syncthreads();
+    return nn;
+}
+
+// One full step of one rollout. All threads call it; returns with the block synchronised.
+template <class R, int KER>
+__device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *part,
+                          typename Store<R>::V *vel, double u_ctrl, const RolloutArgs &a,
+                          bool probe)
+{
+    const int tid = threadIdx.x;
+    int n = w.n;
+    if (tid == 0) plate_geometry(p, w);
+    __syncthreads();
+    plate_sums<R, KER>(p, w, part, n);
+    __syncthreads();
+    if (tid == 0) w.n = plate_solve<R>(p, w, part, n, u_ctrl);
+    __syncthreads();
+    n = w.n;
+    if (probe) {
+        const int M = p.n_c + p.n_b;
+        if (a.probe_vt) for (int t = tid; t < 2 * M; t += kThreads) a.probe_vt[t] = w.vt[t];
+        if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += kThreads) a.probe_gs[t] = w.gs[t];
+        if (a.probe_fm && tid < 3) a.probe_fm[tid] = w.fm[tid];
+    }
+    if constexpr (sizeof(R) == 4) {
+        convect_f32<KER>(p, w, part, vel, n, probe ? a.probe_vel : nullptr);
+        __syncthreads();
+        advect_f32(p, w, part, vel, n);
+    } else {
+        convect_f64<KER>(p, w, part, vel, n, probe ? a.probe_vel : nullptr);
+        __syncthreads();
+        advect_f64(p, w, part, vel, n);
+    }
+    __syncthreads();
+    n = merge_oldest<R>(p, part, n);
+    if (tid == 0) w.n = n;
+    __syncthreads();
+}
+
+template <class R>
+__device__ void load_state(const RolloutArgs &a, Work &w, typename Store<R>::P *part, int rid)
+{
+    using P = typename Store<R>::P;
+    const P *rp = static_cast<const P *>(a.root_part) + (size_t)rid * a.root_stride;
+    const int n = a.root_n[a.root_stride ? rid : 0];
+    for (int i = threadIdx.x; i < n; i += kThreads) part[i] = rp[i];
+    const double *g = a.root_glider + (size_t)rid * a.state_stride;
+    const double *h = a.root_hist + (size_t)rid * a.state_stride;
+    if (threadIdx.x < 7) w.xg[threadIdx.x] = g[threadIdx.x];
+    if (threadIdx.x < a.p.n_b + 2) w.hist[threadIdx.x] = h[threadIdx.x];
+    if (threadIdx.x == 0) { w.n = n; w.flag = 0; }
+    __syncthreads();
+}
+
+template <class R>
+__device__ void store_state(const RolloutArgs &a, Work &w, const typename Store<R>::P *part,
+                            int rid)
+{
+    using P = typename Store<R>::P;
+    P *op = static_cast<P *>(a.out_part) + (size_t)rid * a.out_stride;
+    const int n = w.n;
+    for (int i = threadIdx.x; i < n; i += kThreads) op[i] = part[i];
+    double *g = a.out_glider + (size_t)rid * a.out_state_stride;
+    double *h = a.out_hist + (size_t)rid * a.out_state_stride;
+    if (threadIdx.x < 7) g[threadIdx.x] = w.xg[threadIdx.x];
+    if (threadIdx.x < a.p.n_b + 2) h[threadIdx.x] = w.hist[threadIdx.x];
+    if (threadIdx.x == 0) a.out_n[a.out_stride ? rid : 0] = n;
+}
+
+template <class R>
+__device__ void finish(const RolloutArgs &a, Work &w, const typename Store<R>::P *part, int rid)
+{
+    const DevParams &p = a.p;
+    const int n = w.n;
+    if (threadIdx.x == 0) {
+        double J = 0.0;
+        for (int c = 0; c < 7; ++c) {
+            double d = w.xg[c] - p.x_d[c];
+            J += d * p.q[c] * d;
+        }
+        if (!isfinite(J)) w.flag |= kStNonFinite;
+        if (a.costs) a.costs[rid] = w.flag ? __int_as_float(0x7fc00000) : (float)J;
+        if (w.flag && a.status) atomicOr(a.status, w.flag);
+        if (a.count) a.count[rid] = n;
+    }
+    if (a.final_glider && threadIdx.x < 7) a.final_glider[rid * 7 + threadIdx.x] = w.xg[threadIdx.x];
+    if (a.field) {
+        double *f = a.field + (size_t)rid * a.field_cap * 3;
+        for (int i = threadIdx.x; i < n; i += kThreads) {
+            double x, z;
+            Store<R>::xz(part[i], x, z);
+            f[3 * i] = x;
+            f[3 * i + 1] = z;
+            f[3 * i + 2] = Store<R>::gam(part[i]);
+        }
+    }
+}
+
+// K rollouts (blockIdx.x + rid0 = rollout), H steps each, field resident in shared memory.
+template <class R, int KER>
+__global__ void __launch_bounds__(kThreads) rollout_kernel(const RolloutArgs a)
+{
+    using P = typename Store<R>::P;
+    using V = typename Store<R>::V;
+    extern __shared__ __align__(16) unsigned char smem[];
+    P *part = reinterpret_cast<P *>(smem);
+    V *vel = reinterpret_cast<V *>(smem + sizeof(P) * (size_t)a.cap);
+    __shared__ Work w;
+    const int rid = blockIdx.x + a.rid0;
+    load_state<R>(a, w, part, rid);
+    for (int k = 0; k < a.H; ++k) {
+        const double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k]
+                                    : a.u_const;
+        step_once<R, KER>(a.p, w, part, vel, u, a, a.H == 1);
+        if (a.traj && threadIdx.x < 7)
+            a.traj[((size_t)rid * a.H + k) * 7 + threadIdx.x] = w.xg[threadIdx.x];
+    }
+    if (a.out_part) store_state<R>(a, w, part, rid);
+    finish<R>(a, w, part, rid);
+}
+
+// ------------------------------------------------------------------ host-side launch helpers
+
+template <class R, int KER>
+static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    auto k = rollout_kernel<R, KER>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t rollout_smem_bytes(int precision, int cap)
+{
+    return precision == VPM_FP64 ? (size_t)cap * (sizeof(Part64) + sizeof(double2))
+                                 : (size_t)cap * (sizeof(float4) + sizeof(float2));
+}
+
+cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s)
+{
+    const size_t smem = rollout_smem_bytes(precision, a.cap);
+    const int ker = a.p.kernel;
+    if (precision == VPM_FP64) {
+        if (ker == VPM_KERNEL_GAUSSIAN) return launch_t<double, VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
+        if (ker == VPM_KERNEL_SINGULAR) return launch_t<double, VPM_KERNEL_SINGULAR>(a, grid, smem, s);
+        return launch_t<double, VPM_KERNEL_VATISTAS>(a, grid, smem, s);
+    }
+    if (ker == VPM_KERNEL_GAUSSIAN) return launch_t<float, VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
+    if (ker == VPM_KERNEL_SINGULAR) return launch_t<float, VPM_KERNEL_SINGULAR>(a, grid, smem, s);
+    return launch_t<float, VPM_KERNEL_VATISTAS>(a, grid, smem, s);
+}
+
+}  // namespace vpm

@@ -1,0 +1,39 @@
+// Argument block of the rollout kernel and the launch entry points of the rollout code.
+#pragma once
+
+#include "vpm_device.cuh"
+
+namespace vpm {
+
+struct RolloutArgs {
+    DevParams p;
+    const void *root_part;      // float4 or Part64 records
+    const int *root_n;
+    const double *root_glider;  // 7
+    const double *root_hist;    // n_b + 2
+    long long root_stride;      // records between rollouts of the root arrays (0: shared root)
+    long long state_stride;     // doubles between rollouts of glider / hist arrays (0: shared)
+    int H, K, cap, step0;
+    const float *controls;      // K x ctrl_stride (null: u_const every step)
+    int ctrl_stride;
+    double u_const;
+    int rid0;                   // index of the first rollout of this launch
+    float *costs;
+    double *final_glider, *traj, *field;
+    int field_cap;
+    int *count;
+    // write-back of the state (vpm_step, per-launch form)
+    long long out_stride;       // records between rollouts of the output arrays
+    long long out_state_stride; // doubles between rollouts of the output glider / hist arrays
+    void *out_part;
+    int *out_n;
+    double *out_glider, *out_hist;
+    // single-step probes
+    double *probe_fm, *probe_gs, *probe_vel, *probe_vt;
+    int *status;
+};
+
+size_t rollout_smem_bytes(int precision, int cap);
+cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s);
+
+}  // namespace vpm
