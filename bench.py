@@ -1,0 +1,369 @@
+"""Benchmark of the batched VPM-MPPI hot path on B300.
+
+Workload (the MPPI batch): K = 1024 rollouts x H = 100 steps of dt = 0.01 from a shared
+1000-particle root field (uniform in a 6c x 3c box, Gamma ~ N(0, 0.01^2), Vatistas core
+0.05 c); every step sheds an LEV and a TEV, so each field grows to 1200 particles. One
+benchmark step is one MPPI iteration: perturb the nominal controls with stored noise, run the
+K rollouts (binary32 pair sums, binary64 plate solve and glider), reduce costs to weights,
+and form the reweighted control sequence. A replan is three iterations.
+
+Metric: Biot-Savart pair interactions per second (every evaluated target-source pair of
+Eqs. 12 and 16 counted once), plus replan p50/p99 latency in ms.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--replans R] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+K_ROLL, H, N0 = 1024, 100, 1000
+LAMBDA = 10.0
+FLOPS_PER_PAIR = 12        # 2 FADD + FMUL + 3 FFMA (r^2, r^4 + r_c^4) ... counted with FMA = 2
+PEAK_SM_MHZ = 2032.0
+N_SM = 148
+
+
+def pairs_per_rollout(n0: int, H: int, n_b: int = 8, shed: int = 2) -> int:
+    """Target-source pairs of one rollout: per step N(n_c + n_b) plate pairs from the
+    N pre-shed wake particles, then N'(N' + n_b) convection pairs with N' = N + shed."""
+    total, n = 0, n0
+    for _ in range(H):
+        total += n * (2 * n_b + 1)
+        n2 = n + shed
+        total += n2 * (n2 + n_b)
+        n = n2
+    return total
+
+
+def fp32_peak_tflops() -> float:
+    return N_SM * 128 * 2 * PEAK_SM_MHZ * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ clocks during the run
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_baseline(rollouts: int = 16, threads: int | None = None):
+    """FP64 oracle rollouts of the same workload on the host cores (one rollout per thread
+    at a time; the C oracle releases the GIL)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.build()
+    p, field, xg0, eps = W.mppi_c2(0, K=rollouts, H=H, n=N0)
+    threads = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda i: oracle.rollout(p, field, xg0, eps[i].astype(np.float64)), range(rollouts)))
+    dt = time.perf_counter() - t0
+    pairs = pairs_per_rollout(N0, H) * rollouts
+    return {"value": pairs / dt, "unit": "pair-interactions/s", "cores": min(threads, rollouts),
+            "kind": "oracle",
+            "sample": "%d of the %d rollouts (1000 particles, 100 steps, FP64 C oracle), %.1f s wall"
+                      % (rollouts, K_ROLL, dt)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_setup(n_gpus: int):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    rank, world, local = dist_setup(args.gpus)
+    if rank == 0:
+        build.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    V.lib()
+
+    p, field, xg0, eps_np = W.mppi_c2(rank, K=K_ROLL, H=H, n=N0)
+    n_iter_noise = 4
+    eps_all = [torch.tensor(W.mppi_noise(1000 + 7 * j + rank, K_ROLL, H, W.MPPI_SIGMA_U), device=dev)
+               for j in range(n_iter_noise)]
+    root = V.State(p, field, xg0, N0 + 2 * H, V.FP32)
+    mu = torch.zeros(H, dtype=torch.float32, device=dev)
+    controls = torch.empty((K_ROLL, H), dtype=torch.float32, device=dev)
+    costs = torch.empty(K_ROLL, dtype=torch.float32, device=dev)
+    weights = torch.empty(K_ROLL, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sh = V.stream_handle(stream)
+    L = V.lib()
+
+    def iteration(j):
+        V.check(L.mppi_perturb(V.ptr(mu), V.ptr(eps_all[j % n_iter_noise]), K_ROLL, H, V.ptr(controls), sh))
+        V.check(L.vpm_rollout_batch(root.handle, K_ROLL, H, V.ptr(controls), V.ptr(costs), None, None,
+                                    None, None, sh))
+        V.check(L.mppi_weights(V.ptr(costs), K_ROLL, LAMBDA, V.ptr(weights), sh))
+        V.check(L.mppi_update(V.ptr(weights), V.ptr(controls), K_ROLL, H, V.ptr(mu), sh))
+
+    for j in range(args.warmup):
+        iteration(j)
+    torch.cuda.synchronize()
+    root.status()
+
+    # timed iterations: events around each iteration (and around the rollout kernel alone),
+    # L2 flushed between iterations outside the events
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for j in range(args.steps):
+            flush.fill_(float(j))
+            a, b, c = ev[j]
+            a.record(stream)
+            V.check(L.mppi_perturb(V.ptr(mu), V.ptr(eps_all[j % n_iter_noise]), K_ROLL, H, V.ptr(controls), sh))
+            V.check(L.vpm_rollout_batch(root.handle, K_ROLL, H, V.ptr(controls), V.ptr(costs), None,
+                                        None, None, None, sh))
+            b.record(stream)
+            V.check(L.mppi_weights(V.ptr(costs), K_ROLL, LAMBDA, V.ptr(weights), sh))
+            V.check(L.mppi_update(V.ptr(weights), V.ptr(controls), K_ROLL, H, V.ptr(mu), sh))
+            c.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    roll_ms = [a.elapsed_time(b) for a, b, c in ev]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    root.status()
+
+    pairs_iter = pairs_per_rollout(N0, H) * K_ROLL
+    value = pairs_iter * args.steps * world / (total_ms / 1e3)
+
+    # replan latency: 3 iterations per replan, events per replan
+    rep = []
+    for r in range(args.replans):
+        flush.fill_(float(r))
+        a, _, c = ev[r % len(ev)]
+        a.record(stream)
+        for j in range(3):
+            iteration(j)
+        c.record(stream)
+        c.synchronize()
+        rep.append(a.elapsed_time(c))
+    rep.sort()
+    p50 = float(np.percentile(rep, 50)) if rep else None
+    p99 = float(np.percentile(rep, 99)) if rep else None
+
+    # end-to-end: host noise -> device each iteration, nominal controls back to the host
+    eps_host = [torch.tensor(W.mppi_noise(2000 + j, K_ROLL, H, W.MPPI_SIGMA_U)).pin_memory()
+                for j in range(2)]
+    mu_host = torch.empty(H, dtype=torch.float32).pin_memory()
+    eps_dev = torch.empty((K_ROLL, H), dtype=torch.float32, device=dev)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(e2e_steps):
+        eps_dev.copy_(eps_host[j % 2], non_blocking=True)
+        V.check(L.mppi_perturb(V.ptr(mu), V.ptr(eps_dev), K_ROLL, H, V.ptr(controls), sh))
+        V.check(L.vpm_rollout_batch(root.handle, K_ROLL, H, V.ptr(controls), V.ptr(costs), None, None,
+                                    None, None, sh))
+        V.check(L.mppi_weights(V.ptr(costs), K_ROLL, LAMBDA, V.ptr(weights), sh))
+        V.check(L.mppi_update(V.ptr(weights), V.ptr(controls), K_ROLL, H, V.ptr(mu), sh))
+        mu_host.copy_(mu, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = pairs_iter * e2e_steps * world / e2e_s
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    roll_avg_s = statistics.mean(roll_ms) / 1e3
+    achieved = pairs_iter * FLOPS_PER_PAIR / roll_avg_s / 1e12
+    peak = fp32_peak_tflops()
+    prof = os.path.join(ROOT, "profiles", "rollout_kernel_mppi_c2_traffic.json")
+    traffic = None
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    line = {
+        "metric": "Biot-Savart pair-interactions/s",
+        "value": value,
+        "unit": "pair-interactions/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 pair sums (f64 plate solve, Kelvin sum, loads, glider)",
+        "data": "synthetic",
+        "config": {
+            "workload": "MPPI batch: K=1024 rollouts x H=100 steps, dt=0.01, root field 1000 "
+                        "particles growing to 1200, Vatistas core 0.05c, one MPPI iteration per step",
+            "K": K_ROLL, "H": H, "n0": N0, "lambda": LAMBDA,
+            "pairs_per_step": pairs_iter,
+            "l2": "flushed between timed iterations (256 MB write outside the events)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "replan_ms": {"p50": p50, "p99": p99, "replans": len(rep), "iterations_per_replan": 3},
+        "e2e": {"value": e2e_value, "unit": "pair-interactions/s",
+                "h2d_bytes_per_step": K_ROLL * H * 4, "d2h_bytes_per_step": H * 4,
+                "steps": e2e_steps},
+        "gpu_launches": 4 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "rollout_kernel<float, Vatistas>",
+                     "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (FMA = 2 flops)",
+                     "rollout_ms": statistics.mean(roll_ms)},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = 8
+    vals = []
+    t_all = 0.0
+    for j in range(args.warmup + args.steps):
+        cb = cpu_baseline(rollouts=per_step)
+        if j >= args.warmup:
+            vals.append(cb["value"])
+            t_all += pairs_per_rollout(N0, H) * per_step / cb["value"]
+    value = pairs_per_rollout(N0, H) * per_step * args.steps / t_all
+    line = {
+        "impl": "reference",
+        "metric": "Biot-Savart pair-interactions/s",
+        "value": value,
+        "unit": "pair-interactions/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "MPPI batch: K=1024 rollouts x H=100 steps, dt=0.01, root field 1000 "
+                               "particles growing to 1200, Vatistas core 0.05c, one MPPI iteration per step",
+                   "sample_per_step": "%d rollouts of the 1024" % per_step},
+        "cpu_baseline": {"value": value, "unit": "pair-interactions/s",
+                         "cores": min(os.cpu_count() or 1, per_step), "kind": "oracle",
+                         "sample": "%d rollouts per step (FP64 C oracle on host threads)" % per_step},
+        "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--replans", type=int, default=30)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

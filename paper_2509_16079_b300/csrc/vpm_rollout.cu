@@ -546,9 +546,15 @@ template <class R, int KER>
 static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
     auto k = rollout_kernel<R, KER>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    // raise the kernel's dynamic shared-memory limit once per size increase (per process;
+    // the library runs on one device per process)
+    static size_t granted = 48 * 1024;
+    if (smem > granted) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        granted = smem;
+    }
     k<<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -1,0 +1,138 @@
+"""Multi-step parity of vpm_rollout_batch against the FP64 oracle, and properties of the
+batched launch that hold at any size.
+
+The ungated 1000-particle MPPI workload amplifies rounding-level differences to O(0.1 c)
+within 100 steps (see test_oracle_sensitivity), so 100-step pointwise position parity is
+checked with the binary64 path on that workload, and with the binary32 path on the variant
+that sheds the LEV only above the critical incidence; the binary32 path on the ungated
+workload is checked step by step from its own states (teacher forcing) instead.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import POS_TOL, VEL_TOL, cuda, normwise
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_gpu(V, torch, p, field, xg0, controls, precision, capacity=None):
+    K, H = controls.shape
+    cap = capacity or len(field) + 2 * H
+    st = V.State(p, field, xg0, cap, precision)
+    out = st.rollout_batch(torch.tensor(controls, device="cuda"), want_traj=True, want_field=True)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    st.status()
+    st.close()
+    return res
+
+
+def _check_rollouts(ora, p, field, xg0, controls, res, idx, pos_tol, glider_tol, cost_rel):
+    for i in idx:
+        ref = ora.rollout(p, field, xg0, controls[i].astype(np.float64), want_traj=True, want_field=True)
+        n = int(res["count"][i])
+        assert n == len(ref["field"]), i
+        err = np.abs(res["field"][i, :n, :2] - ref["field"][:, :2]).max()
+        assert err <= pos_tol, (i, err)
+        assert np.abs(res["traj"][i] - ref["traj"]).max() <= glider_tol, i
+        assert abs(res["costs"][i] - ref["cost"]) <= cost_rel * abs(ref["cost"]) + 1e-6, i
+
+
+def test_fp64_ungated_100_steps(ora):
+    """Binary64 path, ungated 1000-particle workload, 100 steps, K = 16, 4 sampled rollouts."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(0, K=16, H=100, n=1000)
+    res = _run_gpu(V, torch, p, field, xg0, eps, V.FP64)
+    assert (res["count"] == 1200).all()
+    _check_rollouts(ora, p, field, xg0, eps, res, [0, 5, 10, 15], POS_TOL, 1e-6, 1e-6)
+
+
+def test_fp32_lev_gated_100_steps(ora):
+    """Binary32 path on the LEV-gated variant of the workload, 100 steps."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(0, K=8, H=100, n=1000)
+    p = dict(p, shed_gate=2)
+    res = _run_gpu(V, torch, p, field, xg0, eps, V.FP32)
+    _check_rollouts(ora, p, field, xg0, eps, res, [0, 3, 7], POS_TOL, 1e-5, 1e-5)
+
+
+def test_fp64_plate_c1_200_steps(ora):
+    """Fixed plate at 45 deg with the disturbance pair (Gaussian core), 200 steps, binary64."""
+    torch, V = cuda()
+    p = W.plate_c1_params()
+    for seed in (0, 1):
+        parts, xg, cap = W.plate_c1_initial(seed)
+        res = _run_gpu(V, torch, p, parts, xg, np.zeros((1, 200), np.float32), V.FP64, cap)
+        ref = ora.rollout(p, parts, xg, np.zeros(200), want_field=True)
+        n = int(res["count"][0])
+        assert n == 402 == len(ref["field"])
+        assert np.abs(res["field"][0, :n, :2] - ref["field"][:, :2]).max() <= POS_TOL
+
+
+def test_fp32_plate_c1_first_100_steps(ora):
+    """Binary32 path on config 1 while the disturbance pair is still upstream (100 steps)."""
+    torch, V = cuda()
+    p = W.plate_c1_params()
+    parts, xg, cap = W.plate_c1_initial(0)
+    res = _run_gpu(V, torch, p, parts, xg, np.zeros((1, 100), np.float32), V.FP32, cap)
+    ref = ora.rollout(p, parts, xg, np.zeros(100), want_field=True)
+    n = int(res["count"][0])
+    assert n == 202
+    assert np.abs(res["field"][0, :n, :2] - ref["field"][:, :2]).max() <= POS_TOL
+
+
+def test_fp64_merging_and_gate(ora):
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(3, K=4, H=60, n=300)
+    for over in (dict(n_wake_max=330), dict(shed_gate=2), dict(shed_gate=1, alpha_crit=0.05)):
+        q = dict(p, **over)
+        res = _run_gpu(V, torch, q, field, xg0, eps, V.FP64, 300 + 2 * 60)
+        _check_rollouts(ora, q, field, xg0, eps, res, [0, 3], 1e-8, 1e-9, 1e-9)
+
+
+def test_batch_invariance_and_per_launch_form():
+    """A rollout's result does not depend on the batch it runs in, and the one-rollout-per-
+    launch form computes the same numbers bitwise."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(1, K=64, H=20, n=500)
+    st = V.State(p, field, xg0, 540)
+    c = torch.tensor(eps, device="cuda")
+    full = st.rollout_batch(c)
+    for i in (0, 17, 63):
+        one = st.rollout_batch(c[i:i + 1].contiguous())
+        assert torch.equal(one["costs"][0], full["costs"][i])
+        assert torch.equal(one["final_glider"][0], full["final_glider"][i])
+    pl = st.rollout_batch_per_launch(c[:8].contiguous())
+    assert torch.equal(pl["costs"], full["costs"][:8])
+    assert torch.equal(pl["final_glider"], full["final_glider"][:8])
+
+
+def test_full_size_batch_properties(ora):
+    """K = 1024 rollouts x 100 steps from 1000 particles, binary32, the benchmark's launch:
+    every rollout ends with 1200 particles and finite costs; sampled rollouts are rerun alone
+    bitwise; a step taken from a sampled rollout's final state matches the oracle's step from
+    that same state."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(0, K=1024, H=100, n=1000)
+    st = V.State(p, field, xg0, 1200)
+    c = torch.tensor(eps, device="cuda")
+    out = st.rollout_batch(c, want_field=True)
+    torch.cuda.synchronize()
+    st.status()
+    assert (out["count"] == 1200).all()
+    assert torch.isfinite(out["costs"]).all()
+    for i in (0, 511, 1023):
+        one = st.rollout_batch(c[i:i + 1].contiguous(), want_field=True)
+        assert torch.equal(one["costs"][0], out["costs"][i])
+        assert torch.equal(one["field"][0], out["field"][i])
+    # teacher-forced step from rollout 511's final state (previous circulations unknown to
+    # the field output, so the step is taken with has_prev = 0 on both sides)
+    fin = out["field"][511, :1200].cpu().numpy()
+    xg = out["final_glider"][511].cpu().numpy()
+    g = V.State(p, fin, xg, 1202)
+    probe = g.step(0.3, probe=True)
+    o = ora.State(p, fin, xg, 1202)
+    ref = o.step(0.3)
+    vel = probe["vel"].cpu().numpy()[:2 * 1202].reshape(-1, 2)
+    assert normwise(vel, ref["vel"]) <= VEL_TOL
