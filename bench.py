@@ -310,6 +310,27 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """A few launches of the MPPI iteration at a reduced size, for ncu captures."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    K, Hh = args.rollouts, args.horizon
+    p, field, xg0, _ = W.mppi_c2(0, K=1, H=1, n=N0)
+    eps = torch.tensor(W.mppi_noise(1000, K, Hh, W.MPPI_SIGMA_U), device="cuda")
+    root = V.State(p, field, xg0, N0 + 2 * Hh, V.FP32)
+    mu = torch.zeros(Hh, dtype=torch.float32, device="cuda")
+    for j in range(args.warmup + args.steps):
+        c = V.mppi_perturb(mu, eps)
+        out = root.rollout_batch(c, want_final=False)
+        w = V.mppi_weights(out["costs"], LAMBDA)
+        mu = V.mppi_update(w, c)
+    torch.cuda.synchronize()
+    root.status()
+    print(json.dumps({"profile_case": True, "K": K, "H": Hh, "launches": 4 * (args.warmup + args.steps)}))
+
+
 # ------------------------------------------------------------------ reference arm (oracle)
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -358,9 +379,15 @@ def main():
     ap.add_argument("--replans", type=int, default=30)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
+    ap.add_argument("--horizon", type=int, default=H)
+    ap.add_argument("--rollouts", type=int, default=K_ROLL)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case:
+        run_profile_case(args)
     else:
         run_gpu(args)
 

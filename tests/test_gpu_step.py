@@ -82,7 +82,9 @@ def test_step_parity(ora, case, precision):
         pos_tol = params["dt"] * tol * vmax + (1e-9 if precision == V.FP32 else 1e-13)
         if len(parts_g):
             assert np.abs(parts_g[:, :2] - o.particles[:, :2]).max() <= pos_tol, msg
-            assert np.abs(parts_g[:, 2] - o.particles[:, 2]).max() <= 1e-6 * max(1e-3, np.abs(o.particles[:, 2]).max()), msg
+            # shed circulations are surface-solve outputs and carry its tolerance
+            g_scale = max(1e-3, np.abs(ref["gamma_s"]).max(), np.abs(o.particles[:, 2]).max())
+            assert np.abs(parts_g[:, 2] - o.particles[:, 2]).max() <= tol * g_scale, msg
         # glider: dt times the load tolerance divided by the mass (and inertia)
         g_tol = params["dt"] * (tol / params["dt"]) * f_scale / min(params["mass"], params["inertia"])
         assert np.allclose(xg_g, o.xg, rtol=0, atol=g_tol + 1e-12), msg
