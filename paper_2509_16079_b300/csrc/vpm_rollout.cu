@@ -148,8 +148,17 @@ __device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>:
             w.vt[2 * t + 1] = sw * kInv2Pi;
         }
     }
-    double gsum = 0.0;
-    for (int j = tid; j < n; j += kThreads) gsum += Store<R>::gam(part[j]);
+    // Kelvin sum (Eq. 7): each thread's share summed exactly enough in compensated arithmetic
+    // of the storage type, then combined in binary64 in a fixed order
+    double gsum;
+    if constexpr (sizeof(R) == 4) {
+        float s = 0.f, c = 0.f;
+        for (int j = tid; j < n; j += kThreads) kahan_add(s, c, part[j].z);
+        gsum = (double)s - (double)c;
+    } else {
+        gsum = 0.0;
+        for (int j = tid; j < n; j += kThreads) gsum += part[j].g;
+    }
     for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
     if (lane == 0) w.red[warp] = gsum;
 }
@@ -239,78 +248,87 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
 }
 
 // Phase C: convection velocity of every wake particle (Eq. 16) plus the free stream.
-// Binary32: each lane holds two targets; sources stream from shared memory (broadcast loads)
-// in tiles of kTile whose plain sums are added into Kahan-compensated totals.
+// Binary32: thread t owns targets t, t + 128, t + 256, ... and processes them T at a time
+// (T = 4, then 2, then 1 for the remainder), so all warps carry the same load. Sources stream
+// from shared memory by broadcast loads, each serving T pairs; plain sums over tiles of kTile
+// sources are added into Kahan-compensated totals.
 constexpr int kTile = 64;
+
+template <int KER, int T>
+__device__ __forceinline__ void convect_chunk(const DevParams &p, const Work &w,
+                                              const float4 *part, float2 *vel, int n, int i0,
+                                              double *probe_vel)
+{
+    const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    float tx[T], tz[T], su[T], cu[T], sw[T], cw[T];
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        const int i = i0 + k * kThreads;
+        const float4 q = part[i < n ? i : 0];
+        tx[k] = q.x;
+        tz[k] = q.y;
+        su[k] = cu[k] = sw[k] = cw[k] = 0.f;
+    }
+    for (int j0 = 0; j0 < n; j0 += kTile) {
+        const int je = min(n, j0 + kTile);
+        float au[T], aw[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) au[k] = aw[k] = 0.f;
+#pragma unroll 2
+        for (int j = j0; j < je; ++j) {
+            const float4 s = part[j];
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                const float dx = tx[k] - s.x, dz = tz[k] - s.y;
+                const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+                au[k] = fmaf(-dz, g, au[k]);
+                aw[k] = fmaf(dx, g, aw[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            kahan_add(su[k], cu[k], au[k]);
+            kahan_add(sw[k], cw[k], aw[k]);
+        }
+    }
+    const float inv2pi = (float)kInv2Pi;
+    const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        const int i = i0 + k * kThreads;
+        if (i >= n) continue;
+        // bound vortices: singular kernel (Eq. 4) with double-length displacements
+        float xl, zl;
+        unpack_lo(part[i].w, xl, zl);
+        float bu = 0.f, bw = 0.f;
+        for (int j = 0; j < p.n_b; ++j) {
+            const float dx = (tx[k] - w.bnd_f[4 * j]) + (xl - w.bnd_f[4 * j + 1]);
+            const float dz = (tz[k] - w.bnd_f[4 * j + 2]) + (zl - w.bnd_f[4 * j + 3]);
+            const float r2 = fmaf(dx, dx, dz * dz);
+            const float q = r2 > 0.f ? __fdividef(w.gb_f[j], r2) : 0.f;
+            bu = fmaf(-dz, q, bu);
+            bw = fmaf(dx, q, bw);
+        }
+        const float u = fmaf((su[k] - cu[k]) + bu, inv2pi, uix);
+        const float v = fmaf((sw[k] - cw[k]) + bw, inv2pi, uiz);
+        vel[i] = make_float2(u, v);
+        if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
+    }
+}
 
 template <int KER>
 __device__ void convect_f32(const DevParams &p, const Work &w, const float4 *part, float2 *vel,
                             int n, double *probe_vel)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
-    const float inv2pi = (float)kInv2Pi;
-    const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
-    for (int base = warp * 64; base < n; base += kThreads * 2) {
-        const int ia = base + lane, ib = base + 32 + lane;
-        const float4 pa = part[ia < n ? ia : 0], pb = part[ib < n ? ib : 0];
-        const float xa = pa.x, za = pa.y, xb = pb.x, zb = pb.y;
-        float sua = 0.f, cua = 0.f, swa = 0.f, cwa = 0.f;
-        float sub = 0.f, cub = 0.f, swb = 0.f, cwb = 0.f;
-        for (int j0 = 0; j0 < n; j0 += kTile) {
-            const int je = min(n, j0 + kTile);
-            float ua = 0.f, wa = 0.f, ub = 0.f, wb = 0.f;
-#pragma unroll 4
-            for (int j = j0; j < je; ++j) {
-                const float4 s = part[j];
-                const float dxa = xa - s.x, dza = za - s.y;
-                const float dxb = xb - s.x, dzb = zb - s.y;
-                const float ga = s.z * PairF32<KER>::q(fmaf(dxa, dxa, dza * dza), rc4, irc2);
-                const float gb = s.z * PairF32<KER>::q(fmaf(dxb, dxb, dzb * dzb), rc4, irc2);
-                ua = fmaf(-dza, ga, ua);
-                wa = fmaf(dxa, ga, wa);
-                ub = fmaf(-dzb, gb, ub);
-                wb = fmaf(dxb, gb, wb);
-            }
-            kahan_add(sua, cua, ua);
-            kahan_add(swa, cwa, wa);
-            kahan_add(sub, cub, ub);
-            kahan_add(swb, cwb, wb);
-        }
-        // bound vortices: singular kernel (Eq. 4) with double-length displacements
-        float xla, zla, xlb, zlb;
-        unpack_lo(pa.w, xla, zla);
-        unpack_lo(pb.w, xlb, zlb);
-        float bua = 0.f, bwa = 0.f, bub = 0.f, bwb = 0.f;
-        for (int j = 0; j < p.n_b; ++j) {
-            const float bxh = w.bnd_f[4 * j], bxl = w.bnd_f[4 * j + 1];
-            const float bzh = w.bnd_f[4 * j + 2], bzl = w.bnd_f[4 * j + 3];
-            const float g = w.gb_f[j];
-            float dx = (xa - bxh) + (xla - bxl), dz = (za - bzh) + (zla - bzl);
-            float r2 = fmaf(dx, dx, dz * dz);
-            float q = r2 > 0.f ? g / r2 : 0.f;
-            bua = fmaf(-dz, q, bua);
-            bwa = fmaf(dx, q, bwa);
-            dx = (xb - bxh) + (xlb - bxl);
-            dz = (zb - bzh) + (zlb - bzl);
-            r2 = fmaf(dx, dx, dz * dz);
-            q = r2 > 0.f ? g / r2 : 0.f;
-            bub = fmaf(-dz, q, bub);
-            bwb = fmaf(dx, q, bwb);
-        }
-        const float ua = fmaf(((sua - cua) + bua), inv2pi, uix);
-        const float wa = fmaf(((swa - cwa) + bwa), inv2pi, uiz);
-        const float ub = fmaf(((sub - cub) + bub), inv2pi, uix);
-        const float wb = fmaf(((swb - cwb) + bwb), inv2pi, uiz);
-        if (ia < n) {
-            vel[ia] = make_float2(ua, wa);
-            if (probe_vel) { probe_vel[2 * ia] = ua; probe_vel[2 * ia + 1] = wa; }
-        }
-        if (ib < n) {
-            vel[ib] = make_float2(ub, wb);
-            if (probe_vel) { probe_vel[2 * ib] = ub; probe_vel[2 * ib + 1] = wb; }
-        }
+    const int tid = threadIdx.x;
+    const int m = (n + kThreads - 1) / kThreads;   // targets per thread (uniform in the block)
+    int k = 0;
+    for (; k + 4 <= m; k += 4) convect_chunk<KER, 4>(p, w, part, vel, n, tid + k * kThreads, probe_vel);
+    if (m - k >= 2) {
+        convect_chunk<KER, 2>(p, w, part, vel, n, tid + k * kThreads, probe_vel);
+        k += 2;
     }
+    if (m - k == 1) convect_chunk<KER, 1>(p, w, part, vel, n, tid + k * kThreads, probe_vel);
 }
 
 template <int KER>
