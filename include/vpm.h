@@ -216,6 +216,23 @@ vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel, d
 vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, double r_core, double dt,
                               int steps, cudaStream_t stream);
 
+/*
+ * The same Heun steps as vpm_freefield_heun for callers that must not let the library
+ * allocate device memory, such as a control loop whose memory is fixed before it starts or a
+ * host that gives all device memory to another owner. The paper has no counterpart; it is a
+ * deployment variant. Its scratch is one device array of fixed size built into the library
+ * (6 MiB, reserved on every device that loads the library until the process exits), so n is
+ * limited to 262144 particles; larger n returns VPM_ERR_CAPACITY without launching anything.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before capturing the stream into a graph.
+ * Every call on a device uses the same array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller. Nothing in
+ * the array needs clearing between calls: each step writes it fully before reading it.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+vpm_status vpm_freefield_heun_noalloc(float *d_particles, int n, int kernel, double r_core,
+                                      double dt, int steps, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ _SIGNATURES = {
     "mppi_perturb": ([_VP, _VP, _I, _I, _VP, _VP], _I),
     "vpm_freefield_velocity": ([_VP, _I, _I, _D, _VP, _VP], _I),
     "vpm_freefield_heun": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
+    "vpm_freefield_heun_noalloc": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
 }
 
 _lib = None

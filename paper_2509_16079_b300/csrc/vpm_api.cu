@@ -27,6 +27,15 @@ using namespace vpm;
 
 static thread_local std::string g_last_error;
 
+namespace vpm {
+// Records a failure message for vpm_last_error() from other translation units of the library.
+vpm_status report_error(vpm_status st, const char *msg)
+{
+    g_last_error = msg;
+    return st;
+}
+}  // namespace vpm
+
 static vpm_status fail(vpm_status st, const char *fmt, ...)
 {
     char buf[512];
