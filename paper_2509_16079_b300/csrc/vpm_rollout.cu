@@ -16,6 +16,7 @@ namespace vpm {
 
 struct Geo {
     double xw, zw, tx, tz, nx, nz, vx, vz, om;
+    double ct, st;                   // cos and sin of the pitch angle
     int lev, tev;
 };
 
@@ -32,6 +33,7 @@ struct Work {
     Geo geo;
     int n;
     int flag;
+    int chunk_next;                  // next unclaimed target chunk of the pair sums
 };
 
 // ------------------------------------------------------------------ geometry (thread 0)
@@ -39,8 +41,10 @@ struct Work {
 __device__ void plate_geometry(const DevParams &p, Work &w)
 {
     const double *xg = w.xg;
-    double th = xg[2], c = cos(th), s = sin(th);
+    double s, c;
+    sincos(xg[2], &s, &c);
     Geo &G = w.geo;
+    G.ct = c; G.st = s;
     G.xw = xg[0] - p.l_w * c;
     G.zw = xg[1] - p.l_w * s;
     G.tx = -c; G.tz = -s;        // leading edge -> trailing edge
@@ -52,20 +56,28 @@ __device__ void plate_geometry(const DevParams &p, Work &w)
         G.vz = xg[5] - p.l_w * xg[6] * c;
         G.om = xg[6];
     }
-    double alpha = th - atan2(G.vz - p.u_inf_z, G.vx - p.u_inf_x);
-    alpha = atan2(sin(alpha), cos(alpha));
-    int open = fabs(alpha) > p.alpha_crit;
-    G.lev = (p.shed_gate == VPM_GATE_OFF) || open;
-    G.tev = (p.shed_gate != VPM_GATE_BOTH) || open;
-    for (int j = 0; j < p.n_b; ++j) {
-        double sj = -0.5 * p.chord + (j + 0.5) * p.lb;
-        double bx = G.xw + sj * G.tx, bz = G.zw + sj * G.tz;
-        float bxh = (float)bx, bzh = (float)bz;
-        w.bnd_f[4 * j + 0] = bxh;
-        w.bnd_f[4 * j + 1] = (float)(bx - (double)bxh);
-        w.bnd_f[4 * j + 2] = bzh;
-        w.bnd_f[4 * j + 3] = (float)(bz - (double)bzh);
+    if (p.shed_gate == VPM_GATE_OFF) {
+        G.lev = G.tev = 1;
+    } else {
+        double alpha = xg[2] - atan2(G.vz - p.u_inf_z, G.vx - p.u_inf_x);
+        alpha = atan2(sin(alpha), cos(alpha));
+        int open = fabs(alpha) > p.alpha_crit;
+        G.lev = (p.shed_gate == VPM_GATE_OFF) || open;
+        G.tev = (p.shed_gate != VPM_GATE_BOTH) || open;
     }
+}
+
+// Bound vortex j as a double-length binary32 pair (x_hi, x_lo, z_hi, z_lo).
+__device__ __forceinline__ void bound_point_f32(const DevParams &p, Work &w, int j)
+{
+    const Geo &G = w.geo;
+    double sj = -0.5 * p.chord + (j + 0.5) * p.lb;
+    double bx = G.xw + sj * G.tx, bz = G.zw + sj * G.tz;
+    float bxh = (float)bx, bzh = (float)bz;
+    w.bnd_f[4 * j + 0] = bxh;
+    w.bnd_f[4 * j + 1] = (float)(bx - (double)bxh);
+    w.bnd_f[4 * j + 2] = bzh;
+    w.bnd_f[4 * j + 3] = (float)(bz - (double)bzh);
 }
 
 // Target point t of the plate: collocation points 0..n_c-1, then bound points.
@@ -80,17 +92,20 @@ __device__ __forceinline__ void plate_point(const DevParams &p, const Geo &G, in
 
 // ------------------------------------------------------------------ glider (§III-B)
 
-__device__ void glider_rhs(const DevParams &p, const double *xg, double fwx, double fwz,
-                           double mw, double u, double *f)
+__device__ void glider_rhs(const DevParams &p, const double *xg, double ct, double st, double fwx,
+                           double fwz, double mw, double u, double *f)
 {
-    double th = xg[2], ph = xg[3], xd = xg[4], zd = xg[5], thd = xg[6];
-    double ct = cos(th), st = sin(th), cp = cos(th + ph), sp = sin(th + ph);
+    double ph = xg[3], xd = xg[4], zd = xg[5], thd = xg[6];
+    double sp, cp;
+    sincos(xg[2] + ph, &sp, &cp);
     // elevator velocity (Eq. 18) with phidot = u
     double exd = xd + p.l * thd * st + p.l_e * (thd + u) * sp;
     double ezd = zd - p.l * thd * ct - p.l_e * (thd + u) * cp;
-    // flat-plate elevator (Eqs. 19-20): C_n = 2 sin(alpha_e) along n_e = (-sin, cos)(th + ph)
-    double alpha_e = th + ph - atan2(ezd, exd);
-    double fe = 0.5 * p.rho * (exd * exd + ezd * ezd) * p.s_e * 2.0 * sin(alpha_e);
+    // flat-plate elevator (Eqs. 19-20): |F_e| = 1/2 rho |v_e|^2 S_e 2 sin(alpha_e) along
+    // n_e = (-sin, cos)(th + ph); with alpha_e = th + ph - atan2(zd_e, xd_e),
+    // |v_e|^2 sin(alpha_e) = |v_e| (sin(th + ph) xd_e - cos(th + ph) zd_e)
+    double vmag = sqrt(exd * exd + ezd * ezd);
+    double fe = p.rho * p.s_e * vmag * (sp * exd - cp * ezd);
     double fex = -fe * sp, fez = fe * cp;
     // pitch moment about the centre of gravity with world-frame arms of x_w and x_e
     double wx = -p.l_w * ct, wz = -p.l_w * st;
@@ -104,15 +119,17 @@ __device__ void glider_rhs(const DevParams &p, const double *xg, double fwx, dou
 
 // ------------------------------------------------------------------ step phases
 
-// Phase A: wake-induced velocity at the plate points (Eq. 12's sum) and the Kelvin sum.
-// Each warp takes plate points in turn; its lanes split the sources and the partial sums
-// are reduced in binary64.
+// Phase A: wake-induced velocity at the plate points (Eq. 12's sum) and the Kelvin sum, by
+// warps warp0 .. warp0 + nwarps - 1. Each warp takes plate points in turn; its lanes split the
+// sources and the partial sums are reduced in binary64.
 template <class R, int KER>
-__device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>::P *part, int n)
+__device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>::P *part, int n,
+                           int warp0, int nwarps)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - warp0;
+    const int tid = threadIdx.x - 32 * warp0;
     const int M = p.n_c + p.n_b;
-    for (int t = warp; t < M; t += kThreads / 32) {
+    for (int t = warp; t < M; t += nwarps) {
         double tx, tz;
         plate_point(p, w.geo, t, tx, tz);
         double su = 0.0, sw = 0.0;
@@ -153,14 +170,16 @@ __device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>:
     double gsum;
     if constexpr (sizeof(R) == 4) {
         float s = 0.f, c = 0.f;
-        for (int j = tid; j < n; j += kThreads) kahan_add(s, c, part[j].z);
+        for (int j = tid; j < n; j += 32 * nwarps) kahan_add(s, c, part[j].z);
         gsum = (double)s - (double)c;
     } else {
         gsum = 0.0;
-        for (int j = tid; j < n; j += kThreads) gsum += part[j].g;
+        for (int j = tid; j < n; j += 32 * nwarps) gsum += part[j].g;
     }
     for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
     if (lane == 0) w.red[warp] = gsum;
+    if (tid == 0)
+        for (int i = nwarps; i < kThreads / 32; ++i) w.red[i] = 0.0;
 }
 
 // Phase B (thread 0): surface solve, loads, glider update, shedding. Returns the new count.
@@ -220,7 +239,7 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
     // glider explicit Euler update with this step's loads
     if (!p.fixed_plate) {
         double f[7];
-        glider_rhs(p, w.xg, fwx, fwz, mw, u_ctrl, f);
+        glider_rhs(p, w.xg, G.ct, G.st, fwx, fwz, mw, u_ctrl, f);
         for (int c = 0; c < 7; ++c) w.xg[c] += p.dt * f[c];
     }
     for (int j = 0; j < nb; ++j) {
@@ -248,22 +267,32 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
 }
 
 // Phase C: convection velocity of every wake particle (Eq. 16) plus the free stream.
-// Binary32: thread t owns targets t, t + 128, t + 256, ... and processes them T at a time
-// (T = 4, then 2, then 1 for the remainder), so all warps carry the same load. Sources stream
-// from shared memory by broadcast loads, each serving T pairs; plain sums over tiles of kTile
-// sources are added into Kahan-compensated totals.
+//
+// Binary32 path. The sum over pairs of particles that existed before this step's shedding
+// does not depend on the surface solve, so it runs while warp 0 does the plate work; only the
+// bound vortices and the freshly shed vortices need Gamma_S, and their terms are added after.
+// The old-old sum is split into chunks of up to 128 consecutive targets that the warps claim
+// from a shared counter; lane l of a chunk starting at b owns targets b + l + 32 k, k < T.
+// Sources stream from shared memory by broadcast loads, each serving T pairs; plain sums over
+// tiles of kTile sources are added into Kahan-compensated totals. Every target's sum is formed
+// by one lane in a fixed order, so the result does not depend on which warp claimed it.
 constexpr int kTile = 64;
+constexpr int kChunk = 128;
+#ifndef VPM_SRC_UNROLL
+#define VPM_SRC_UNROLL 4      // sources in flight per inner-loop iteration
+#endif
+constexpr int kSrcUnroll = VPM_SRC_UNROLL;
 
 template <int KER, int T>
-__device__ __forceinline__ void convect_chunk(const DevParams &p, const Work &w,
-                                              const float4 *part, float2 *vel, int n, int i0,
-                                              double *probe_vel)
+__device__ __forceinline__ void old_pairs_chunk(const DevParams &p, const float4 *part,
+                                                float2 *vel, int n, int base)
 {
+    const int lane = threadIdx.x & 31;
     const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
     float tx[T], tz[T], su[T], cu[T], sw[T], cw[T];
 #pragma unroll
     for (int k = 0; k < T; ++k) {
-        const int i = i0 + k * kThreads;
+        const int i = base + lane + 32 * k;
         const float4 q = part[i < n ? i : 0];
         tx[k] = q.x;
         tz[k] = q.y;
@@ -274,7 +303,7 @@ __device__ __forceinline__ void convect_chunk(const DevParams &p, const Work &w,
         float au[T], aw[T];
 #pragma unroll
         for (int k = 0; k < T; ++k) au[k] = aw[k] = 0.f;
-#pragma unroll 2
+#pragma unroll kSrcUnroll
         for (int j = j0; j < je; ++j) {
             const float4 s = part[j];
 #pragma unroll
@@ -291,44 +320,100 @@ __device__ __forceinline__ void convect_chunk(const DevParams &p, const Work &w,
             kahan_add(sw[k], cw[k], aw[k]);
         }
     }
-    const float inv2pi = (float)kInv2Pi;
-    const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
 #pragma unroll
     for (int k = 0; k < T; ++k) {
-        const int i = i0 + k * kThreads;
-        if (i >= n) continue;
-        // bound vortices: singular kernel (Eq. 4) with double-length displacements
-        float xl, zl;
-        unpack_lo(part[i].w, xl, zl);
-        float bu = 0.f, bw = 0.f;
-        for (int j = 0; j < p.n_b; ++j) {
-            const float dx = (tx[k] - w.bnd_f[4 * j]) + (xl - w.bnd_f[4 * j + 1]);
-            const float dz = (tz[k] - w.bnd_f[4 * j + 2]) + (zl - w.bnd_f[4 * j + 3]);
-            const float r2 = fmaf(dx, dx, dz * dz);
-            const float q = r2 > 0.f ? __fdividef(w.gb_f[j], r2) : 0.f;
-            bu = fmaf(-dz, q, bu);
-            bw = fmaf(dx, q, bw);
-        }
-        const float u = fmaf((su[k] - cu[k]) + bu, inv2pi, uix);
-        const float v = fmaf((sw[k] - cw[k]) + bw, inv2pi, uiz);
-        vel[i] = make_float2(u, v);
-        if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
+        const int i = base + lane + 32 * k;
+        if (i < n) vel[i] = make_float2(su[k] - cu[k], sw[k] - cw[k]);   // raw, unscaled
     }
 }
 
 template <int KER>
-__device__ void convect_f32(const DevParams &p, const Work &w, const float4 *part, float2 *vel,
-                            int n, double *probe_vel)
+__device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, float2 *vel, int n)
 {
-    const int tid = threadIdx.x;
-    const int m = (n + kThreads - 1) / kThreads;   // targets per thread (uniform in the block)
-    int k = 0;
-    for (; k + 4 <= m; k += 4) convect_chunk<KER, 4>(p, w, part, vel, n, tid + k * kThreads, probe_vel);
-    if (m - k >= 2) {
-        convect_chunk<KER, 2>(p, w, part, vel, n, tid + k * kThreads, probe_vel);
-        k += 2;
+    const int lane = threadIdx.x & 31;
+    const int nchunks = (n + kChunk - 1) / kChunk;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&w.chunk_next, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const int base = c * kChunk, rem = n - base;
+        if (rem > 64)
+            old_pairs_chunk<KER, 4>(p, part, vel, n, base);
+        else if (rem > 32)
+            old_pairs_chunk<KER, 2>(p, part, vel, n, base);
+        else
+            old_pairs_chunk<KER, 1>(p, part, vel, n, base);
     }
-    if (m - k == 1) convect_chunk<KER, 1>(p, w, part, vel, n, tid + k * kThreads, probe_vel);
+}
+
+// Bound vortices (singular kernel, Eq. 4) at a target with double-length displacements.
+__device__ __forceinline__ void bound_terms_f32(const DevParams &p, const Work &w, float x,
+                                                float z, float xl, float zl, float &bu, float &bw)
+{
+    for (int j = 0; j < p.n_b; ++j) {
+        const float dx = (x - w.bnd_f[4 * j]) + (xl - w.bnd_f[4 * j + 1]);
+        const float dz = (z - w.bnd_f[4 * j + 2]) + (zl - w.bnd_f[4 * j + 3]);
+        const float r2 = fmaf(dx, dx, dz * dz);
+        const float q = r2 > 0.f ? __fdividef(w.gb_f[j], r2) : 0.f;
+        bu = fmaf(-dz, q, bu);
+        bw = fmaf(dx, q, bw);
+    }
+}
+
+// Adds the terms that need this step's Gamma_S to the old targets, forms the full sums of the
+// freshly shed particles n .. n1-1, and scales to velocities.
+template <int KER>
+__device__ void finalize_f32(const DevParams &p, const Work &w, const float4 *part, float2 *vel,
+                             int n, int n1, double *probe_vel)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    const float inv2pi = (float)kInv2Pi;
+    const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
+    for (int i = tid; i < n; i += kThreads) {
+        const float4 q = part[i];
+        const float2 raw = vel[i];
+        float xl, zl;
+        unpack_lo(q.w, xl, zl);
+        float bu = 0.f, bw = 0.f;
+        bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
+        for (int j = n; j < n1; ++j) {
+            const float4 s = part[j];
+            const float dx = q.x - s.x, dz = q.y - s.y;
+            const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+            bu = fmaf(-dz, g, bu);
+            bw = fmaf(dx, g, bw);
+        }
+        const float u = fmaf(raw.x + bu, inv2pi, uix), v = fmaf(raw.y + bw, inv2pi, uiz);
+        vel[i] = make_float2(u, v);
+        if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
+    }
+    for (int i = n + warp; i < n1; i += kThreads / 32) {
+        const float4 q = part[i];
+        float su = 0.f, cu = 0.f, sw = 0.f, cw = 0.f;
+        for (int j = lane; j < n1; j += 32) {
+            const float4 s = part[j];
+            const float dx = q.x - s.x, dz = q.y - s.y;
+            const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+            kahan_add(su, cu, -dz * g);
+            kahan_add(sw, cw, dx * g);
+        }
+        double du = (double)su - (double)cu, dw = (double)sw - (double)cw;
+        for (int o = 16; o > 0; o >>= 1) {
+            du += __shfl_xor_sync(0xffffffffu, du, o);
+            dw += __shfl_xor_sync(0xffffffffu, dw, o);
+        }
+        if (lane == 0) {
+            float xl, zl;
+            unpack_lo(q.w, xl, zl);
+            float bu = 0.f, bw = 0.f;
+            bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
+            const float u = fmaf((float)du + bu, inv2pi, uix), v = fmaf((float)dw + bw, inv2pi, uiz);
+            vel[i] = make_float2(u, v);
+            if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
+        }
+    }
 }
 
 template <int KER>
@@ -446,33 +531,53 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
                           typename Store<R>::V *vel, double u_ctrl, const RolloutArgs &a,
                           bool probe)
 {
-    const int tid = threadIdx.x;
-    int n = w.n;
-    if (tid == 0) plate_geometry(p, w);
-    __syncthreads();
-    plate_sums<R, KER>(p, w, part, n);
-    __syncthreads();
-    if (tid == 0) w.n = plate_solve<R>(p, w, part, n, u_ctrl);
-    __syncthreads();
-    n = w.n;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n = w.n;
+    int n1;
+    if constexpr (sizeof(R) == 4) {
+        // warp 0: plate geometry, plate sums, surface solve, loads, glider, shedding;
+        // meanwhile (and afterwards for warp 0) every warp works on the old-old pair sums
+        if (warp == 0) {
+            const int lane = tid & 31;
+            if (lane == 0) plate_geometry(p, w);
+            __syncwarp();
+            if (lane < p.n_b) bound_point_f32(p, w, lane);
+            plate_sums<R, KER>(p, w, part, n, 0, 1);
+            __syncwarp();
+            if (lane == 0) w.n = plate_solve<R>(p, w, part, n, u_ctrl);
+            __syncwarp();
+        }
+        old_pairs_f32<KER>(p, w, part, vel, n);
+        __syncthreads();
+        n1 = w.n;
+        finalize_f32<KER>(p, w, part, vel, n, n1, probe ? a.probe_vel : nullptr);
+    } else {
+        if (tid == 0) plate_geometry(p, w);
+        __syncthreads();
+        plate_sums<R, KER>(p, w, part, n, 0, kThreads / 32);
+        __syncthreads();
+        if (tid == 0) w.n = plate_solve<R>(p, w, part, n, u_ctrl);
+        __syncthreads();
+        n1 = w.n;
+        convect_f64<KER>(p, w, part, vel, n1, probe ? a.probe_vel : nullptr);
+    }
     if (probe) {
         const int M = p.n_c + p.n_b;
         if (a.probe_vt) for (int t = tid; t < 2 * M; t += kThreads) a.probe_vt[t] = w.vt[t];
         if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += kThreads) a.probe_gs[t] = w.gs[t];
         if (a.probe_fm && tid < 3) a.probe_fm[tid] = w.fm[tid];
     }
-    if constexpr (sizeof(R) == 4) {
-        convect_f32<KER>(p, w, part, vel, n, probe ? a.probe_vel : nullptr);
-        __syncthreads();
-        advect_f32(p, w, part, vel, n);
-    } else {
-        convect_f64<KER>(p, w, part, vel, n, probe ? a.probe_vel : nullptr);
-        __syncthreads();
-        advect_f64(p, w, part, vel, n);
-    }
     __syncthreads();
-    n = merge_oldest<R>(p, part, n);
-    if (tid == 0) w.n = n;
+    if constexpr (sizeof(R) == 4)
+        advect_f32(p, w, part, vel, n1);
+    else
+        advect_f64(p, w, part, vel, n1);
+    __syncthreads();
+    const int nm = merge_oldest<R>(p, part, n1);
+    if (tid == 0) {
+        w.n = nm;
+        w.chunk_next = 0;
+    }
     __syncthreads();
 }
 
@@ -487,7 +592,7 @@ __device__ void load_state(const RolloutArgs &a, Work &w, typename Store<R>::P *
     const double *h = a.root_hist + (size_t)rid * a.state_stride;
     if (threadIdx.x < 7) w.xg[threadIdx.x] = g[threadIdx.x];
     if (threadIdx.x < a.p.n_b + 2) w.hist[threadIdx.x] = h[threadIdx.x];
-    if (threadIdx.x == 0) { w.n = n; w.flag = 0; }
+    if (threadIdx.x == 0) { w.n = n; w.flag = 0; w.chunk_next = 0; }
     __syncthreads();
 }
 
@@ -536,8 +641,12 @@ __device__ void finish(const RolloutArgs &a, Work &w, const typename Store<R>::P
 }
 
 // K rollouts (blockIdx.x + rid0 = rollout), H steps each, field resident in shared memory.
+#ifndef VPM_MIN_BLOCKS
+#define VPM_MIN_BLOCKS 7      // 7 blocks of 128 threads per SM: 1024 rollouts of ~1200 particles in one wave
+#endif
+
 template <class R, int KER>
-__global__ void __launch_bounds__(kThreads) rollout_kernel(const RolloutArgs a)
+__global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) rollout_kernel(const RolloutArgs a)
 {
     using P = typename Store<R>::P;
     using V = typename Store<R>::V;
