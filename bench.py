@@ -32,7 +32,7 @@ import workloads as W  # noqa: E402
 
 K_ROLL, H, N0 = 1024, 100, 1000
 LAMBDA = 10.0
-FLOPS_PER_PAIR = 12        # 2 FADD + FMUL + 3 FFMA (r^2, r^4 + r_c^4) ... counted with FMA = 2
+FLOPS_PER_PAIR = 12        # 2 FADD, 2 FMUL, 4 FFMA per pair (FMA = 2 flops), plus one MUFU.RSQ
 PEAK_SM_MHZ = 2032.0
 N_SM = 148
 
