@@ -53,6 +53,23 @@ def fp32_peak_tflops() -> float:
     return N_SM * 128 * 2 * PEAK_SM_MHZ * 1e6 / 1e12
 
 
+def profiled_traffic(summary: str, source: str):
+    """DRAM bytes per full-size launch recorded in profiles/<summary> by an ncu capture, or None
+    when the kernel source has changed since (the summary records the source's hash)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2509_16079_b300", "csrc", source)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source\s+([0-9a-f]{16})", text)
+    if not m:
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return int(m.group(1)) if digest == m.group(2) else None
+
+
 # ------------------------------------------------------------------ clocks during the run
 class ClockSampler:
     def __init__(self, index: int):
@@ -265,13 +282,7 @@ def run_gpu(args):
     roll_avg_s = statistics.mean(roll_ms) / 1e3
     achieved = pairs_iter * FLOPS_PER_PAIR / roll_avg_s / 1e12
     peak = fp32_peak_tflops()
-    prof = os.path.join(ROOT, "profiles", "rollout_kernel_mppi_c2_traffic.json")
-    traffic = None
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = profiled_traffic("rollout_kernel_mppi_c2.md", "vpm_rollout.cu")
     line = {
         "metric": "Biot-Savart pair-interactions/s",
         "value": value,
@@ -331,6 +342,122 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": True, "K": K, "H": Hh, "launches": 4 * (args.warmup + args.steps)}))
 
 
+
+# ------------------------------------------------------------------ extra workloads
+def run_freefield(args):
+    """Large free field: N = 2^20 regularised vortices (64 Gaussian blobs, core 1e-3), 10 Heun
+    steps in binary32 with compensated tile sums; error of the final velocities against the FP64
+    oracle on 4096 sampled targets."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    n, steps, dt, rc = args.n, args.ff_steps, 1e-3, 1e-3
+    P = W.blob_field(0, n)
+    a = np.zeros((n, 4), np.float32)
+    a[:, :3] = P
+    d = torch.tensor(a, device="cuda")
+    V.freefield_heun(d.clone(), V.KERNEL_VATISTAS, rc, dt, 1)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        V.freefield_heun(d, V.KERNEL_VATISTAS, rc, dt, steps)
+        e1.record()
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    pairs = 2.0 * steps * n * n
+    # one velocity evaluation for the error check and the per-launch timing of the kernel alone
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0.record()
+    vel = V.freefield_velocity(d, V.KERNEL_VATISTAS, rc)
+    v1.record()
+    v1.synchronize()
+    kern_ms = v0.elapsed_time(v1)
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.build()
+    Pf = d[:, :3].double().cpu().numpy()
+    idx = W.sample_indices(1, n, 4096)
+    chunks = np.array_split(idx, os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+        parts = list(ex.map(lambda c: oracle.velocity_at(Pf, Pf[c, :2], 1, rc, skip=c), chunks))
+    ref = np.concatenate(parts)
+    got = vel.cpu().numpy()[idx].astype(np.float64)
+    err = np.linalg.norm(got - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max()
+    achieved = n * float(n) * FLOPS_PER_PAIR / (kern_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    print(json.dumps({
+        "metric": "Biot-Savart pair-interactions/s", "value": pairs / (ms / 1e3),
+        "unit": "pair-interactions/s", "n_gpus": 1, "steps": steps, "ms_per_step": ms / steps,
+        "higher_is_better": True, "dtype": "f32 (Kahan-compensated tile sums)", "data": "synthetic",
+        "config": {"workload": "free field N=%d, 64 Gaussian blobs sigma 0.1 in a 10x10 box, "
+                               "Vatistas core 1e-3, Heun dt=1e-3" % n, "pairs_per_step": 2 * n * n},
+        "error_vs_fp64_oracle": {"normwise_velocity": err, "targets": int(len(idx))},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "kernel": "freefield_kernel<Vatistas, velocity>",
+                     "traffic": profiled_traffic("freefield_kernel_2pow20.md", "vpm_freefield.cu"),
+                     "launch_ms": kern_ms},
+        "clocks": clk.summary()}), flush=True)
+
+
+def run_northstar(args):
+    """Replan latency at K = 1024 rollouts x H = 100 steps with ~2000-particle fields (1900 -> 2100),
+    persistent form against the one-rollout-per-launch form. The latter issues K x H single-block
+    launches per iteration on one stream, so its time is linear in K: it is timed on a subset of
+    rollouts and scaled to K = 1024."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    K, Hh, n0 = 1024, 100, args.n0
+    p, field, xg0, _ = W.mppi_c2(0, K=1, H=1, n=n0)
+    root = V.State(p, field, xg0, n0 + 2 * Hh, V.FP32)
+    eps = [torch.tensor(W.mppi_noise(3000 + j, K, Hh, W.MPPI_SIGMA_U), device="cuda") for j in range(3)]
+    mu = torch.zeros(Hh, dtype=torch.float32, device="cuda")
+
+    def replan(mu):
+        for j in range(3):
+            c = V.mppi_perturb(mu, eps[j])
+            out = root.rollout_batch(c, want_final=False)
+            mu = V.mppi_update(V.mppi_weights(out["costs"], LAMBDA), c)
+        return mu
+
+    for _ in range(2):
+        replan(mu)
+    torch.cuda.synchronize()
+    lat = []
+    for r in range(args.replans):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        replan(mu)
+        b.record()
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+    # one-rollout-per-launch form on a subset
+    ks = args.per_launch_subset
+    c = V.mppi_perturb(mu, eps[0])[:ks].contiguous()
+    root.rollout_batch_per_launch(c[:2].contiguous())
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    pl = root.rollout_batch_per_launch(c)
+    b.record()
+    b.synchronize()
+    per_launch_iter_ms = a.elapsed_time(b) * K / ks
+    ref = root.rollout_batch(c, want_final=False)
+    same = bool(torch.equal(ref["costs"], pl["costs"]))
+    pairs_iter = pairs_per_rollout(n0, Hh) * K
+    print(json.dumps({
+        "metric": "MPPI replan latency (3 iterations)", "unit": "ms", "higher_is_better": False,
+        "config": {"workload": "K=1024 x H=100, fields %d -> %d particles" % (n0, n0 + 2 * Hh)},
+        "persistent": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "replans": len(lat), "pairs_per_s": 3 * pairs_iter / (np.median(lat) / 1e3)},
+        "one_rollout_per_launch": {"replan_ms_scaled": 3 * per_launch_iter_ms,
+                                   "timed_rollouts": ks, "launches_per_iteration": K * Hh,
+                                   "bitwise_equal_costs": same},
+        "speedup_p50": 3 * per_launch_iter_ms / float(np.percentile(lat, 50))}), flush=True)
+
 # ------------------------------------------------------------------ reference arm (oracle)
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -382,12 +509,21 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar"])
+    ap.add_argument("--n", type=int, default=1 << 20, help="free-field particle count")
+    ap.add_argument("--ff-steps", type=int, default=10)
+    ap.add_argument("--n0", type=int, default=1900, help="north-star root field size")
+    ap.add_argument("--per-launch-subset", type=int, default=16)
     ap.add_argument("--rollouts", type=int, default=K_ROLL)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.profile_case:
         run_profile_case(args)
+    elif args.workload == "freefield":
+        run_freefield(args)
+    elif args.workload == "northstar":
+        run_northstar(args)
     else:
         run_gpu(args)
 
