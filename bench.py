@@ -458,6 +458,66 @@ def run_northstar(args):
                                    "bitwise_equal_costs": same},
         "speedup_p50": 3 * per_launch_iter_ms / float(np.percentile(lat, 50))}), flush=True)
 
+
+def run_uneven(args):
+    """Uneven batching: 4096 rollouts with particle counts log-uniform in [64, 8192], H = 50,
+    binary32, persistent class launches with autotuned block sizes, the horizon replayed from a
+    CUDA graph; against one launch per rollout (timed on a systematic sample of the rollouts
+    sorted by size and scaled to all of them: the launches are serial on one stream)."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    R, Hh = args.rollouts_uneven, 50
+    counts = W.uneven_counts(0, R, 64, 8192)
+    fields = [W.background_field(10_000 + i, int(n)) for i, n in enumerate(counts)]
+    gliders = np.tile(np.array(W.GLIDER_X0), (R, 1))
+    p = W.glider_params()
+    controls = torch.tensor(W.mppi_noise(11, R, Hh, W.MPPI_SIGMA_U), device="cuda")
+    b = V.Batch(p, fields, gliders, Hh)
+    b.tune(controls)
+    out = b.rollout(controls, use_graph=True)
+    torch.cuda.synchronize()
+    b.status()
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.rollout(controls, use_graph=True, out=out)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    pairs = sum(pairs_per_rollout(int(n), Hh) for n in counts)
+    ms = float(np.median(times))
+    # one launch per rollout, systematic sample
+    order = np.argsort(counts)
+    sample = order[len(order) // (2 * args.sample) :: max(1, len(order) // args.sample)][: args.sample]
+    single_ms = []
+    for i in sample:
+        st = V.State(p, fields[i], gliders[i], int(counts[i]) + 2 * Hh, V.FP32)
+        c = controls[i:i + 1].contiguous()
+        st.rollout_batch(c, want_final=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st.rollout_batch(c, want_final=False)
+        e1.record()
+        e1.synchronize()
+        single_ms.append(e0.elapsed_time(e1))
+        st.close()
+    per_launch_ms = float(np.sum(single_ms)) * R / len(sample)
+    print(json.dumps({
+        "metric": "Biot-Savart pair-interactions/s", "value": pairs / (ms / 1e3),
+        "unit": "pair-interactions/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uneven batch: %d rollouts, counts log-uniform in [64, 8192], H=50" % R,
+                   "pairs_per_step": pairs, "max_count": int(counts.max()),
+                   "schedule": b.schedule(), "graph": True},
+        "one_launch_per_rollout": {"ms_scaled": per_launch_ms, "sampled_rollouts": int(len(sample)),
+                                   "pairs_per_s": pairs / (per_launch_ms / 1e3)},
+        "speedup": per_launch_ms / ms, "clocks": clk.summary()}), flush=True)
+
 # ------------------------------------------------------------------ reference arm (oracle)
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -509,7 +569,9 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven"])
+    ap.add_argument("--rollouts-uneven", type=int, default=4096)
+    ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
     ap.add_argument("--n", type=int, default=1 << 20, help="free-field particle count")
     ap.add_argument("--ff-steps", type=int, default=10)
     ap.add_argument("--n0", type=int, default=1900, help="north-star root field size")
@@ -524,6 +586,8 @@ def main():
         run_freefield(args)
     elif args.workload == "northstar":
         run_northstar(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_gpu(args)
 

@@ -216,6 +216,56 @@ vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel, d
 vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, double r_core, double dt,
                               int steps, cudaStream_t stream);
 
+/* ------------------------------------------------------------------ uneven batches
+ * Rollouts from many different roots at once: the MPPI step of §IV-A applied to R scenarios
+ * whose fields have different particle counts (one rollout per root). Roots are grouped by
+ * the shared memory their fields can need into classes; each class runs as one persistent
+ * launch (blocks claim rollouts largest-first) on its own stream, forked from and joined back
+ * into the caller's stream. A rollout's result does not depend on the class, the block size or
+ * the order of execution.
+ */
+typedef struct vpm_batch vpm_batch;
+
+/*
+ * Creates a batch of R roots: h_counts[R] particle counts, h_particles the concatenated fields
+ * (sum of counts x 3, binary64 x, z, Gamma in root order), h_gliders[R x 7] glider states.
+ * max_horizon bounds the H of later rollouts (capacities are counts + 2 max_horizon).
+ * Synchronises `stream`. Errors: VPM_ERR_INVALID, VPM_ERR_NONFINITE, VPM_ERR_CAPACITY (a field
+ * would not fit one block's shared memory: about 9300 particles on the binary32 path, 4500 on
+ * the binary64 path), VPM_ERR_OOM, VPM_ERR_CUDA.
+ */
+vpm_status vpm_batch_create(const vpm_params *params, int R, const int *h_counts,
+                            const double *h_particles, const double *h_gliders, int max_horizon,
+                            vpm_batch **out, cudaStream_t stream);
+
+vpm_status vpm_batch_destroy(vpm_batch *batch);
+
+/*
+ * One rollout of H steps per root under d_controls[R x H]; d_costs[R] receives the terminal
+ * costs (Eq. 24), d_count[R] (or null) the final particle counts, d_final_glider[R x 7] (or
+ * null) the final glider states. With use_graph = 1 the class launches of this (H, buffers)
+ * combination are captured once into a CUDA graph on a library stream and replayed on
+ * `stream` afterwards; changing H or a buffer recaptures.
+ */
+vpm_status vpm_batch_rollout(vpm_batch *batch, int H, const float *d_controls, float *d_costs,
+                             int *d_count, double *d_final_glider, int use_graph,
+                             cudaStream_t stream);
+
+/*
+ * Autotuner: times each class alone over min(H, 3) steps with 128, 256 and 512 threads per
+ * block (where they fit) and keeps the fastest per class. It changes speed only, never
+ * results. Synchronises `stream`.
+ */
+vpm_status vpm_batch_tune(vpm_batch *batch, int H, const float *d_controls, cudaStream_t stream);
+
+/* The schedule: number of non-empty classes and, per class, its capacity, threads per block,
+ * number of rollouts and tuned time (ms, 0 before tuning). Arrays hold up to 5 entries. */
+vpm_status vpm_batch_schedule(const vpm_batch *batch, int *h_nclasses, int *h_cap, int *h_nt,
+                              int *h_items, float *h_tuned_ms);
+
+/* Reads and clears the batch's device error word (synchronises `stream`). */
+vpm_status vpm_batch_status(vpm_batch *batch, cudaStream_t stream);
+
 /*
  * The same Heun steps as vpm_freefield_heun for callers that must not let the library
  * allocate device memory, such as a control loop whose memory is fixed before it starts or a

@@ -83,6 +83,12 @@ _SIGNATURES = {
     "vpm_freefield_velocity": ([_VP, _I, _I, _D, _VP, _VP], _I),
     "vpm_freefield_heun": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
     "vpm_freefield_heun_noalloc": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
+    "vpm_batch_create": ([C.POINTER(Params), _I, _VP, _VP, _VP, _I, C.POINTER(_VP), _VP], _I),
+    "vpm_batch_destroy": ([_VP], _I),
+    "vpm_batch_rollout": ([_VP, _I, _VP, _VP, _VP, _VP, _I, _VP], _I),
+    "vpm_batch_tune": ([_VP, _I, _VP, _VP], _I),
+    "vpm_batch_schedule": ([_VP, C.POINTER(_I), _VP, _VP, _VP, _VP], _I),
+    "vpm_batch_status": ([_VP, _VP], _I),
 }
 
 _lib = None
@@ -235,6 +241,67 @@ class State:
         check(lib().vpm_rollout_batch_per_launch(self._h, K, H, ptr(controls), ptr(costs),
                                                  ptr(fin), stream_handle(stream)))
         return dict(costs=costs, final_glider=fin)
+
+
+class Batch:
+    """Rollouts from R roots with uneven particle counts (one rollout per root)."""
+
+    def __init__(self, params: dict, fields, gliders, max_horizon: int, precision: int = FP32,
+                 stream=None):
+        self.params = dict(params)
+        self._P = make_params(params, precision)
+        counts = np.ascontiguousarray([len(f) for f in fields], dtype=np.int32)
+        parts = np.ascontiguousarray(np.concatenate([np.asarray(f, np.float64).reshape(-1, 3) for f in fields])
+                                     if len(fields) else np.zeros((0, 3)))
+        xg = np.ascontiguousarray(np.asarray(gliders, dtype=np.float64).reshape(-1, 7))
+        self.R = len(counts)
+        self.counts = counts
+        h = C.c_void_p()
+        check(lib().vpm_batch_create(C.byref(self._P), self.R, counts.ctypes.data_as(_VP),
+                                     parts.ctypes.data_as(_VP), xg.ctypes.data_as(_VP),
+                                     int(max_horizon), C.byref(h), stream_handle(stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vpm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rollout(self, controls, use_graph: bool = False, out=None, stream=None):
+        import torch
+        controls = _dev_tensor(controls, torch.float32)
+        R, H = controls.shape
+        dev = controls.device
+        o = out or dict(costs=torch.empty(R, dtype=torch.float32, device=dev),
+                        count=torch.empty(R, dtype=torch.int32, device=dev),
+                        final_glider=torch.empty((R, 7), dtype=torch.float64, device=dev))
+        check(lib().vpm_batch_rollout(self._h, H, ptr(controls), ptr(o["costs"]), ptr(o["count"]),
+                                      ptr(o["final_glider"]), int(use_graph), stream_handle(stream)))
+        return o
+
+    def tune(self, controls, stream=None):
+        import torch
+        controls = _dev_tensor(controls, torch.float32)
+        check(lib().vpm_batch_tune(self._h, controls.shape[1], ptr(controls), stream_handle(stream)))
+
+    def schedule(self):
+        n = C.c_int()
+        cap, nt, items = (np.zeros(5, np.int32) for _ in range(3))
+        ms = np.zeros(5, np.float32)
+        check(lib().vpm_batch_schedule(self._h, C.byref(n), cap.ctypes.data_as(_VP), nt.ctypes.data_as(_VP),
+                                       items.ctypes.data_as(_VP), ms.ctypes.data_as(_VP)))
+        k = n.value
+        return [dict(cap=int(cap[i]), threads=int(nt[i]), rollouts=int(items[i]), tuned_ms=float(ms[i]))
+                for i in range(k)]
+
+    def status(self, stream=None):
+        check(lib().vpm_batch_status(self._h, stream_handle(stream)))
 
 
 def mppi_weights(costs, lam: float, out=None, stream=None):

@@ -276,6 +276,14 @@ static void unpack_records(int precision, const void *in, int n, double *h)
     }
 }
 
+// Entry points for the batch code in vpm_batch.cu.
+namespace vpm {
+vpm_status check_params_ext(const vpm_params *p) { return check_params(p); }
+vpm_status surface_inverses_ext(const vpm_params *p, double *kinv) { return surface_inverses(p, kinv); }
+void fill_dev_params_ext(const vpm_params *p, DevParams &d) { fill_dev_params(p, d); }
+void pack_records_ext(int precision, const double *h, int n, void *out) { pack_records(precision, h, n, out); }
+}  // namespace vpm
+
 // ------------------------------------------------------------------ state
 
 static size_t max_smem_optin()

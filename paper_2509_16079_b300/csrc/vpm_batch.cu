@@ -1,0 +1,386 @@
+// Batches of rollouts from many different roots (uneven particle counts) in persistent
+// launches: host-side grouping into shared-memory classes, longest-first ordering, the
+// block-size autotuner, and capture of a whole horizon into a CUDA graph.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "vpm_rollout.cuh"
+
+namespace vpm {
+vpm_status report_error(vpm_status st, const char *msg);
+}
+
+using namespace vpm;
+
+static vpm_status bfail(vpm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return report_error(st, buf);
+}
+
+static vpm_status bcuda(cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    return bfail(VPM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BTRY(call, what)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return bcuda(e_, what);     \
+    } while (0)
+
+// Shared-memory classes: a rollout whose field can reach `cap` particles goes to the first
+// class with cap <= limit. The limits are where the number of resident 128-thread blocks per
+// SM changes (24 bytes per particle on the binary32 path): 7, 4, 3, 2, 1.
+static const int kClassLimit[] = {1300, 2300, 3000, 4500, 9300};
+static const int kNumClasses = 5;
+static const int kStateStride = kMaxB + 2;
+
+struct BatchClass {
+    int cap = 0;                 // largest capacity in the class (shared-memory size)
+    int nt = 128;                // threads per block (autotuned)
+    int grid = 0;                // persistent blocks for nt (resident blocks per SM x SMs)
+    float tuned_ms = 0.f;
+    std::vector<int> items;      // rollout indices, largest first
+    int *d_order = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+struct vpm_batch {
+    vpm_params params;
+    DevParams dp;
+    int R = 0, max_h = 0, device = 0, sms = 0;
+    size_t rec_bytes = 0;
+    std::vector<int> counts;
+    void *d_part = nullptr;
+    long long *d_offset = nullptr;
+    int *d_n = nullptr;
+    double *d_glider = nullptr, *d_hist = nullptr, *d_kinv = nullptr;
+    int *d_counters = nullptr, *d_status = nullptr;
+    BatchClass cls[kNumClasses];
+    cudaEvent_t fork = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int g_h = -1;
+    const void *g_ctrl = nullptr, *g_costs = nullptr, *g_count = nullptr, *g_final = nullptr;
+};
+
+// Defined in vpm_api.cu (parameter checks, body-frame surface inverses, record packing).
+namespace vpm {
+vpm_status check_params_ext(const vpm_params *p);
+vpm_status surface_inverses_ext(const vpm_params *p, double *kinv);
+void fill_dev_params_ext(const vpm_params *p, DevParams &d);
+void pack_records_ext(int precision, const double *h, int n, void *out);
+}
+
+static void batch_free(vpm_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto &c : b->cls) {
+        cudaFree(c.d_order);
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    cudaFree(b->d_part); cudaFree(b->d_offset); cudaFree(b->d_n); cudaFree(b->d_glider);
+    cudaFree(b->d_hist); cudaFree(b->d_kinv); cudaFree(b->d_counters); cudaFree(b->d_status);
+    cudaGetLastError();
+    delete b;
+}
+
+extern "C" vpm_status vpm_batch_create(const vpm_params *params, int R, const int *h_counts,
+                                       const double *h_particles, const double *h_gliders,
+                                       int max_horizon, vpm_batch **out, cudaStream_t stream)
+{
+    vpm_status st = check_params_ext(params);
+    if (st) return st;
+    if (!out || !h_counts || !h_gliders || R < 1 || max_horizon < 1)
+        return bfail(VPM_ERR_INVALID, "vpm_batch_create: need R >= 1, max_horizon >= 1 and non-null arrays");
+    long long total = 0;
+    for (int i = 0; i < R; ++i) {
+        if (h_counts[i] < 0) return bfail(VPM_ERR_INVALID, "vpm_batch_create: negative count");
+        total += h_counts[i];
+    }
+    if (total > 0 && !h_particles) return bfail(VPM_ERR_INVALID, "vpm_batch_create: null particles");
+    for (long long i = 0; i < 3 * total; ++i)
+        if (!isfinite(h_particles[i])) return bfail(VPM_ERR_NONFINITE, "vpm_batch_create: non-finite particle");
+    for (int i = 0; i < 7 * R; ++i)
+        if (!isfinite(h_gliders[i])) return bfail(VPM_ERR_NONFINITE, "vpm_batch_create: non-finite glider");
+    int dev = 0, count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return bfail(VPM_ERR_CUDA, "no CUDA device available");
+    }
+    BTRY(cudaGetDevice(&dev), "cudaGetDevice");
+    vpm_batch *b = new vpm_batch();
+    b->params = *params;
+    b->R = R;
+    b->max_h = max_horizon;
+    b->device = dev;
+    b->counts.assign(h_counts, h_counts + R);
+    BTRY(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    b->rec_bytes = params->precision == VPM_FP64 ? sizeof(Part64) : sizeof(float4);
+    fill_dev_params_ext(params, b->dp);
+    // classes by capacity, longest first within a class
+    for (int i = 0; i < R; ++i) {
+        long long cap = (long long)h_counts[i] + 2LL * max_horizon;
+        if (params->n_wake_max > 0)
+            cap = std::min<long long>(cap, std::max<long long>(params->n_wake_max, h_counts[i]) + 2);
+        int c = 0;
+        while (c < kNumClasses && cap > kClassLimit[c]) ++c;
+        if (c == kNumClasses || (params->precision == VPM_FP64 && cap > 4500)) {
+            batch_free(b);
+            return bfail(VPM_ERR_CAPACITY, "rollout %d may reach %lld particles, beyond one block's shared memory", i, cap);
+        }
+        b->cls[c].items.push_back(i);
+        b->cls[c].cap = std::max(b->cls[c].cap, (int)std::max<long long>(cap, 1));
+    }
+    for (auto &c : b->cls)
+        std::stable_sort(c.items.begin(), c.items.end(),
+                         [&](int x, int y) { return h_counts[x] > h_counts[y]; });
+    // device copies
+    std::vector<long long> off(R);
+    long long acc = 0;
+    for (int i = 0; i < R; ++i) { off[i] = acc; acc += h_counts[i]; }
+    std::vector<char> rec(b->rec_bytes * (size_t)std::max<long long>(total, 1));
+    pack_records_ext(params->precision, h_particles, (int)total, rec.data());
+    std::vector<double> gl((size_t)kStateStride * R, 0.0), hist((size_t)kStateStride * R, 0.0);
+    for (int i = 0; i < R; ++i)
+        for (int k = 0; k < 7; ++k) gl[(size_t)kStateStride * i + k] = h_gliders[7 * i + k];
+    std::vector<double> kinv(4 * kMaxS * kMaxS);
+    if ((st = surface_inverses_ext(params, kinv.data()))) { batch_free(b); return st; }
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&b->d_part, rec.size())) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_offset, sizeof(long long) * R)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_n, sizeof(int) * R)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_glider, sizeof(double) * gl.size())) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_hist, sizeof(double) * hist.size())) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_kinv, sizeof(double) * kinv.size())) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_counters, sizeof(int) * kNumClasses)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_status, sizeof(int))) != cudaSuccess) {
+        batch_free(b);
+        cudaGetLastError();
+        return bfail(VPM_ERR_OOM, "vpm_batch_create: %s", cudaGetErrorString(e));
+    }
+    b->dp.kinv = b->d_kinv;
+    e = cudaMemcpyAsync(b->d_part, rec.data(), rec.size(), cudaMemcpyHostToDevice, stream);
+    if (!e) e = cudaMemcpyAsync(b->d_offset, off.data(), sizeof(long long) * R, cudaMemcpyHostToDevice, stream);
+    if (!e) e = cudaMemcpyAsync(b->d_n, h_counts, sizeof(int) * R, cudaMemcpyHostToDevice, stream);
+    if (!e) e = cudaMemcpyAsync(b->d_glider, gl.data(), sizeof(double) * gl.size(), cudaMemcpyHostToDevice, stream);
+    if (!e) e = cudaMemcpyAsync(b->d_hist, hist.data(), sizeof(double) * hist.size(), cudaMemcpyHostToDevice, stream);
+    if (!e) e = cudaMemcpyAsync(b->d_kinv, kinv.data(), sizeof(double) * kinv.size(), cudaMemcpyHostToDevice, stream);
+    if (!e) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), stream);
+    for (auto &c : b->cls) {
+        if (c.items.empty() || e) continue;
+        if (!e) e = cudaMalloc((void **)&c.d_order, sizeof(int) * c.items.size());
+        if (!e) e = cudaMemcpyAsync(c.d_order, c.items.data(), sizeof(int) * c.items.size(), cudaMemcpyHostToDevice, stream);
+        if (!e) e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming);
+        // default block size before tuning: more threads where fewer blocks fit per SM
+        c.nt = c.cap <= kClassLimit[0] ? 128 : (c.cap <= kClassLimit[2] ? 256 : 512);
+        if (params->precision == VPM_FP64) c.nt = 128;
+    }
+    if (!e) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (!e) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamSynchronize(stream);
+    if (e) { batch_free(b); return bcuda(e, "vpm_batch_create"); }
+    *out = b;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_batch_destroy(vpm_batch *b)
+{
+    batch_free(b);
+    return VPM_OK;
+}
+
+static void batch_args(const vpm_batch *b, int H, const float *ctrl, float *costs, int *count,
+                       double *final_glider, RolloutArgs &a)
+{
+    memset(&a, 0, sizeof a);
+    a.p = b->dp;
+    a.root_part = b->d_part;
+    a.root_n = b->d_n;
+    a.root_glider = b->d_glider;
+    a.root_hist = b->d_hist;
+    a.root_offset = b->d_offset;
+    a.state_stride = kStateStride;
+    a.H = H;
+    a.K = b->R;
+    a.controls = ctrl;
+    a.ctrl_stride = H;
+    a.costs = costs;
+    a.count = count;
+    a.final_glider = final_glider;
+    a.status = b->d_status;
+}
+
+// Persistent grid of class c for nt threads per block; also sets the kernel's shared-memory
+// limit, so it runs before any capture.
+static cudaError_t prepare_class(vpm_batch *b, int c, int nt)
+{
+    BatchClass &k = b->cls[c];
+    const size_t smem = rollout_smem_bytes(b->params.precision, k.cap);
+    const int per_sm = uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, smem);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    k.grid = std::min<int>((int)k.items.size(), per_sm * b->sms);
+    return cudaSuccess;
+}
+
+// Enqueues the class launches on the class streams, forked from and joined back into s. The
+// classes must have been prepared for the block sizes used.
+static cudaError_t enqueue_classes(vpm_batch *b, int H, const float *ctrl, float *costs,
+                                   int *count, double *final_glider, cudaStream_t s,
+                                   int only_class = -1, int nt_override = 0)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * kNumClasses, s);
+    if (!e) e = cudaEventRecord(b->fork, s);
+    for (int c = 0; c < kNumClasses && !e; ++c) {
+        BatchClass &k = b->cls[c];
+        if (k.items.empty() || (only_class >= 0 && c != only_class)) continue;
+        const int nt = nt_override ? nt_override : k.nt;
+        const int grid = k.grid;
+        RolloutArgs a;
+        batch_args(b, H, ctrl, costs, count, final_glider, a);
+        a.cap = k.cap;
+        a.order = k.d_order;
+        a.counter = b->d_counters + c;
+        a.n_items = (int)k.items.size();
+        e = cudaStreamWaitEvent(k.stream, b->fork, 0);
+        if (!e) e = launch_uneven(b->params.precision, a, grid, nt, k.stream);
+        if (!e) e = cudaEventRecord(k.done, k.stream);
+        if (!e) e = cudaStreamWaitEvent(s, k.done, 0);
+    }
+    return e;
+}
+
+extern "C" vpm_status vpm_batch_rollout(vpm_batch *b, int H, const float *d_controls,
+                                        float *d_costs, int *d_count, double *d_final_glider,
+                                        int use_graph, cudaStream_t stream)
+{
+    if (!b || !d_controls || !d_costs) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: null argument");
+    if (H < 1 || H > b->max_h) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: need 1 <= H <= %d", b->max_h);
+    for (int c = 0; c < kNumClasses; ++c)
+        if (!b->cls[c].items.empty()) BTRY(prepare_class(b, c, b->cls[c].nt), "prepare class");
+    if (!use_graph) {
+        cudaError_t e = enqueue_classes(b, H, d_controls, d_costs, d_count, d_final_glider, stream);
+        if (e) return bcuda(e, "vpm_batch_rollout");
+        return VPM_OK;
+    }
+    if (!b->graph || b->g_h != H || b->g_ctrl != d_controls || b->g_costs != d_costs ||
+        b->g_count != d_count || b->g_final != d_final_glider) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        BTRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = enqueue_classes(b, H, d_controls, d_costs, d_count, d_final_glider, b->capture_stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
+        if (e || e2) {
+            if (g) cudaGraphDestroy(g);
+            return bcuda(e ? e : e2, "graph capture");
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e) { b->graph = nullptr; return bcuda(e, "graph instantiate"); }
+        b->g_h = H; b->g_ctrl = d_controls; b->g_costs = d_costs; b->g_count = d_count;
+        b->g_final = d_final_glider;
+    }
+    BTRY(cudaGraphLaunch(b->graph, stream), "graph launch");
+    return VPM_OK;
+}
+
+// Autotuner: for every class, times one launch of the class alone for each block size that
+// fits (128, 256, 512 threads) over min(H, 3) steps and keeps the fastest. Results of a rollout
+// do not depend on the block size, so tuning changes speed only. Synchronises `stream`.
+extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_controls,
+                                     cudaStream_t stream)
+{
+    if (!b || !d_controls) return bfail(VPM_ERR_INVALID, "vpm_batch_tune: null argument");
+    if (H < 1 || H > b->max_h) return bfail(VPM_ERR_INVALID, "vpm_batch_tune: bad H");
+    if (b->params.precision == VPM_FP64) return VPM_OK;
+    const int Ht = std::min(H, 3);
+    float *costs = nullptr;
+    BTRY(cudaMallocAsync((void **)&costs, sizeof(float) * b->R, stream), "tune scratch");
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    vpm_status st = VPM_OK;
+    for (int c = 0; c < kNumClasses && st == VPM_OK; ++c) {
+        BatchClass &k = b->cls[c];
+        if (k.items.empty()) continue;
+        const size_t smem = rollout_smem_bytes(b->params.precision, k.cap);
+        float best = INFINITY;
+        int best_nt = k.nt;
+        for (int nt : {128, 256, 512}) {
+            if (uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, smem) < 1) continue;
+            cudaError_t e = prepare_class(b, c, nt);
+            if (!e) e = enqueue_classes(b, Ht, d_controls, costs, nullptr, nullptr, stream, c, nt);
+            if (!e) e = cudaEventRecord(t0, stream);
+            if (!e) e = enqueue_classes(b, Ht, d_controls, costs, nullptr, nullptr, stream, c, nt);
+            if (!e) e = cudaEventRecord(t1, stream);
+            if (!e) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (!e) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e) { st = bcuda(e, "vpm_batch_tune"); break; }
+            if (ms < best) { best = ms; best_nt = nt; }
+        }
+        k.nt = best_nt;
+        k.tuned_ms = best;
+        if (st == VPM_OK) {
+            cudaError_t e = prepare_class(b, c, best_nt);
+            if (e) st = bcuda(e, "vpm_batch_tune");
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFreeAsync(costs, stream);
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (st == VPM_OK && e) st = bcuda(e, "vpm_batch_tune sync");
+    return st;
+}
+
+extern "C" vpm_status vpm_batch_schedule(const vpm_batch *b, int *h_nclasses, int *h_cap,
+                                         int *h_nt, int *h_items, float *h_tuned_ms)
+{
+    if (!b || !h_nclasses) return bfail(VPM_ERR_INVALID, "vpm_batch_schedule: null argument");
+    int m = 0;
+    for (const auto &k : b->cls) {
+        if (k.items.empty()) continue;
+        if (h_cap) h_cap[m] = k.cap;
+        if (h_nt) h_nt[m] = k.nt;
+        if (h_items) h_items[m] = (int)k.items.size();
+        if (h_tuned_ms) h_tuned_ms[m] = k.tuned_ms;
+        ++m;
+    }
+    *h_nclasses = m;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_batch_status(vpm_batch *b, cudaStream_t stream)
+{
+    if (!b) return bfail(VPM_ERR_INVALID, "null batch");
+    int st = 0;
+    BTRY(cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, stream), "status");
+    BTRY(cudaStreamSynchronize(stream), "status sync");
+    if (st) {
+        BTRY(cudaMemsetAsync(b->d_status, 0, sizeof(int), stream), "status clear");
+        return bfail(VPM_ERR_NONFINITE, "non-finite value in a batched rollout");
+    }
+    return VPM_OK;
+}

@@ -13,7 +13,8 @@ namespace vpm {
 constexpr int kMaxB = 32;                 // largest N_b accepted by the library
 constexpr int kMaxC = kMaxB + 1;          // collocation points
 constexpr int kMaxS = kMaxB + 2;          // surface unknowns (bound + LEV + TEV)
-constexpr int kThreads = 128;             // threads of one rollout block
+constexpr int kThreads = 128;             // threads of a rollout block on the default path
+constexpr int kMaxWarps = 16;             // largest rollout block: 512 threads
 constexpr double kInv2Pi = 0.15915494309189533577;
 
 enum Status : int { kStOk = 0, kStNonFinite = 1, kStCapacity = 2 };

@@ -27,7 +27,7 @@ struct Work {
     double vt[2 * (2 * kMaxB + 1)];  // relative velocity at collocation then bound points
     double gs[kMaxS];                // Gamma_b, Gamma_LEV, Gamma_TEV of this step
     double fm[3];
-    double red[kThreads / 32];
+    double red[kMaxWarps];
     float bnd_f[4 * kMaxB];          // bound positions as (x_hi, x_lo, z_hi, z_lo)
     float gb_f[kMaxB];               // bound circulations (binary32 copy)
     Geo geo;
@@ -179,7 +179,7 @@ __device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>:
     for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
     if (lane == 0) w.red[warp] = gsum;
     if (tid == 0)
-        for (int i = nwarps; i < kThreads / 32; ++i) w.red[i] = 0.0;
+        for (int i = nwarps; i < kMaxWarps; ++i) w.red[i] = 0.0;
 }
 
 // Phase B (thread 0): surface solve, loads, glider update, shedding. Returns the new count.
@@ -198,7 +198,7 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
         w.vt[2 * t + 1] += p.u_inf_z - G.vz - G.om * rx;
     }
     double gw = 0.0;
-    for (int i = 0; i < kThreads / 32; ++i) gw += w.red[i];
+    for (int i = 0; i < kMaxWarps; ++i) gw += w.red[i];
     // right-hand side of Eq. 10 for the active rows, Gamma_S = K^-1 b (Eq. 11)
     const int lev = G.lev, tev = G.tev, m = nb + lev + tev;
     double b[kMaxS];
@@ -371,7 +371,7 @@ __device__ void finalize_f32(const DevParams &p, const Work &w, const float4 *pa
     const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
     const float inv2pi = (float)kInv2Pi;
     const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
-    for (int i = tid; i < n; i += kThreads) {
+    for (int i = tid; i < n; i += (int)blockDim.x) {
         const float4 q = part[i];
         const float2 raw = vel[i];
         float xl, zl;
@@ -389,7 +389,7 @@ __device__ void finalize_f32(const DevParams &p, const Work &w, const float4 *pa
         vel[i] = make_float2(u, v);
         if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
     }
-    for (int i = n + warp; i < n1; i += kThreads / 32) {
+    for (int i = n + warp; i < n1; i += (int)(blockDim.x >> 5)) {
         const float4 q = part[i];
         float su = 0.f, cu = 0.f, sw = 0.f, cw = 0.f;
         for (int j = lane; j < n1; j += 32) {
@@ -421,7 +421,7 @@ __device__ void convect_f64(const DevParams &p, const Work &w, const Part64 *par
                             int n, double *probe_vel)
 {
     const Geo &G = w.geo;
-    for (int i = threadIdx.x; i < n; i += kThreads) {
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) {
         const Part64 pi = part[i];
         double su = 0.0, sw = 0.0;
         for (int j = 0; j < n; ++j) {
@@ -452,7 +452,7 @@ __device__ void advect_f32(const DevParams &p, Work &w, float4 *part, const floa
     const float dth = (float)p.dt, dtl = (float)(p.dt - (double)dth);
     const float dch = (float)p.decay, dcl = (float)(p.decay - (double)dch);
     bool bad = false;
-    for (int i = threadIdx.x; i < n; i += kThreads) {
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) {
         float4 q = part[i];
         const float2 v = vel[i];
         bad |= !(isfinite(v.x) && isfinite(v.y));
@@ -475,7 +475,7 @@ __device__ void advect_f32(const DevParams &p, Work &w, float4 *part, const floa
 __device__ void advect_f64(const DevParams &p, Work &w, Part64 *part, const double2 *vel, int n)
 {
     bool bad = false;
-    for (int i = threadIdx.x; i < n; i += kThreads) {
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) {
         Part64 q = part[i];
         const double2 v = vel[i];
         bad |= !(isfinite(v.x) && isfinite(v.y));
@@ -512,7 +512,7 @@ __device__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int 
     }
     __syncthreads();
     const int nn = n - m;
-    for (int base = 1; base < nn; base += kThreads) {
+    for (int base = 1; base < nn; base += (int)blockDim.x) {
         const int i = base + threadIdx.x;
         P tmp;
         if (i < nn) tmp = part[i + m];
@@ -554,7 +554,7 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
     } else {
         if (tid == 0) plate_geometry(p, w);
         __syncthreads();
-        plate_sums<R, KER>(p, w, part, n, 0, kThreads / 32);
+        plate_sums<R, KER>(p, w, part, n, 0, (int)(blockDim.x >> 5));
         __syncthreads();
         if (tid == 0) w.n = plate_solve<R>(p, w, part, n, u_ctrl);
         __syncthreads();
@@ -563,8 +563,8 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
     }
     if (probe) {
         const int M = p.n_c + p.n_b;
-        if (a.probe_vt) for (int t = tid; t < 2 * M; t += kThreads) a.probe_vt[t] = w.vt[t];
-        if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += kThreads) a.probe_gs[t] = w.gs[t];
+        if (a.probe_vt) for (int t = tid; t < 2 * M; t += (int)blockDim.x) a.probe_vt[t] = w.vt[t];
+        if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += (int)blockDim.x) a.probe_gs[t] = w.gs[t];
         if (a.probe_fm && tid < 3) a.probe_fm[tid] = w.fm[tid];
     }
     __syncthreads();
@@ -585,9 +585,10 @@ template <class R>
 __device__ void load_state(const RolloutArgs &a, Work &w, typename Store<R>::P *part, int rid)
 {
     using P = typename Store<R>::P;
-    const P *rp = static_cast<const P *>(a.root_part) + (size_t)rid * a.root_stride;
-    const int n = a.root_n[a.root_stride ? rid : 0];
-    for (int i = threadIdx.x; i < n; i += kThreads) part[i] = rp[i];
+    const long long off = a.root_offset ? a.root_offset[rid] : (long long)rid * a.root_stride;
+    const P *rp = static_cast<const P *>(a.root_part) + off;
+    const int n = a.root_n[(a.root_stride || a.root_offset) ? rid : 0];
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) part[i] = rp[i];
     const double *g = a.root_glider + (size_t)rid * a.state_stride;
     const double *h = a.root_hist + (size_t)rid * a.state_stride;
     if (threadIdx.x < 7) w.xg[threadIdx.x] = g[threadIdx.x];
@@ -603,7 +604,7 @@ __device__ void store_state(const RolloutArgs &a, Work &w, const typename Store<
     using P = typename Store<R>::P;
     P *op = static_cast<P *>(a.out_part) + (size_t)rid * a.out_stride;
     const int n = w.n;
-    for (int i = threadIdx.x; i < n; i += kThreads) op[i] = part[i];
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) op[i] = part[i];
     double *g = a.out_glider + (size_t)rid * a.out_state_stride;
     double *h = a.out_hist + (size_t)rid * a.out_state_stride;
     if (threadIdx.x < 7) g[threadIdx.x] = w.xg[threadIdx.x];
@@ -630,7 +631,7 @@ __device__ void finish(const RolloutArgs &a, Work &w, const typename Store<R>::P
     if (a.final_glider && threadIdx.x < 7) a.final_glider[rid * 7 + threadIdx.x] = w.xg[threadIdx.x];
     if (a.field) {
         double *f = a.field + (size_t)rid * a.field_cap * 3;
-        for (int i = threadIdx.x; i < n; i += kThreads) {
+        for (int i = threadIdx.x; i < n; i += (int)blockDim.x) {
             double x, z;
             Store<R>::xz(part[i], x, z);
             f[3 * i] = x;
@@ -640,21 +641,11 @@ __device__ void finish(const RolloutArgs &a, Work &w, const typename Store<R>::P
     }
 }
 
-// K rollouts (blockIdx.x + rid0 = rollout), H steps each, field resident in shared memory.
-#ifndef VPM_MIN_BLOCKS
-#define VPM_MIN_BLOCKS 7      // 7 blocks of 128 threads per SM: 1024 rollouts of ~1200 particles in one wave
-#endif
-
+// One rollout of a.H steps by the whole block, field resident in shared memory.
 template <class R, int KER>
-__global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) rollout_kernel(const RolloutArgs a)
+__device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P *part,
+                            typename Store<R>::V *vel, int rid)
 {
-    using P = typename Store<R>::P;
-    using V = typename Store<R>::V;
-    extern __shared__ __align__(16) unsigned char smem[];
-    P *part = reinterpret_cast<P *>(smem);
-    V *vel = reinterpret_cast<V *>(smem + sizeof(P) * (size_t)a.cap);
-    __shared__ Work w;
-    const int rid = blockIdx.x + a.rid0;
     load_state<R>(a, w, part, rid);
     for (int k = 0; k < a.H; ++k) {
         const double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k]
@@ -665,6 +656,52 @@ __global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) rollout_kernel(const
     }
     if (a.out_part) store_state<R>(a, w, part, rid);
     finish<R>(a, w, part, rid);
+}
+
+#ifndef VPM_MIN_BLOCKS
+#define VPM_MIN_BLOCKS 7      // 7 blocks of 128 threads per SM: 1024 rollouts of ~1200 particles in one wave
+#endif
+
+// Register budget per block size: 128 threads keep 7 blocks per SM; larger blocks serve large
+// fields, whose shared memory allows 1-3 blocks per SM anyway.
+__host__ __device__ constexpr int min_blocks_for(int nt)
+{
+    return nt <= 128 ? VPM_MIN_BLOCKS : (nt <= 256 ? 3 : 1);
+}
+
+// K rollouts (blockIdx.x + rid0 = rollout), H steps each.
+template <class R, int KER>
+__global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) rollout_kernel(const RolloutArgs a)
+{
+    using P = typename Store<R>::P;
+    using V = typename Store<R>::V;
+    extern __shared__ __align__(16) unsigned char smem[];
+    P *part = reinterpret_cast<P *>(smem);
+    V *vel = reinterpret_cast<V *>(smem + sizeof(P) * (size_t)a.cap);
+    __shared__ Work w;
+    run_rollout<R, KER>(a, w, part, vel, blockIdx.x + a.rid0);
+}
+
+// Persistent form for batches of uneven rollouts: each block claims the next rollout of
+// a.order until all a.n_items are done. Which block runs a rollout does not change its result.
+template <class R, int KER, int NT>
+__global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const RolloutArgs a)
+{
+    using P = typename Store<R>::P;
+    using V = typename Store<R>::V;
+    extern __shared__ __align__(16) unsigned char smem[];
+    P *part = reinterpret_cast<P *>(smem);
+    V *vel = reinterpret_cast<V *>(smem + sizeof(P) * (size_t)a.cap);
+    __shared__ Work w;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int q = s_item;
+        __syncthreads();
+        if (q >= a.n_items) break;
+        run_rollout<R, KER>(a, w, part, vel, a.order[q]);
+    }
 }
 
 // ------------------------------------------------------------------ host-side launch helpers
@@ -704,6 +741,85 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
     if (ker == VPM_KERNEL_GAUSSIAN) return launch_t<float, VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
     if (ker == VPM_KERNEL_SINGULAR) return launch_t<float, VPM_KERNEL_SINGULAR>(a, grid, smem, s);
     return launch_t<float, VPM_KERNEL_VATISTAS>(a, grid, smem, s);
+}
+
+template <class R, int KER, int NT>
+static cudaError_t launch_u(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    auto k = uneven_kernel<R, KER, NT>;
+    static size_t granted = 48 * 1024;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (smem > granted && cs == cudaStreamCaptureStatusNone) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        granted = smem;
+    }
+    k<<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class R, int KER>
+static cudaError_t launch_u_nt(const RolloutArgs &a, int grid, int nt, size_t smem, cudaStream_t s)
+{
+    if (nt == 512) return launch_u<R, KER, 512>(a, grid, smem, s);
+    if (nt == 256) return launch_u<R, KER, 256>(a, grid, smem, s);
+    return launch_u<R, KER, 128>(a, grid, smem, s);
+}
+
+cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, cudaStream_t s)
+{
+    const size_t smem = rollout_smem_bytes(precision, a.cap);
+    const int ker = a.p.kernel;
+    if (precision == VPM_FP64) {
+        if (ker == VPM_KERNEL_GAUSSIAN) return launch_u<double, VPM_KERNEL_GAUSSIAN, 128>(a, grid, smem, s);
+        if (ker == VPM_KERNEL_SINGULAR) return launch_u<double, VPM_KERNEL_SINGULAR, 128>(a, grid, smem, s);
+        return launch_u<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
+    }
+    if (ker == VPM_KERNEL_GAUSSIAN) return launch_u_nt<float, VPM_KERNEL_GAUSSIAN>(a, grid, nt, smem, s);
+    if (ker == VPM_KERNEL_SINGULAR) return launch_u_nt<float, VPM_KERNEL_SINGULAR>(a, grid, nt, smem, s);
+    return launch_u_nt<float, VPM_KERNEL_VATISTAS>(a, grid, nt, smem, s);
+}
+
+// Sets the kernel's dynamic shared-memory limit to at least smem and returns the resident
+// blocks per SM.
+template <class F>
+static int occupancy_of(F k, int nt, size_t smem)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nt, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem)
+{
+    if (precision == VPM_FP64) {
+        if (kernel == VPM_KERNEL_GAUSSIAN) return occupancy_of(uneven_kernel<double, VPM_KERNEL_GAUSSIAN, 128>, 128, smem);
+        if (kernel == VPM_KERNEL_SINGULAR) return occupancy_of(uneven_kernel<double, VPM_KERNEL_SINGULAR, 128>, 128, smem);
+        return occupancy_of(uneven_kernel<double, VPM_KERNEL_VATISTAS, 128>, 128, smem);
+    }
+#define VPM_OCC(KER)                                                                         \
+    if (nt == 512) return occupancy_of(uneven_kernel<float, KER, 512>, 512, smem);           \
+    if (nt == 256) return occupancy_of(uneven_kernel<float, KER, 256>, 256, smem);           \
+    return occupancy_of(uneven_kernel<float, KER, 128>, 128, smem);
+    if (kernel == VPM_KERNEL_GAUSSIAN) { VPM_OCC(VPM_KERNEL_GAUSSIAN) }
+    if (kernel == VPM_KERNEL_SINGULAR) { VPM_OCC(VPM_KERNEL_SINGULAR) }
+    VPM_OCC(VPM_KERNEL_VATISTAS)
+#undef VPM_OCC
 }
 
 }  // namespace vpm

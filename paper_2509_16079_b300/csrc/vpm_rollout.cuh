@@ -31,9 +31,20 @@ struct RolloutArgs {
     // single-step probes
     double *probe_fm, *probe_gs, *probe_vel, *probe_vt;
     int *status;
+    // persistent uneven batches: per-rollout record offsets into root_part (overrides
+    // root_stride), the order in which rollouts are claimed, and the claim counter
+    const long long *root_offset;
+    const int *order;
+    int *counter;
+    int n_items;
 };
 
 size_t rollout_smem_bytes(int precision, int cap);
 cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s);
+// Persistent launch over a.n_items rollouts with `nt` threads per block (128, 256 or 512; the
+// binary64 path uses 128); `grid` blocks claim rollouts in a.order through a.counter.
+cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, cudaStream_t s);
+// Resident blocks per SM of the persistent kernel for this configuration (0 if it cannot run).
+int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem);
 
 }  // namespace vpm

@@ -1,0 +1,100 @@
+"""Uneven batches (many roots with different particle counts in persistent class launches)
+against single-root rollouts and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _roots(counts, seed=0):
+    fields = [W.background_field(seed * 1000 + i, int(n)) for i, n in enumerate(counts)]
+    rng = np.random.default_rng(seed)
+    gliders = np.tile(np.array(W.GLIDER_X0), (len(counts), 1))
+    gliders[:, 4] += rng.uniform(-0.5, 0.5, len(counts))
+    return fields, gliders
+
+
+def _singles(V, torch, p, fields, gliders, controls, precision):
+    H = controls.shape[1]
+    res = []
+    for i, f in enumerate(fields):
+        st = V.State(p, f, gliders[i], len(f) + 2 * H, precision)
+        out = st.rollout_batch(controls[i:i + 1].contiguous(), want_field=True)
+        res.append((out["costs"][0].item(), int(out["count"][0]), out["final_glider"][0].cpu().numpy()))
+        st.close()
+    return res
+
+
+@pytest.mark.parametrize("counts", [
+    list(W.uneven_counts(3, 24, 64, 1500)),
+    [60, 900, 1500, 2200, 2600, 4000, 7000, 0, 130, 3100],
+])
+def test_batch_matches_single_rollouts(counts):
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 6
+    fields, gliders = _roots(counts)
+    controls = torch.tensor(W.mppi_noise(5, len(counts), H, W.MPPI_SIGMA_U), device="cuda")
+    b = V.Batch(p, fields, gliders, H)
+    out = b.rollout(controls)
+    torch.cuda.synchronize()
+    b.status()
+    ref = _singles(V, torch, p, fields, gliders, controls, V.FP32)
+    for i, (c, n, xg) in enumerate(ref):
+        assert out["costs"][i].item() == c, i
+        assert int(out["count"][i]) == n == counts[i] + 2 * H
+        assert np.array_equal(out["final_glider"][i].cpu().numpy(), xg), i
+    if max(counts) > 2300:
+        assert len(b.schedule()) >= 3
+
+
+def test_graph_replay_and_tuning_do_not_change_results():
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 5
+    counts = list(W.uneven_counts(4, 40, 64, 3000))
+    fields, gliders = _roots(counts, 1)
+    controls = torch.tensor(W.mppi_noise(6, len(counts), H, W.MPPI_SIGMA_U), device="cuda")
+    b = V.Batch(p, fields, gliders, H)
+    base = {k: v.clone() for k, v in b.rollout(controls).items()}
+    outs = [dict(costs=torch.empty_like(base["costs"]), count=torch.empty_like(base["count"]),
+                 final_glider=torch.empty_like(base["final_glider"]))]
+    for _ in range(2):                  # capture, then replay into the same buffers
+        b.rollout(controls, use_graph=True, out=outs[0])
+        torch.cuda.synchronize()
+        for k in base:
+            assert torch.equal(outs[0][k], base[k])
+    b.tune(controls)
+    sched = b.schedule()
+    assert all(s["threads"] in (128, 256, 512) and s["tuned_ms"] > 0 for s in sched)
+    tuned = b.rollout(controls)
+    torch.cuda.synchronize()
+    for k in base:
+        assert torch.equal(tuned[k], base[k])
+
+
+def test_batch_fp64_against_oracle(ora):
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 20
+    counts = [0, 50, 300, 700, 64]
+    fields, gliders = _roots(counts, 2)
+    eps = W.mppi_noise(7, len(counts), H, W.MPPI_SIGMA_U)
+    b = V.Batch(p, fields, gliders, H, precision=V.FP64)
+    out = b.rollout(torch.tensor(eps, device="cuda"))
+    torch.cuda.synchronize()
+    for i in range(len(counts)):
+        ref = ora.rollout(p, fields[i], gliders[i], eps[i].astype(np.float64))
+        assert np.abs(out["final_glider"][i].cpu().numpy() - ref["xg"]).max() <= 1e-6
+        assert abs(out["costs"][i].item() - ref["cost"]) <= 1e-6 * abs(ref["cost"]) + 1e-5
+
+
+def test_batch_rejects_fields_beyond_shared_memory():
+    torch, V = cuda()
+    fields, gliders = _roots([100, 9400])
+    with pytest.raises(V.VpmError) as e:
+        V.Batch(W.glider_params(), fields, gliders, 10)
+    assert e.value.status == V.VPM_ERR_CAPACITY
