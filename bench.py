@@ -518,6 +518,58 @@ def run_uneven(args):
                                    "pairs_per_s": pairs / (per_launch_ms / 1e3)},
         "speedup": per_launch_ms / ms, "clocks": clk.summary()}), flush=True)
 
+
+def run_serving(args):
+    """Serving: 16 scenarios with resident fields of 500-5000 particles (merging caps growth
+    at n + 300), replanning requests arriving as Poisson streams at 50 Hz each, K drawn from
+    {256, 1024, 4096}, H = 100, each request first advancing its scenario by 2 steps. The
+    arrival trace is replayed in real time against the continuous-batching server (16 slots)
+    and then against the plain per-request form (1 slot). The offered load is far above one
+    GPU's capacity, so a newer request for a scenario supersedes its queued one."""
+    import threading as th
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    Hh, T = 100, args.serve_seconds
+    fields = W.serving_scenarios(0)
+    arrivals, streams = W.poisson_arrivals(1, 50.0, T, len(fields))
+    sizes = W.request_sizes(2, len(arrivals))
+    noise = {k: [W.mppi_noise(100 + 7 * j + k, k, Hh, W.MPPI_SIGMA_U) for j in range(3)]
+             for k in (256, 1024, 4096)}
+    out = {"metric": "MPPI replan latency under load", "unit": "ms", "higher_is_better": False,
+           "config": {"workload": "serving: 16 scenarios, 500-5000 particles, Poisson 50 Hz each, "
+                                  "K in {256, 1024, 4096}, H=100", "seconds": T,
+                      "offered_requests": int(len(arrivals))}}
+    for label, slots in (("continuous", 16), ("per_request", 1)):
+        srv = V.Server(max_inflight=slots, max_rollouts=4096, max_horizon=Hh)
+        for f in fields:
+            p = W.glider_params(n_wake_max=len(f) + 300)
+            srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 300 + 2 * Hh + 8)
+        tickets = []
+        t0 = time.perf_counter()
+        for j, (ta, sc) in enumerate(zip(arrivals, streams)):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            k = int(sizes[j])
+            tickets.append(srv.submit(int(sc), noise[k][j % 3], advance_steps=2, advance_u=0.0))
+        lat, done_k, superseded = [], 0, 0
+        for t in tickets:
+            r = srv.poll(t)
+            if r[0]["status"] == V.VPM_OK:
+                lat.append(r[0]["t_done_ms"] - r[0]["t_submit_ms"])
+                done_k += r[0]["K"]
+            else:
+                superseded += 1
+        wall = time.perf_counter() - t0
+        srv.close()
+        out[label] = {"completed": len(lat), "superseded": superseded,
+                      "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+                      "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+                      "rollouts_per_s": done_k / wall, "wall_s": wall}
+    print(json.dumps(out), flush=True)
+
 # ------------------------------------------------------------------ reference arm (oracle)
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -569,7 +621,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
     ap.add_argument("--n", type=int, default=1 << 20, help="free-field particle count")
@@ -588,6 +641,8 @@ def main():
         run_northstar(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

@@ -266,6 +266,68 @@ vpm_status vpm_batch_schedule(const vpm_batch *batch, int *h_nclasses, int *h_ca
 /* Reads and clears the batch's device error word (synchronises `stream`). */
 vpm_status vpm_batch_status(vpm_batch *batch, cudaStream_t stream);
 
+/* ------------------------------------------------------------------ replanning server
+ * Serves replanning requests (§IV-C: re-running the MPPI iteration of §IV-A from each
+ * scenario's current vortex state) from many scenarios at once. Each scenario's field stays
+ * resident on the device between requests. A worker thread admits queued requests in arrival
+ * order whenever a slot is free, the scenario has nothing on the device, and the request's
+ * device buffers fit the memory budget; admitted requests run on their own streams and overlap
+ * on the GPU. A newer request for a scenario supersedes its older request still in the queue
+ * (that one completes with VPM_ERR_BUSY). Results do not depend on what else runs.
+ */
+typedef struct vpm_server vpm_server;
+
+typedef struct {
+    int max_inflight;     /* requests on the device at once; 1 gives the plain per-request form */
+    size_t hbm_budget;    /* device bytes of request buffers in flight; 0: 80 % of free memory   */
+    int max_rollouts;     /* largest K accepted                                                 */
+    int max_horizon;      /* largest H accepted                                                 */
+} vpm_server_config;
+
+typedef struct {
+    int status;           /* VPM_OK, VPM_ERR_BUSY (superseded), or the error that stopped it     */
+    int scenario, K, H;
+    double t_submit_ms, t_start_ms, t_done_ms;   /* host clock, ms since the server was created   */
+    float j_min;          /* smallest rollout cost of the iteration                              */
+} vpm_server_result;
+
+vpm_status vpm_server_create(const vpm_server_config *cfg, vpm_server **out);
+
+/* Adds a scenario with a resident field (as vpm_state_create, default stream); *scenario
+ * receives its index. */
+vpm_status vpm_server_add_scenario(vpm_server *server, const vpm_params *params,
+                                   const double *h_particles, int n, int capacity,
+                                   const double *h_glider7, int *scenario);
+
+/*
+ * Queues one MPPI iteration on a scenario: controls h_mu[H] (null: zeros) plus noise
+ * h_eps[K x H] (both copied before return), temperature lambda; before the rollouts the
+ * scenario's field is advanced by advance_steps committed steps at elevator rate advance_u.
+ * *ticket identifies the request. Errors: VPM_ERR_INVALID, VPM_ERR_CAPACITY (the request can
+ * never fit the memory budget).
+ */
+vpm_status vpm_server_submit(vpm_server *server, int scenario, int K, int H, const float *h_mu,
+                             const float *h_eps, float lambda, int advance_steps,
+                             float advance_u, long long *ticket);
+
+/* Waits up to timeout_ms (-1: forever, 0: no wait) for a request; on completion fills *out and
+ * h_mu_out[H] (the reweighted controls, if non-null) and forgets the ticket. Returns
+ * VPM_ERR_BUSY (not done, no wait) or VPM_ERR_TIMEOUT when it is not done yet. */
+vpm_status vpm_server_poll(vpm_server *server, long long ticket, int timeout_ms,
+                           vpm_server_result *out, float *h_mu_out);
+
+/* Rollouts completed so far, requests queued, requests and bytes on the device. */
+vpm_status vpm_server_stats(vpm_server *server, long long *completed_rollouts, int *queued,
+                            int *in_flight, size_t *in_flight_bytes);
+
+/* Copies a scenario's resident field and glider state to the host once it is idle
+ * (h_particles must hold its capacity x 3 values). */
+vpm_status vpm_server_read_scenario(vpm_server *server, int scenario, double *h_particles,
+                                    int *n_out, double *h_glider7);
+
+/* Stops the worker, waits for the device, frees everything. */
+vpm_status vpm_server_destroy(vpm_server *server);
+
 /*
  * The same Heun steps as vpm_freefield_heun for callers that must not let the library
  * allocate device memory, such as a control loop whose memory is fixed before it starts or a

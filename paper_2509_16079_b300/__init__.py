@@ -89,6 +89,14 @@ _SIGNATURES = {
     "vpm_batch_tune": ([_VP, _I, _VP, _VP], _I),
     "vpm_batch_schedule": ([_VP, C.POINTER(_I), _VP, _VP, _VP, _VP], _I),
     "vpm_batch_status": ([_VP, _VP], _I),
+    "vpm_server_create": ([_VP, C.POINTER(_VP)], _I),
+    "vpm_server_add_scenario": ([_VP, C.POINTER(Params), _VP, _I, _I, _VP, C.POINTER(_I)], _I),
+    "vpm_server_submit": ([_VP, _I, _I, _I, _VP, _VP, _F, _I, _F, C.POINTER(C.c_longlong)], _I),
+    "vpm_server_poll": ([_VP, C.c_longlong, _I, _VP, _VP], _I),
+    "vpm_server_stats": ([_VP, C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_I),
+                          C.POINTER(C.c_size_t)], _I),
+    "vpm_server_read_scenario": ([_VP, _I, _VP, C.POINTER(_I), _VP], _I),
+    "vpm_server_destroy": ([_VP], _I),
 }
 
 _lib = None
@@ -241,6 +249,87 @@ class State:
         check(lib().vpm_rollout_batch_per_launch(self._h, K, H, ptr(controls), ptr(costs),
                                                  ptr(fin), stream_handle(stream)))
         return dict(costs=costs, final_glider=fin)
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_inflight", C.c_int), ("hbm_budget", C.c_size_t), ("max_rollouts", C.c_int),
+                ("max_horizon", C.c_int)]
+
+
+class ServerResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("scenario", C.c_int), ("K", C.c_int), ("H", C.c_int),
+                ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double),
+                ("j_min", C.c_float)]
+
+
+class Server:
+    """Replanning server with resident scenario fields (see vpm_server_* in include/vpm.h)."""
+
+    def __init__(self, max_inflight: int = 8, max_rollouts: int = 4096, max_horizon: int = 100,
+                 hbm_budget: int = 0):
+        cfg = ServerConfig(int(max_inflight), int(hbm_budget), int(max_rollouts), int(max_horizon))
+        h = C.c_void_p()
+        check(lib().vpm_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self.max_horizon = max_horizon
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vpm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_scenario(self, params: dict, particles, glider7, capacity: int, precision: int = FP32) -> int:
+        P = make_params(params, precision)
+        parts = np.ascontiguousarray(np.asarray(particles, dtype=np.float64).reshape(-1, 3))
+        xg = np.ascontiguousarray(np.asarray(glider7, dtype=np.float64))
+        sid = C.c_int()
+        check(lib().vpm_server_add_scenario(self._h, C.byref(P), parts.ctypes.data_as(_VP), len(parts),
+                                            int(capacity), xg.ctypes.data_as(_VP), C.byref(sid)))
+        return sid.value
+
+    def submit(self, scenario: int, eps, mu=None, lam: float = 10.0, advance_steps: int = 0,
+               advance_u: float = 0.0) -> int:
+        eps = np.ascontiguousarray(eps, dtype=np.float32)
+        K, H = eps.shape
+        m = None if mu is None else np.ascontiguousarray(mu, dtype=np.float32)
+        t = C.c_longlong()
+        check(lib().vpm_server_submit(self._h, int(scenario), K, H,
+                                      None if m is None else m.ctypes.data_as(_VP),
+                                      eps.ctypes.data_as(_VP), float(lam), int(advance_steps),
+                                      float(advance_u), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """Returns (result dict, mu) or None when not done within the timeout."""
+        r = ServerResult()
+        mu = np.zeros(self.max_horizon, np.float32)
+        st = lib().vpm_server_poll(self._h, C.c_longlong(ticket), int(timeout_ms), C.byref(r),
+                                   mu.ctypes.data_as(_VP))
+        if st in (VPM_ERR_BUSY, VPM_ERR_TIMEOUT):
+            return None
+        check(st)
+        res = {k: getattr(r, k) for k, _ in ServerResult._fields_}
+        return res, mu[:r.H].copy()
+
+    def stats(self):
+        done, q, f, b = C.c_longlong(), C.c_int(), C.c_int(), C.c_size_t()
+        check(lib().vpm_server_stats(self._h, C.byref(done), C.byref(q), C.byref(f), C.byref(b)))
+        return dict(completed_rollouts=done.value, queued=q.value, in_flight=f.value,
+                    in_flight_bytes=b.value)
+
+    def read_scenario(self, scenario: int, capacity: int):
+        parts = np.zeros((capacity, 3))
+        xg = np.zeros(7)
+        n = C.c_int()
+        check(lib().vpm_server_read_scenario(self._h, int(scenario), parts.ctypes.data_as(_VP),
+                                             C.byref(n), xg.ctypes.data_as(_VP)))
+        return parts[:n.value].copy(), xg
 
 
 class Batch:

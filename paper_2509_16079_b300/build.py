@@ -20,7 +20,7 @@ NVCC_FLAGS = [
     # binary32 denormals flush to zero: the pair kernels never produce them in a meaningful
     # way (r^4 + r_core^4 >= r_core^4), and without the flush rsqrtf needs a fix-up sequence
     "-ftz=true",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-shared",
     "-cudart", "static",
     "-I", os.path.join(ROOT, "include"),
 ]

@@ -670,8 +670,8 @@ __host__ __device__ constexpr int min_blocks_for(int nt)
 }
 
 // K rollouts (blockIdx.x + rid0 = rollout), H steps each.
-template <class R, int KER>
-__global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) rollout_kernel(const RolloutArgs a)
+template <class R, int KER, int NT>
+__global__ void __launch_bounds__(NT, min_blocks_for(NT)) rollout_kernel(const RolloutArgs a)
 {
     using P = typename Store<R>::P;
     using V = typename Store<R>::V;
@@ -706,10 +706,10 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const Ro
 
 // ------------------------------------------------------------------ host-side launch helpers
 
-template <class R, int KER>
+template <class R, int KER, int NT>
 static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    auto k = rollout_kernel<R, KER>;
+    auto k = rollout_kernel<R, KER, NT>;
     // raise the kernel's dynamic shared-memory limit once per size increase (per process;
     // the library runs on one device per process)
     static size_t granted = 48 * 1024;
@@ -719,8 +719,18 @@ static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStr
         if (e != cudaSuccess) return e;
         granted = smem;
     }
-    k<<<grid, kThreads, smem, s>>>(a);
+    k<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Binary32 block size by field capacity: more warps where shared memory admits fewer blocks
+// per SM (results do not depend on it).
+template <int KER>
+static cudaError_t launch_f32(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    if (a.cap > 3000) return launch_t<float, KER, 512>(a, grid, smem, s);
+    if (a.cap > 1300) return launch_t<float, KER, 256>(a, grid, smem, s);
+    return launch_t<float, KER, 128>(a, grid, smem, s);
 }
 
 size_t rollout_smem_bytes(int precision, int cap)
@@ -734,13 +744,13 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
     const size_t smem = rollout_smem_bytes(precision, a.cap);
     const int ker = a.p.kernel;
     if (precision == VPM_FP64) {
-        if (ker == VPM_KERNEL_GAUSSIAN) return launch_t<double, VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
-        if (ker == VPM_KERNEL_SINGULAR) return launch_t<double, VPM_KERNEL_SINGULAR>(a, grid, smem, s);
-        return launch_t<double, VPM_KERNEL_VATISTAS>(a, grid, smem, s);
+        if (ker == VPM_KERNEL_GAUSSIAN) return launch_t<double, VPM_KERNEL_GAUSSIAN, 128>(a, grid, smem, s);
+        if (ker == VPM_KERNEL_SINGULAR) return launch_t<double, VPM_KERNEL_SINGULAR, 128>(a, grid, smem, s);
+        return launch_t<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
     }
-    if (ker == VPM_KERNEL_GAUSSIAN) return launch_t<float, VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
-    if (ker == VPM_KERNEL_SINGULAR) return launch_t<float, VPM_KERNEL_SINGULAR>(a, grid, smem, s);
-    return launch_t<float, VPM_KERNEL_VATISTAS>(a, grid, smem, s);
+    if (ker == VPM_KERNEL_GAUSSIAN) return launch_f32<VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
+    if (ker == VPM_KERNEL_SINGULAR) return launch_f32<VPM_KERNEL_SINGULAR>(a, grid, smem, s);
+    return launch_f32<VPM_KERNEL_VATISTAS>(a, grid, smem, s);
 }
 
 template <class R, int KER, int NT>

@@ -1,0 +1,370 @@
+// Replanning server: resident scenario fields, requests admitted by free device memory and
+// slots, overlapping on the device (continuous batching at the granularity of requests).
+//
+// A request asks for one MPPI iteration (§IV-A, Eq. 25) of K rollouts over H steps on one
+// scenario's resident field, optionally after advancing that field by a few committed steps
+// (the tracking instance of §IV-C). A worker thread owns all device work: it completes finished
+// requests, then admits queued ones in arrival order while a slot is free, the scenario has no
+// request on the device, and the request's device buffers fit the memory budget. Each admitted
+// request runs on its own stream, so requests that arrive while others are on the GPU overlap
+// with them. A request for a scenario supersedes that scenario's older request still waiting
+// in the queue. Every request is computed by the same deterministic kernels, so its result is
+// the same alone and in a mix.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/vpm.h"
+
+namespace vpm {
+vpm_status report_error(vpm_status st, const char *msg);
+}
+
+static vpm_status sfail(vpm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return vpm::report_error(st, buf);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    long long ticket = 0;
+    int scenario = 0, K = 0, H = 0, advance_steps = 0;
+    float lambda = 1.f, advance_u = 0.f;
+    std::vector<float> mu, eps;
+    size_t bytes = 0;                 // device bytes the request holds while in flight
+    double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+struct Result {
+    int status = VPM_OK;
+    Request req;
+    float j_min = 0.f;
+    std::vector<float> mu;
+};
+
+struct Slot {
+    bool busy = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    float *pinned = nullptr;          // eps + mu in, mu + costs out
+    size_t pinned_floats = 0;
+    float *d_buf = nullptr;           // eps, controls, costs, weights, mu (stream-ordered)
+    Request req;
+};
+
+}  // namespace
+
+struct vpm_server {
+    vpm_server_config cfg;
+    int device = 0;
+    size_t budget = 0, in_flight_bytes = 0;
+    Clock::time_point t0;
+    std::vector<vpm_state *> scenarios;
+    std::vector<int> scenario_busy;
+    std::vector<Slot> slots;
+    std::deque<Request> queue;
+    std::map<long long, Result> done;
+    long long next_ticket = 1;
+    long long completed_rollouts = 0;
+    std::mutex m;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::thread worker;
+
+    double now_ms() const
+    {
+        return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    }
+};
+
+static size_t request_bytes(int K, int H)
+{
+    // eps, controls (K x H each), costs, weights (K each), mu (H): binary32
+    return sizeof(float) * (2 * (size_t)K * H + 2 * (size_t)K + (size_t)H);
+}
+
+// Enqueues one request on its slot's stream. Called by the worker with the lock held.
+static vpm_status start_request(vpm_server *s, Slot &sl, const Request &r)
+{
+    const int K = r.K, H = r.H;
+    float *pin = sl.pinned;
+    memcpy(pin, r.eps.data(), sizeof(float) * (size_t)K * H);
+    memcpy(pin + (size_t)K * H, r.mu.data(), sizeof(float) * H);
+    cudaError_t e = cudaMallocAsync((void **)&sl.d_buf, r.bytes, sl.stream);
+    if (e) { cudaGetLastError(); return sfail(VPM_ERR_OOM, "server: cudaMallocAsync: %s", cudaGetErrorString(e)); }
+    float *d_eps = sl.d_buf, *d_ctrl = d_eps + (size_t)K * H, *d_costs = d_ctrl + (size_t)K * H;
+    float *d_w = d_costs + K, *d_mu = d_w + K;
+    e = cudaMemcpyAsync(d_eps, pin, sizeof(float) * (size_t)K * H, cudaMemcpyHostToDevice, sl.stream);
+    if (!e) e = cudaMemcpyAsync(d_mu, pin + (size_t)K * H, sizeof(float) * H, cudaMemcpyHostToDevice, sl.stream);
+    if (e) { cudaGetLastError(); return sfail(VPM_ERR_CUDA, "server: upload: %s", cudaGetErrorString(e)); }
+    vpm_state *st = s->scenarios[r.scenario];
+    vpm_status v = VPM_OK;
+    for (int k = 0; k < r.advance_steps && v == VPM_OK; ++k)
+        v = vpm_step(st, (double)r.advance_u, nullptr, nullptr, nullptr, nullptr, sl.stream);
+    if (v == VPM_OK) v = mppi_perturb(d_mu, d_eps, K, H, d_ctrl, sl.stream);
+    if (v == VPM_OK) v = vpm_rollout_batch(st, K, H, d_ctrl, d_costs, nullptr, nullptr, nullptr, nullptr, sl.stream);
+    if (v == VPM_OK) v = mppi_weights(d_costs, K, r.lambda, d_w, sl.stream);
+    if (v == VPM_OK) v = mppi_update(d_w, d_ctrl, K, H, d_mu, sl.stream);
+    if (v != VPM_OK) return v;
+    e = cudaMemcpyAsync(pin, d_mu, sizeof(float) * H, cudaMemcpyDeviceToHost, sl.stream);
+    if (!e) e = cudaMemcpyAsync(pin + H, d_costs, sizeof(float) * K, cudaMemcpyDeviceToHost, sl.stream);
+    if (!e) e = cudaFreeAsync(sl.d_buf, sl.stream);
+    if (!e) e = cudaEventRecord(sl.done, sl.stream);
+    if (e) { cudaGetLastError(); return sfail(VPM_ERR_CUDA, "server: enqueue: %s", cudaGetErrorString(e)); }
+    return VPM_OK;
+}
+
+static void finish(vpm_server *s, const Request &r, int status, const float *mu, float jmin)
+{
+    Result res;
+    res.status = status;
+    res.req = r;
+    res.req.eps.clear();
+    res.req.eps.shrink_to_fit();
+    res.req.t_done = s->now_ms();
+    res.j_min = jmin;
+    if (mu) res.mu.assign(mu, mu + r.H);
+    s->done[r.ticket] = std::move(res);
+    s->cv_done.notify_all();
+}
+
+static void worker_loop(vpm_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->m);
+    while (!s->stop) {
+        bool progressed = false;
+        // completions
+        for (auto &sl : s->slots) {
+            if (!sl.busy) continue;
+            cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) continue;
+            const Request &r = sl.req;
+            int status = VPM_OK;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                status = VPM_ERR_CUDA;
+            } else if (vpm_state_status(s->scenarios[r.scenario], sl.stream) != VPM_OK) {
+                status = VPM_ERR_NONFINITE;
+            }
+            float jmin = INFINITY;
+            for (int i = 0; i < r.K; ++i) jmin = fminf(jmin, sl.pinned[r.H + i]);
+            s->completed_rollouts += r.K;
+            finish(s, r, status, sl.pinned, jmin);
+            s->in_flight_bytes -= r.bytes;
+            s->scenario_busy[r.scenario] = 0;
+            sl.busy = false;
+            progressed = true;
+        }
+        // admission in arrival order: free slot, idle scenario, memory budget
+        for (auto it = s->queue.begin(); it != s->queue.end();) {
+            Slot *free_slot = nullptr;
+            for (auto &sl : s->slots)
+                if (!sl.busy) { free_slot = &sl; break; }
+            if (!free_slot) break;
+            if (s->scenario_busy[it->scenario] || s->in_flight_bytes + it->bytes > s->budget) { ++it; continue; }
+            Request r = std::move(*it);
+            it = s->queue.erase(it);
+            r.t_start = s->now_ms();
+            vpm_status v = start_request(s, *free_slot, r);
+            if (v != VPM_OK) {
+                finish(s, r, v, nullptr, 0.f);
+                continue;
+            }
+            free_slot->req = std::move(r);
+            free_slot->req.eps.clear();
+            free_slot->busy = true;
+            s->in_flight_bytes += free_slot->req.bytes;
+            s->scenario_busy[free_slot->req.scenario] = 1;
+            progressed = true;
+        }
+        bool any_busy = false;
+        for (auto &sl : s->slots) any_busy |= sl.busy;
+        if (!progressed) {
+            // idle: sleep until a submission; busy: poll the device again shortly
+            if (any_busy)
+                s->cv_work.wait_for(lk, std::chrono::microseconds(50));
+            else
+                s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+        }
+    }
+}
+
+extern "C" vpm_status vpm_server_create(const vpm_server_config *cfg, vpm_server **out)
+{
+    if (!cfg || !out || cfg->max_inflight < 1 || cfg->max_rollouts < 1 || cfg->max_horizon < 1)
+        return sfail(VPM_ERR_INVALID, "vpm_server_create: need max_inflight, max_rollouts, max_horizon >= 1");
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return sfail(VPM_ERR_CUDA, "no CUDA device available");
+    }
+    vpm_server *s = new vpm_server();
+    s->cfg = *cfg;
+    s->t0 = Clock::now();
+    cudaGetDevice(&s->device);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    s->budget = cfg->hbm_budget ? cfg->hbm_budget : (size_t)(0.8 * (double)free_b);
+    s->slots.resize(cfg->max_inflight);
+    const size_t pf = (size_t)cfg->max_rollouts * cfg->max_horizon + cfg->max_horizon + cfg->max_rollouts;
+    for (auto &sl : s->slots) {
+        cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (!e) e = cudaMallocHost((void **)&sl.pinned, sizeof(float) * pf);
+        if (e) {
+            cudaGetLastError();
+            vpm_server_destroy(s);
+            return sfail(VPM_ERR_OOM, "vpm_server_create: %s", cudaGetErrorString(e));
+        }
+        sl.pinned_floats = pf;
+    }
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_server_add_scenario(vpm_server *s, const vpm_params *params,
+                                              const double *h_particles, int n, int capacity,
+                                              const double *h_glider7, int *scenario)
+{
+    if (!s || !scenario) return sfail(VPM_ERR_INVALID, "vpm_server_add_scenario: null argument");
+    std::lock_guard<std::mutex> lk(s->m);
+    vpm_state *st = nullptr;
+    vpm_status v = vpm_state_create(params, h_particles, n, capacity, h_glider7, &st, nullptr);
+    if (v != VPM_OK) return v;
+    s->scenarios.push_back(st);
+    s->scenario_busy.push_back(0);
+    *scenario = (int)s->scenarios.size() - 1;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_server_submit(vpm_server *s, int scenario, int K, int H,
+                                        const float *h_mu, const float *h_eps, float lambda,
+                                        int advance_steps, float advance_u, long long *ticket)
+{
+    if (!s || !h_eps || !ticket) return sfail(VPM_ERR_INVALID, "vpm_server_submit: null argument");
+    if (K < 1 || H < 1 || K > s->cfg.max_rollouts || H > s->cfg.max_horizon || advance_steps < 0 ||
+        !(lambda > 0.f))
+        return sfail(VPM_ERR_INVALID, "vpm_server_submit: K, H outside the server's limits or lambda <= 0");
+    Request r;
+    r.K = K;
+    r.H = H;
+    r.scenario = scenario;
+    r.lambda = lambda;
+    r.advance_steps = advance_steps;
+    r.advance_u = advance_u;
+    r.bytes = request_bytes(K, H);
+    r.eps.assign(h_eps, h_eps + (size_t)K * H);
+    r.mu.assign(H, 0.f);
+    if (h_mu) r.mu.assign(h_mu, h_mu + H);
+    std::lock_guard<std::mutex> lk(s->m);
+    if (scenario < 0 || scenario >= (int)s->scenarios.size())
+        return sfail(VPM_ERR_INVALID, "vpm_server_submit: unknown scenario %d", scenario);
+    if (r.bytes > s->budget)
+        return sfail(VPM_ERR_CAPACITY, "vpm_server_submit: request needs %zu bytes, budget %zu", r.bytes, s->budget);
+    r.ticket = s->next_ticket++;
+    r.t_submit = s->now_ms();
+    // the newest request for a scenario supersedes the one still waiting in the queue
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+        if (it->scenario == scenario) {
+            finish(s, *it, VPM_ERR_BUSY, nullptr, 0.f);
+            s->queue.erase(it);
+            break;
+        }
+    s->queue.push_back(std::move(r));
+    *ticket = s->next_ticket - 1;
+    s->cv_work.notify_one();
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_server_poll(vpm_server *s, long long ticket, int timeout_ms,
+                                      vpm_server_result *out, float *h_mu_out)
+{
+    if (!s || !out) return sfail(VPM_ERR_INVALID, "vpm_server_poll: null argument");
+    std::unique_lock<std::mutex> lk(s->m);
+    auto ready = [&] { return s->done.count(ticket) > 0; };
+    if (!ready()) {
+        if (timeout_ms == 0) return VPM_ERR_BUSY;
+        if (timeout_ms < 0)
+            s->cv_done.wait(lk, ready);
+        else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            return VPM_ERR_TIMEOUT;
+    }
+    Result &r = s->done[ticket];
+    out->status = r.status;
+    out->scenario = r.req.scenario;
+    out->K = r.req.K;
+    out->H = r.req.H;
+    out->t_submit_ms = r.req.t_submit;
+    out->t_start_ms = r.req.t_start;
+    out->t_done_ms = r.req.t_done;
+    out->j_min = r.j_min;
+    if (h_mu_out && !r.mu.empty()) memcpy(h_mu_out, r.mu.data(), sizeof(float) * r.mu.size());
+    s->done.erase(ticket);
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_server_stats(vpm_server *s, long long *completed_rollouts,
+                                       int *queued, int *in_flight, size_t *in_flight_bytes)
+{
+    if (!s) return sfail(VPM_ERR_INVALID, "null server");
+    std::lock_guard<std::mutex> lk(s->m);
+    if (completed_rollouts) *completed_rollouts = s->completed_rollouts;
+    if (queued) *queued = (int)s->queue.size();
+    int b = 0;
+    for (auto &sl : s->slots) b += sl.busy;
+    if (in_flight) *in_flight = b;
+    if (in_flight_bytes) *in_flight_bytes = s->in_flight_bytes;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_server_read_scenario(vpm_server *s, int scenario, double *h_particles,
+                                               int *n_out, double *h_glider7)
+{
+    if (!s) return sfail(VPM_ERR_INVALID, "null server");
+    std::unique_lock<std::mutex> lk(s->m);
+    if (scenario < 0 || scenario >= (int)s->scenarios.size())
+        return sfail(VPM_ERR_INVALID, "unknown scenario");
+    s->cv_done.wait(lk, [&] { return !s->scenario_busy[scenario]; });
+    for (auto &r : s->queue)
+        if (r.scenario == scenario) return sfail(VPM_ERR_BUSY, "scenario has a queued request");
+    return vpm_state_read(s->scenarios[scenario], h_particles, n_out, h_glider7, nullptr, nullptr);
+}
+
+extern "C" vpm_status vpm_server_destroy(vpm_server *s)
+{
+    if (!s) return VPM_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->m);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    cudaDeviceSynchronize();
+    for (auto &sl : s->slots) {
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+    }
+    for (auto *st : s->scenarios) vpm_state_destroy(st);
+    cudaGetLastError();
+    delete s;
+    return VPM_OK;
+}

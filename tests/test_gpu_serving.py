@@ -1,0 +1,96 @@
+"""Replanning server: results alone and in a mix, the plain per-request form, supersession of
+queued requests, admission by the memory budget, resident fields advanced between replans."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import cuda
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [300, 500, 800, 400, 1000, 600]
+
+
+def _server(V, max_inflight, budget=0, H=20):
+    srv = V.Server(max_inflight=max_inflight, max_rollouts=2048, max_horizon=100, hbm_budget=budget)
+    p = W.glider_params()
+    fields = [W.background_field(50 + i, n) for i, n in enumerate(SIZES)]
+    for f in fields:
+        srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 2 * 100 + 10)
+    return srv, p, fields
+
+
+def _direct_mu(V, torch, p, field, eps, lam):
+    st = V.State(p, field, W.GLIDER_X0, len(field) + 2 * eps.shape[1])
+    c = V.mppi_perturb(torch.zeros(eps.shape[1], device="cuda"), torch.tensor(eps, device="cuda"))
+    out = st.rollout_batch(c, want_final=False)
+    mu = V.mppi_update(V.mppi_weights(out["costs"], lam), c)
+    return mu.cpu().numpy(), out["costs"].min().item()
+
+
+def test_same_result_alone_in_mix_and_per_request():
+    torch, V = cuda()
+    eps_x = W.mppi_noise(1, 128, 20, W.MPPI_SIGMA_U)
+    srv, p, fields = _server(V, 8)
+    res_a, mu_a = srv.poll(srv.submit(0, eps_x))
+    assert res_a["status"] == V.VPM_OK
+    # the same request among others on the device
+    tickets = [srv.submit(0, eps_x)]
+    for s in range(1, len(SIZES)):
+        tickets.append(srv.submit(s, W.mppi_noise(10 + s, 256 * (1 + s % 3), 20, W.MPPI_SIGMA_U)))
+    results = [srv.poll(t) for t in tickets]
+    assert all(r[0]["status"] == V.VPM_OK for r in results)
+    assert np.array_equal(results[0][1], mu_a) and results[0][0]["j_min"] == res_a["j_min"]
+    # requests overlapped on the device
+    spans = sorted((r[0]["t_start_ms"], r[0]["t_done_ms"]) for r in results)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+    srv.close()
+    # the plain per-request form and the direct library calls give the same numbers
+    srv1, _, _ = _server(V, 1)
+    res_1, mu_1 = srv1.poll(srv1.submit(0, eps_x))
+    srv1.close()
+    assert np.array_equal(mu_1, mu_a)
+    mu_d, jmin_d = _direct_mu(V, torch, p, fields[0], eps_x, 10.0)
+    assert np.array_equal(mu_d, mu_a) and jmin_d == res_a["j_min"]
+
+
+def test_newer_request_supersedes_queued_one():
+    torch, V = cuda()
+    srv, p, fields = _server(V, 1)
+    long_t = srv.submit(4, W.mppi_noise(2, 2048, 100, W.MPPI_SIGMA_U))
+    a = srv.submit(1, W.mppi_noise(3, 64, 20, W.MPPI_SIGMA_U))
+    b = srv.submit(1, W.mppi_noise(4, 64, 20, W.MPPI_SIGMA_U))
+    ra, rb, rl = srv.poll(a), srv.poll(b), srv.poll(long_t)
+    assert ra[0]["status"] == V.VPM_ERR_BUSY
+    assert rb[0]["status"] == V.VPM_OK and rl[0]["status"] == V.VPM_OK
+    srv.close()
+
+
+def test_admission_by_memory_budget():
+    torch, V = cuda()
+    K, H = 512, 20
+    need = 4 * (2 * K * H + 2 * K + H)
+    srv, p, fields = _server(V, 4, budget=need + need // 2)
+    tickets = [srv.submit(s, W.mppi_noise(20 + s, K, H, W.MPPI_SIGMA_U)) for s in range(3)]
+    res = [srv.poll(t)[0] for t in tickets]
+    assert all(r["status"] == V.VPM_OK for r in res)
+    spans = sorted((r["t_start_ms"], r["t_done_ms"]) for r in res)
+    assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))   # one at a time
+    with pytest.raises(V.VpmError) as e:
+        srv.submit(0, W.mppi_noise(30, 2048, H, W.MPPI_SIGMA_U))
+    assert e.value.status == V.VPM_ERR_CAPACITY
+    srv.close()
+
+
+def test_resident_field_advances_like_vpm_step():
+    torch, V = cuda()
+    srv, p, fields = _server(V, 2)
+    t = srv.submit(2, W.mppi_noise(40, 32, 10, W.MPPI_SIGMA_U), advance_steps=3, advance_u=0.7)
+    assert srv.poll(t)[0]["status"] == V.VPM_OK
+    parts, xg = srv.read_scenario(2, SIZES[2] + 210)
+    st = V.State(p, fields[2], W.GLIDER_X0, SIZES[2] + 210)
+    for _ in range(3):
+        st.step(0.7)
+    ref_parts, ref_xg, _ = st.read()
+    assert np.array_equal(parts, ref_parts) and np.array_equal(xg, ref_xg)
+    srv.close()
