@@ -282,6 +282,10 @@ typedef struct {
     size_t hbm_budget;    /* device bytes of request buffers in flight; 0: 80 % of free memory   */
     int max_rollouts;     /* largest K accepted                                                 */
     int max_horizon;      /* largest H accepted                                                 */
+    int max_inflight_rollouts;  /* rollouts on the device at once; a request is admitted while the
+                                   total stays within it or when nothing else runs. 0: the rollout
+                                   blocks the device holds at once (SMs x 7), beyond which more
+                                   concurrency only adds latency                                */
 } vpm_server_config;
 
 typedef struct {

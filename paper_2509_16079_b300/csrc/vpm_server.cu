@@ -5,7 +5,9 @@
 // scenario's resident field, optionally after advancing that field by a few committed steps
 // (the tracking instance of §IV-C). A worker thread owns all device work: it completes finished
 // requests, then admits queued ones in arrival order while a slot is free, the scenario has no
-// request on the device, and the request's device buffers fit the memory budget. Each admitted
+// request on the device, the request's device buffers fit the memory budget, and its rollouts
+// fit the rollout budget (beyond the rollout blocks the device holds at once, more concurrency
+// adds latency without throughput). Each admitted
 // request runs on its own stream, so requests that arrive while others are on the GPU overlap
 // with them. A request for a scenario supersedes that scenario's older request still waiting
 // in the queue. Every request is computed by the same deterministic kernels, so its result is
@@ -74,6 +76,7 @@ struct vpm_server {
     vpm_server_config cfg;
     int device = 0;
     size_t budget = 0, in_flight_bytes = 0;
+    long long rollout_budget = 0, in_flight_rollouts = 0;
     Clock::time_point t0;
     std::vector<vpm_state *> scenarios;
     std::vector<int> scenario_busy;
@@ -168,6 +171,7 @@ static void worker_loop(vpm_server *s)
             s->completed_rollouts += r.K;
             finish(s, r, status, sl.pinned, jmin);
             s->in_flight_bytes -= r.bytes;
+            s->in_flight_rollouts -= r.K;
             s->scenario_busy[r.scenario] = 0;
             sl.busy = false;
             progressed = true;
@@ -178,6 +182,9 @@ static void worker_loop(vpm_server *s)
             for (auto &sl : s->slots)
                 if (!sl.busy) { free_slot = &sl; break; }
             if (!free_slot) break;
+            const bool fits_rollouts = s->in_flight_rollouts == 0 ||
+                                       s->in_flight_rollouts + it->K <= s->rollout_budget;
+            if (!fits_rollouts) break;        // keep arrival order for work that fills the device
             if (s->scenario_busy[it->scenario] || s->in_flight_bytes + it->bytes > s->budget) { ++it; continue; }
             Request r = std::move(*it);
             it = s->queue.erase(it);
@@ -191,6 +198,7 @@ static void worker_loop(vpm_server *s)
             free_slot->req.eps.clear();
             free_slot->busy = true;
             s->in_flight_bytes += free_slot->req.bytes;
+            s->in_flight_rollouts += free_slot->req.K;
             s->scenario_busy[free_slot->req.scenario] = 1;
             progressed = true;
         }
@@ -222,6 +230,9 @@ extern "C" vpm_status vpm_server_create(const vpm_server_config *cfg, vpm_server
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     s->budget = cfg->hbm_budget ? cfg->hbm_budget : (size_t)(0.8 * (double)free_b);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    s->rollout_budget = cfg->max_inflight_rollouts > 0 ? cfg->max_inflight_rollouts : (long long)sms * 7;
     s->slots.resize(cfg->max_inflight);
     const size_t pf = (size_t)cfg->max_rollouts * cfg->max_horizon + cfg->max_horizon + cfg->max_rollouts;
     for (auto &sl : s->slots) {

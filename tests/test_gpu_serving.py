@@ -11,8 +11,9 @@ pytestmark = pytest.mark.gpu
 SIZES = [300, 500, 800, 400, 1000, 600]
 
 
-def _server(V, max_inflight, budget=0, H=20):
-    srv = V.Server(max_inflight=max_inflight, max_rollouts=2048, max_horizon=100, hbm_budget=budget)
+def _server(V, max_inflight, budget=0, H=20, max_rollouts_inflight=0):
+    srv = V.Server(max_inflight=max_inflight, max_rollouts=2048, max_horizon=100, hbm_budget=budget,
+                   max_inflight_rollouts=max_rollouts_inflight)
     p = W.glider_params()
     fields = [W.background_field(50 + i, n) for i, n in enumerate(SIZES)]
     for f in fields:
@@ -31,7 +32,7 @@ def _direct_mu(V, torch, p, field, eps, lam):
 def test_same_result_alone_in_mix_and_per_request():
     torch, V = cuda()
     eps_x = W.mppi_noise(1, 128, 20, W.MPPI_SIGMA_U)
-    srv, p, fields = _server(V, 8)
+    srv, p, fields = _server(V, 8, max_rollouts_inflight=100000)
     res_a, mu_a = srv.poll(srv.submit(0, eps_x))
     assert res_a["status"] == V.VPM_OK
     # the same request among others on the device
@@ -66,6 +67,18 @@ def test_newer_request_supersedes_queued_one():
     srv.close()
 
 
+def test_admission_by_rollouts_in_flight():
+    torch, V = cuda()
+    srv, p, fields = _server(V, 8, max_rollouts_inflight=600)
+    ks = [512, 512, 64, 64]
+    tickets = [srv.submit(s, W.mppi_noise(60 + s, k, 20, W.MPPI_SIGMA_U)) for s, k in enumerate(ks)]
+    res = [srv.poll(t)[0] for t in tickets]
+    assert all(r["status"] == V.VPM_OK for r in res)
+    # the two 512-rollout requests never share the device; the 64-rollout ones may join
+    assert res[1]["t_start_ms"] >= res[0]["t_done_ms"]
+    srv.close()
+
+
 def test_admission_by_memory_budget():
     torch, V = cuda()
     K, H = 512, 20
@@ -85,12 +98,12 @@ def test_admission_by_memory_budget():
 def test_resident_field_advances_like_vpm_step():
     torch, V = cuda()
     srv, p, fields = _server(V, 2)
-    t = srv.submit(2, W.mppi_noise(40, 32, 10, W.MPPI_SIGMA_U), advance_steps=3, advance_u=0.7)
+    t = srv.submit(2, W.mppi_noise(40, 32, 10, W.MPPI_SIGMA_U), advance_steps=3, advance_u=0.75)
     assert srv.poll(t)[0]["status"] == V.VPM_OK
     parts, xg = srv.read_scenario(2, SIZES[2] + 210)
     st = V.State(p, fields[2], W.GLIDER_X0, SIZES[2] + 210)
     for _ in range(3):
-        st.step(0.7)
+        st.step(0.75)
     ref_parts, ref_xg, _ = st.read()
     assert np.array_equal(parts, ref_parts) and np.array_equal(xg, ref_xg)
     srv.close()
