@@ -17,6 +17,7 @@ namespace vpm {
 struct Geo {
     double xw, zw, tx, tz, nx, nz, vx, vz, om;
     double ct, st;                   // cos and sin of the pitch angle
+    double cp, sp;                   // cos and sin of pitch + elevator angle (Eqs. 18-20)
     int lev, tev;
 };
 
@@ -28,43 +29,58 @@ struct Work {
     double gs[kMaxS];                // Gamma_b, Gamma_LEV, Gamma_TEV of this step
     double fm[3];
     double red[kMaxWarps];
+    union {                          // scratch of successive phases of the plate work
+        float tgt_f[2 * (kMaxC + kMaxB)];  // plate points in binary32 (binary32 plate sums)
+        double b[kMaxS];             // right-hand side of Eq. 10 (active rows; the solve)
+        double ld[3 * kMaxB];        // per-panel force x, force z, moment (the loads)
+    };
     float bnd_f[4 * kMaxB];          // bound positions as (x_hi, x_lo, z_hi, z_lo)
     float gb_f[kMaxB];               // bound circulations (binary32 copy)
+    float4 fresh[2];                 // this step's shed particles before advection (binary32)
+    float2 fresh_vel[2];             // and their convection velocities
     Geo geo;
     int n;
     int flag;
     int chunk_next;                  // next unclaimed target chunk of the pair sums
 };
 
-// ------------------------------------------------------------------ geometry (thread 0)
+// ------------------------------------------------------------------ geometry (warp 0)
 
+// Plate frame from the glider state. All lanes of the calling warp take part: lane 1 forms sin
+// and cos of pitch + elevator angle (needed by the elevator force of Eqs. 18-20 later in the
+// step) in the same call in which lane 0 forms those of the pitch angle; lane 0 writes the frame.
 __device__ void plate_geometry(const DevParams &p, Work &w)
 {
+    const int lane = threadIdx.x & 31;
     const double *xg = w.xg;
     double s, c;
-    sincos(xg[2], &s, &c);
+    sincos(lane == 1 ? xg[2] + xg[3] : xg[2], &s, &c);
     Geo &G = w.geo;
-    G.ct = c; G.st = s;
-    G.xw = xg[0] - p.l_w * c;
-    G.zw = xg[1] - p.l_w * s;
-    G.tx = -c; G.tz = -s;        // leading edge -> trailing edge
-    G.nx = -s; G.nz = c;         // body-up normal
-    if (p.fixed_plate) {
-        G.vx = 0.0; G.vz = 0.0; G.om = 0.0;
-    } else {
-        G.vx = xg[4] + p.l_w * xg[6] * s;
-        G.vz = xg[5] - p.l_w * xg[6] * c;
-        G.om = xg[6];
+    if (lane == 1) { G.cp = c; G.sp = s; }
+    if (lane == 0) {
+        G.ct = c; G.st = s;
+        G.xw = xg[0] - p.l_w * c;
+        G.zw = xg[1] - p.l_w * s;
+        G.tx = -c; G.tz = -s;        // leading edge -> trailing edge
+        G.nx = -s; G.nz = c;         // body-up normal
+        if (p.fixed_plate) {
+            G.vx = 0.0; G.vz = 0.0; G.om = 0.0;
+        } else {
+            G.vx = xg[4] + p.l_w * xg[6] * s;
+            G.vz = xg[5] - p.l_w * xg[6] * c;
+            G.om = xg[6];
+        }
+        if (p.shed_gate == VPM_GATE_OFF) {
+            G.lev = G.tev = 1;
+        } else {
+            double alpha = xg[2] - atan2(G.vz - p.u_inf_z, G.vx - p.u_inf_x);
+            alpha = atan2(sin(alpha), cos(alpha));
+            int open = fabs(alpha) > p.alpha_crit;
+            G.lev = open;
+            G.tev = (p.shed_gate != VPM_GATE_BOTH) || open;
+        }
     }
-    if (p.shed_gate == VPM_GATE_OFF) {
-        G.lev = G.tev = 1;
-    } else {
-        double alpha = xg[2] - atan2(G.vz - p.u_inf_z, G.vx - p.u_inf_x);
-        alpha = atan2(sin(alpha), cos(alpha));
-        int open = fabs(alpha) > p.alpha_crit;
-        G.lev = (p.shed_gate == VPM_GATE_OFF) || open;
-        G.tev = (p.shed_gate != VPM_GATE_BOTH) || open;
-    }
+    __syncwarp();
 }
 
 // Bound vortex j as a double-length binary32 pair (x_hi, x_lo, z_hi, z_lo).
@@ -92,12 +108,10 @@ __device__ __forceinline__ void plate_point(const DevParams &p, const Geo &G, in
 
 // ------------------------------------------------------------------ glider (§III-B)
 
-__device__ void glider_rhs(const DevParams &p, const double *xg, double ct, double st, double fwx,
-                           double fwz, double mw, double u, double *f)
+__device__ void glider_rhs(const DevParams &p, const double *xg, double ct, double st, double cp,
+                           double sp, double fwx, double fwz, double mw, double u, double *f)
 {
-    double ph = xg[3], xd = xg[4], zd = xg[5], thd = xg[6];
-    double sp, cp;
-    sincos(xg[2] + ph, &sp, &cp);
+    double xd = xg[4], zd = xg[5], thd = xg[6];
     // elevator velocity (Eq. 18) with phidot = u
     double exd = xd + p.l * thd * st + p.l_e * (thd + u) * sp;
     double ezd = zd - p.l * thd * ct - p.l_e * (thd + u) * cp;
@@ -119,42 +133,26 @@ __device__ void glider_rhs(const DevParams &p, const double *xg, double ct, doub
 
 // ------------------------------------------------------------------ step phases
 
-// Phase A: wake-induced velocity at the plate points (Eq. 12's sum) and the Kelvin sum, by
-// warps warp0 .. warp0 + nwarps - 1. Each warp takes plate points in turn; its lanes split the
-// sources and the partial sums are reduced in binary64.
-template <class R, int KER>
-__device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>::P *part, int n,
-                           int warp0, int nwarps)
+// Phase A, binary64 path: wake-induced velocity at the plate points (Eq. 12's sum) and the
+// Kelvin sum, by all warps of the block. Each warp takes plate points in turn; its lanes split
+// the sources and the partial sums are reduced in binary64. w.red receives one Kelvin partial
+// per warp.
+template <int KER>
+__device__ void plate_sums_f64(const DevParams &p, Work &w, const Part64 *part, int n)
 {
-    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - warp0;
-    const int tid = threadIdx.x - 32 * warp0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int M = p.n_c + p.n_b;
     for (int t = warp; t < M; t += nwarps) {
         double tx, tz;
         plate_point(p, w.geo, t, tx, tz);
         double su = 0.0, sw = 0.0;
-        if constexpr (sizeof(R) == 4) {
-            const float txf = (float)tx, tzf = (float)tz;
-            const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
-            float u = 0.f, v = 0.f;
-            for (int j = lane; j < n; j += 32) {
-                float4 s = part[j];
-                float dx = txf - s.x, dz = tzf - s.y;
-                float r2 = fmaf(dx, dx, dz * dz);
-                float g = s.z * PairF32<KER>::q(r2, rc4, irc2);
-                u = fmaf(-dz, g, u);
-                v = fmaf(dx, g, v);
-            }
-            su = u; sw = v;
-        } else {
-            for (int j = lane; j < n; j += 32) {
-                Part64 s = part[j];
-                double dx = tx - s.x, dz = tz - s.z;
-                double r2 = fma(dx, dx, dz * dz);
-                double g = s.g * PairF64<KER>::q(r2, p.rc4, p.inv_rc2);
-                su = fma(-dz, g, su);
-                sw = fma(dx, g, sw);
-            }
+        for (int j = lane; j < n; j += 32) {
+            Part64 s = part[j];
+            double dx = tx - s.x, dz = tz - s.z;
+            double r2 = fma(dx, dx, dz * dz);
+            double g = s.g * PairF64<KER>::q(r2, p.rc4, p.inv_rc2);
+            su = fma(-dz, g, su);
+            sw = fma(dx, g, sw);
         }
         for (int o = 16; o > 0; o >>= 1) {
             su += __shfl_xor_sync(0xffffffffu, su, o);
@@ -165,105 +163,185 @@ __device__ void plate_sums(const DevParams &p, Work &w, const typename Store<R>:
             w.vt[2 * t + 1] = sw * kInv2Pi;
         }
     }
-    // Kelvin sum (Eq. 7): each thread's share summed exactly enough in compensated arithmetic
-    // of the storage type, then combined in binary64 in a fixed order
-    double gsum;
-    if constexpr (sizeof(R) == 4) {
-        float s = 0.f, c = 0.f;
-        for (int j = tid; j < n; j += 32 * nwarps) kahan_add(s, c, part[j].z);
-        gsum = (double)s - (double)c;
-    } else {
-        gsum = 0.0;
-        for (int j = tid; j < n; j += 32 * nwarps) gsum += part[j].g;
-    }
+    double gsum = 0.0;
+    for (int j = threadIdx.x; j < n; j += (int)blockDim.x) gsum += part[j].g;
     for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
     if (lane == 0) w.red[warp] = gsum;
-    if (tid == 0)
-        for (int i = nwarps; i < kMaxWarps; ++i) w.red[i] = 0.0;
 }
 
-// Phase B (thread 0): surface solve, loads, glider update, shedding. Returns the new count.
+// Phase A, binary32 path, by warp 0 alone while the other warps start on the pair sums. The
+// plate points are formed in binary64 (one lane each) and rounded once; targets then go
+// kPlateG at a time so that their dependency chains overlap. Lanes split the sources; the 32
+// partial sums of a target are combined by a butterfly in binary32. The Kelvin sum (Eq. 7) is
+// Kahan-compensated per lane and combined in binary64; w.red[0] receives it.
+constexpr int kPlateG = 4;
+
+template <int KER>
+__device__ void plate_sums_f32(const DevParams &p, Work &w, const float4 *part, int n)
+{
+    const int lane = threadIdx.x & 31;
+    const int M = p.n_c + p.n_b;
+    const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    for (int t = lane; t < M; t += 32) {
+        double x, z;
+        plate_point(p, w.geo, t, x, z);
+        w.tgt_f[2 * t] = (float)x;
+        w.tgt_f[2 * t + 1] = (float)z;
+    }
+    __syncwarp();
+    for (int t0 = 0; t0 < M; t0 += kPlateG) {
+        float tx[kPlateG], tz[kPlateG], u[kPlateG], v[kPlateG];
+#pragma unroll
+        for (int g = 0; g < kPlateG; ++g) {
+            const int t = min(t0 + g, M - 1);
+            tx[g] = w.tgt_f[2 * t];
+            tz[g] = w.tgt_f[2 * t + 1];
+            u[g] = v[g] = 0.f;
+        }
+        for (int j = lane; j < n; j += 32) {
+            const float4 s = part[j];
+#pragma unroll
+            for (int g = 0; g < kPlateG; ++g) {
+                const float dx = tx[g] - s.x, dz = tz[g] - s.y;
+                const float q = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+                u[g] = fmaf(-dz, q, u[g]);
+                v[g] = fmaf(dx, q, v[g]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int g = 0; g < kPlateG; ++g) {
+                u[g] += __shfl_xor_sync(0xffffffffu, u[g], o);
+                v[g] += __shfl_xor_sync(0xffffffffu, v[g], o);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int g = 0; g < kPlateG; ++g) {
+                if (t0 + g < M) {
+                    w.vt[2 * (t0 + g)] = (double)u[g] * kInv2Pi;
+                    w.vt[2 * (t0 + g) + 1] = (double)v[g] * kInv2Pi;
+                }
+            }
+        }
+    }
+    float gs = 0.f, gc = 0.f;
+    for (int j = lane; j < n; j += 32) kahan_add(gs, gc, part[j].z);
+    double gsum = (double)gs - (double)gc;
+    for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+    if (lane == 0) w.red[0] = gsum;
+}
+
+// Phase B by one warp (all 32 lanes call it): relative velocity at the plate points (Eq. 12),
+// the surface solve Gamma_S = K^-1 b (Eq. 11), unsteady Bernoulli loads (Eqs. 13-15), the
+// glider's explicit Euler update (Eqs. 18-22) and shedding. Rows of the solve and panels of
+// the loads go one per lane; every per-row and per-panel value is formed in the same order as
+// a serial evaluation, and the panel loads are summed by lane 0 in panel order. nred is the
+// number of Kelvin partials in w.red. Returns the new particle count (all lanes).
 template <class R>
 __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *part, int n,
-                           double u_ctrl)
+                           double u_ctrl, int nred)
 {
+    const int lane = threadIdx.x & 31;
     const Geo &G = w.geo;
     const int nb = p.n_b, nc = p.n_c, M = nc + nb;
     // complete Eq. 12: free stream, minus plate translation and rotation e_z x (r_s - r_g)
-    for (int t = 0; t < M; ++t) {
+    for (int t = lane; t < M; t += 32) {
         double x, z;
         plate_point(p, G, t, x, z);
         double rx = x - G.xw, rz = z - G.zw;
         w.vt[2 * t] += p.u_inf_x - G.vx + G.om * rz;
         w.vt[2 * t + 1] += p.u_inf_z - G.vz - G.om * rx;
     }
-    double gw = 0.0;
-    for (int i = 0; i < kMaxWarps; ++i) gw += w.red[i];
-    // right-hand side of Eq. 10 for the active rows, Gamma_S = K^-1 b (Eq. 11)
+    __syncwarp();
+    // right-hand side of Eq. 10 for the active rows (normal condition, then Kelvin)
     const int lev = G.lev, tev = G.tev, m = nb + lev + tev;
-    double b[kMaxS];
-    int r = 0;
-    for (int i = 0; i < nc; ++i) {
+    for (int i = lane; i < nc; i += 32) {
         if ((i == 0 && !lev) || (i == nc - 1 && !tev)) continue;
-        b[r++] = -(w.vt[2 * i] * G.nx + w.vt[2 * i + 1] * G.nz);
+        w.b[i - (lev ? 0 : 1)] = -(w.vt[2 * i] * G.nx + w.vt[2 * i + 1] * G.nz);
     }
-    b[r] = -gw;
+    if (lane == 0) {
+        double gw = 0.0;
+        for (int i = 0; i < nred; ++i) gw += w.red[i];
+        w.b[m - 1] = -gw;
+    }
+    __syncwarp();
+    // Gamma_S = K^-1 b (Eq. 11), one row per lane
     const double *ki = p.kinv + (size_t)(lev * 2 + tev) * kMaxS * kMaxS;
-    double gs[kMaxS];
-    for (int i = 0; i < m; ++i) {
+    for (int i = lane; i < m; i += 32) {
         double s = 0.0;
-        for (int j = 0; j < m; ++j) s = fma(__ldg(ki + i * kMaxS + j), b[j], s);
-        gs[i] = s;
+        for (int j = 0; j < m; ++j) s = fma(__ldg(ki + i * kMaxS + j), w.b[j], s);
+        const int dst = i < nb ? i : (i == nb && lev ? nb : nb + 1);
+        w.gs[dst] = s;
     }
-    for (int j = 0; j < nb; ++j) w.gs[j] = gs[j];
-    w.gs[nb] = lev ? gs[nb] : 0.0;
-    w.gs[nb + 1] = tev ? gs[nb + lev] : 0.0;
-    // unsteady Bernoulli pressure (Eq. 13) and wing load (Eqs. 14-15)
+    if (lane == 0) {
+        if (!lev) w.gs[nb] = 0.0;
+        if (!tev) w.gs[nb + 1] = 0.0;
+    }
+    __syncwarp();
+    // unsteady Bernoulli pressure (Eq. 13) and panel loads (Eqs. 14-15), one panel per lane;
+    // the running sums of Gamma_b up to the panel are formed as in a serial pass
     const bool hp = w.hist[nb + 1] != 0.0;
-    double cum = 0.0, cum_prev = 0.0, fwx = 0.0, fwz = 0.0, mw = 0.0;
     const double dlev = hp ? (w.gs[nb] - w.hist[nb]) / p.dt : 0.0;
-    for (int i = 0; i < nb; ++i) {
-        cum += w.gs[i];
-        cum_prev += w.hist[i];
+    for (int i = lane; i < nb; i += 32) {
+        double cum = 0.0, cum_prev = 0.0;
+        for (int k = 0; k <= i; ++k) {
+            cum += w.gs[k];
+            cum_prev += w.hist[k];
+        }
         const double *vb = &w.vt[2 * (nc + i)];
         double tang = (w.gs[i] / p.lb) * (vb[0] * G.tx + vb[1] * G.tz);
         double dsum = hp ? (cum - cum_prev) / p.dt : 0.0;
         double dp = p.rho * (tang + dsum + dlev);
         double fx = p.lb * p.span * dp * G.nx, fz = p.lb * p.span * dp * G.nz;
-        fwx += fx;
-        fwz += fz;
         double si = -0.5 * p.chord + (i + 0.5) * p.lb;
-        mw += (si * G.tx) * fz - (si * G.tz) * fx;
+        w.ld[3 * i] = fx;
+        w.ld[3 * i + 1] = fz;
+        w.ld[3 * i + 2] = (si * G.tx) * fz - (si * G.tz) * fx;
     }
-    w.fm[0] = fwx; w.fm[1] = fwz; w.fm[2] = mw;
-    // glider explicit Euler update with this step's loads
-    if (!p.fixed_plate) {
-        double f[7];
-        glider_rhs(p, w.xg, G.ct, G.st, fwx, fwz, mw, u_ctrl, f);
-        for (int c = 0; c < 7; ++c) w.xg[c] += p.dt * f[c];
+    __syncwarp();
+    if (lane == 0) {
+        double fwx = 0.0, fwz = 0.0, mw = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            fwx += w.ld[3 * i];
+            fwz += w.ld[3 * i + 1];
+            mw += w.ld[3 * i + 2];
+        }
+        w.fm[0] = fwx; w.fm[1] = fwz; w.fm[2] = mw;
+        // glider explicit Euler update with this step's loads
+        if (!p.fixed_plate) {
+            double f[7];
+            glider_rhs(p, w.xg, G.ct, G.st, G.cp, G.sp, fwx, fwz, mw, u_ctrl, f);
+            for (int c = 0; c < 7; ++c) w.xg[c] += p.dt * f[c];
+        }
+        bool finite = isfinite(fwx) && isfinite(fwz) && isfinite(mw);
+        for (int c = 0; c < 7; ++c) finite = finite && isfinite(w.xg[c]);
+        if (!finite) w.flag |= kStNonFinite;
+        w.hist[nb] = w.gs[nb];
+        w.hist[nb + 1] = 1.0;
     }
-    for (int j = 0; j < nb; ++j) {
+    for (int j = lane; j < nb; j += 32) {
         w.hist[j] = w.gs[j];
         w.gb_f[j] = (float)w.gs[j];
     }
-    w.hist[nb] = w.gs[nb];
-    w.hist[nb + 1] = 1.0;
-    bool finite = isfinite(fwx) && isfinite(fwz) && isfinite(mw);
-    for (int c = 0; c < 7; ++c) finite = finite && isfinite(w.xg[c]);
-    if (!finite) w.flag |= kStNonFinite;
-    // W <- W u E (LEV first, then TEV)
+    // W <- W u E (LEV first, then TEV): lane 0 sheds the LEV, lane 1 the TEV
     const double ds = p.shed_dist;
-    if (lev) {
-        double x, z;
-        plate_point(p, G, 0, x, z);
-        part[n++] = Store<R>::make(x - ds * G.tx, z - ds * G.tz, w.gs[nb]);
+    if ((lane == 0 && lev) || (lane == 1 && tev)) {
+        double x, z, g;
+        if (lane == 0) {
+            plate_point(p, G, 0, x, z);
+            x -= ds * G.tx; z -= ds * G.tz; g = w.gs[nb];
+        } else {
+            plate_point(p, G, nc - 1, x, z);
+            x += ds * G.tx; z += ds * G.tz; g = w.gs[nb + 1];
+        }
+        const int k = lane == 0 ? 0 : lev;
+        part[n + k] = Store<R>::make(x, z, g);
+        if constexpr (sizeof(R) == 4) w.fresh[k] = part[n + k];
     }
-    if (tev) {
-        double x, z;
-        plate_point(p, G, nc - 1, x, z);
-        part[n++] = Store<R>::make(x + ds * G.tx, z + ds * G.tz, w.gs[nb + 1]);
-    }
-    return n;
+    __syncwarp();
+    return n + lev + tev;
 }
 
 // Phase C: convection velocity of every wake particle (Eq. 16) plus the free stream.
@@ -271,29 +349,30 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
 // Binary32 path. The sum over pairs of particles that existed before this step's shedding
 // does not depend on the surface solve, so it runs while warp 0 does the plate work; only the
 // bound vortices and the freshly shed vortices need Gamma_S, and their terms are added after.
-// The old-old sum is split into chunks of up to 128 consecutive targets that the warps claim
-// from a shared counter; lane l of a chunk starting at b owns targets b + l + 32 k, k < T.
-// Sources stream from shared memory by broadcast loads, each serving T pairs; plain sums over
-// tiles of kTile sources are added into Kahan-compensated totals. Every target's sum is formed
-// by one lane in a fixed order, so the result does not depend on which warp claimed it.
+// The old-old sum is split into chunks of consecutive targets that the warps claim from a
+// shared counter; lane l of a chunk starting at b owns targets b + l + 32 k, k < T. Sources
+// stream from shared memory by broadcast loads, each serving T pairs; plain sums over tiles of
+// kTile sources are added into Kahan-compensated totals. Every target's sum is formed by one
+// lane in a fixed order, so the result does not depend on which warp claimed it or on T.
 constexpr int kTile = 64;
-constexpr int kChunk = 128;
 #ifndef VPM_SRC_UNROLL
 #define VPM_SRC_UNROLL 4      // sources in flight per inner-loop iteration
 #endif
 constexpr int kSrcUnroll = VPM_SRC_UNROLL;
 
+
+// Sources 0 .. n-1; targets base + lane + 32 k below lim.
 template <int KER, int T>
 __device__ __forceinline__ void old_pairs_chunk(const DevParams &p, const float4 *part,
-                                                float2 *vel, int n, int base)
+                                                float2 *vel, int n, int base, int lim)
 {
     const int lane = threadIdx.x & 31;
-    const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    const float rc4s = (float)p.rc4, irc2 = (float)p.inv_rc2;
     float tx[T], tz[T], su[T], cu[T], sw[T], cw[T];
 #pragma unroll
     for (int k = 0; k < T; ++k) {
         const int i = base + lane + 32 * k;
-        const float4 q = part[i < n ? i : 0];
+        const float4 q = part[i < lim ? i : 0];
         tx[k] = q.x;
         tz[k] = q.y;
         su[k] = cu[k] = sw[k] = cw[k] = 0.f;
@@ -309,7 +388,7 @@ __device__ __forceinline__ void old_pairs_chunk(const DevParams &p, const float4
 #pragma unroll
             for (int k = 0; k < T; ++k) {
                 const float dx = tx[k] - s.x, dz = tz[k] - s.y;
-                const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+                const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4s, irc2);
                 au[k] = fmaf(-dz, g, au[k]);
                 aw[k] = fmaf(dx, g, aw[k]);
             }
@@ -323,27 +402,67 @@ __device__ __forceinline__ void old_pairs_chunk(const DevParams &p, const float4
 #pragma unroll
     for (int k = 0; k < T; ++k) {
         const int i = base + lane + 32 * k;
-        if (i < n) vel[i] = make_float2(su[k] - cu[k], sw[k] - cw[k]);   // raw, unscaled
+        if (i < lim) vel[i] = make_float2(su[k] - cu[k], sw[k] - cw[k]);   // raw, unscaled
     }
 }
 
+// Guided chunk schedule over the n old targets: chunks of kBulk targets first (kBulk / 32
+// targets per lane, fewer shared-memory loads per pair), then 64-target chunks, and the last
+// kTail32 targets in 32-target chunks so that the warps finish the phase close together.
+// Every target's sum is formed by one lane in the same order whatever chunk holds it.
+#ifndef VPM_BULK
+#define VPM_BULK 128          // targets per bulk chunk: 128 (4 per lane) or 64 (2 per lane)
+#endif
+#ifndef VPM_TAIL32
+#define VPM_TAIL32 128        // targets at the end of the list served in 32-target chunks
+#endif
+#ifndef VPM_MID64
+#define VPM_MID64 256         // targets before the tail served in 64-target chunks
+#endif
+constexpr int kBulk = VPM_BULK, kTail32 = VPM_TAIL32, kMid64 = VPM_MID64;
+
+struct ChunkPlan {
+    int n_bulk, n_mid, c_bulk, c_mid, nchunks;
+};
+
+__device__ __forceinline__ ChunkPlan chunk_plan(int n)
+{
+    ChunkPlan c;
+    const int head = max(0, n - kTail32 - kMid64);
+    c.n_bulk = (head / kBulk) * kBulk;
+    c.n_mid = max(0, n - kTail32 - c.n_bulk);
+    c.c_bulk = c.n_bulk / kBulk;
+    c.c_mid = (c.n_mid + 63) / 64;
+    c.nchunks = c.c_bulk + c.c_mid + (n - c.n_bulk - c.n_mid + 31) / 32;
+    return c;
+}
+
+// Chunks are claimed from a counter that is never reset within a rollout: every warp makes
+// exactly one failing claim per step, so a step consumes nchunks + nwarps claims and every
+// thread can track the counter's base for the next step without a barrier.
 template <int KER>
-__device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, float2 *vel, int n)
+__device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, float2 *vel, int n,
+                              const ChunkPlan &cp, int claim_base)
 {
     const int lane = threadIdx.x & 31;
-    const int nchunks = (n + kChunk - 1) / kChunk;
     for (;;) {
         int c = 0;
-        if (lane == 0) c = atomicAdd(&w.chunk_next, 1);
+        if (lane == 0) c = atomicAdd(&w.chunk_next, 1) - claim_base;
         c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= nchunks) break;
-        const int base = c * kChunk, rem = n - base;
-        if (rem > 64)
-            old_pairs_chunk<KER, 4>(p, part, vel, n, base);
-        else if (rem > 32)
-            old_pairs_chunk<KER, 2>(p, part, vel, n, base);
-        else
-            old_pairs_chunk<KER, 1>(p, part, vel, n, base);
+        if (c >= cp.nchunks) break;
+        if (c < cp.c_bulk) {
+            old_pairs_chunk<KER, kBulk / 32>(p, part, vel, n, c * kBulk, n);
+        } else if (c < cp.c_bulk + cp.c_mid) {
+            const int base = cp.n_bulk + 64 * (c - cp.c_bulk);
+            const int lim = cp.n_bulk + cp.n_mid;
+            if (lim - base > 32)
+                old_pairs_chunk<KER, 2>(p, part, vel, n, base, lim);
+            else
+                old_pairs_chunk<KER, 1>(p, part, vel, n, base, lim);
+        } else {
+            const int base = cp.n_bulk + cp.n_mid + 32 * (c - cp.c_bulk - cp.c_mid);
+            old_pairs_chunk<KER, 1>(p, part, vel, n, base, n);
+        }
     }
 }
 
@@ -361,59 +480,109 @@ __device__ __forceinline__ void bound_terms_f32(const DevParams &p, const Work &
     }
 }
 
-// Adds the terms that need this step's Gamma_S to the old targets, forms the full sums of the
-// freshly shed particles n .. n1-1, and scales to velocities.
+// Full sums of the freshly shed particles n .. n1-1 (at most two; warp 0, right after the
+// solve, while the other warps are still on the old-old pairs), both targets in one pass:
+// lanes split the sources, partial sums are combined in binary64, lane f adds the bound terms
+// and the free stream for shed particle f.
 template <int KER>
-__device__ void finalize_f32(const DevParams &p, const Work &w, const float4 *part, float2 *vel,
-                             int n, int n1, double *probe_vel)
+__device__ void fresh_velocities_f32(const DevParams &p, Work &w, const float4 *part, int n, int n1)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nf = n1 - n;
+    if (nf <= 0) return;
+    const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    const float inv2pi = (float)kInv2Pi;
+    const float4 q[2] = {w.fresh[0], w.fresh[nf - 1]};
+    float su[2] = {0.f, 0.f}, cu[2] = {0.f, 0.f}, sw[2] = {0.f, 0.f}, cw[2] = {0.f, 0.f};
+    for (int j = lane; j < n1; j += 32) {
+        const float4 s = part[j];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const float dx = q[f].x - s.x, dz = q[f].y - s.y;
+            const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+            kahan_add(su[f], cu[f], -dz * g);
+            kahan_add(sw[f], cw[f], dx * g);
+        }
+    }
+    double du[2], dw[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+        du[f] = (double)su[f] - (double)cu[f];
+        dw[f] = (double)sw[f] - (double)cw[f];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            du[f] += __shfl_xor_sync(0xffffffffu, du[f], o);
+            dw[f] += __shfl_xor_sync(0xffffffffu, dw[f], o);
+        }
+    }
+    if (lane < nf) {
+        const float4 t = lane ? q[1] : q[0];
+        const double tu = lane ? du[1] : du[0], tw = lane ? dw[1] : dw[0];
+        float xl, zl;
+        unpack_lo(t.w, xl, zl);
+        float bu = 0.f, bw = 0.f;
+        bound_terms_f32(p, w, t.x, t.y, xl, zl, bu, bw);
+        w.fresh_vel[lane] = make_float2(fmaf((float)tu + bu, inv2pi, (float)p.u_inf_x),
+                                        fmaf((float)tw + bw, inv2pi, (float)p.u_inf_z));
+    }
+}
+
+// Phase C completion and phase D for one particle at a time: the old targets add the bound
+// terms and the freshly shed vortices (from their pre-advection copies) to their old-old sums;
+// every particle is then advected by explicit Euler (double-length positions) and decayed
+// exactly, Gamma <- Gamma exp(-gamma dt) (Eq. 17). Each record is read and written by the
+// thread that owns it, so no barrier separates the velocity from the advection.
+template <int KER>
+__device__ void finalize_advect_f32(const DevParams &p, Work &w, float4 *part, const float2 *vel,
+                                    int n, int n1, double *probe_vel)
+{
     const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
     const float inv2pi = (float)kInv2Pi;
     const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
-    for (int i = tid; i < n; i += (int)blockDim.x) {
-        const float4 q = part[i];
-        const float2 raw = vel[i];
+    const float dth = (float)p.dt, dtl = (float)(p.dt - (double)dth);
+    const float dch = (float)p.decay, dcl = (float)(p.decay - (double)dch);
+    const int nf = n1 - n;
+    bool bad = false;
+    for (int i = threadIdx.x; i < n1; i += (int)blockDim.x) {
+        float4 q;
+        float2 v;
         float xl, zl;
-        unpack_lo(q.w, xl, zl);
-        float bu = 0.f, bw = 0.f;
-        bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
-        for (int j = n; j < n1; ++j) {
-            const float4 s = part[j];
-            const float dx = q.x - s.x, dz = q.y - s.y;
-            const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
-            bu = fmaf(-dz, g, bu);
-            bw = fmaf(dx, g, bw);
-        }
-        const float u = fmaf(raw.x + bu, inv2pi, uix), v = fmaf(raw.y + bw, inv2pi, uiz);
-        vel[i] = make_float2(u, v);
-        if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
-    }
-    for (int i = n + warp; i < n1; i += (int)(blockDim.x >> 5)) {
-        const float4 q = part[i];
-        float su = 0.f, cu = 0.f, sw = 0.f, cw = 0.f;
-        for (int j = lane; j < n1; j += 32) {
-            const float4 s = part[j];
-            const float dx = q.x - s.x, dz = q.y - s.y;
-            const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
-            kahan_add(su, cu, -dz * g);
-            kahan_add(sw, cw, dx * g);
-        }
-        double du = (double)su - (double)cu, dw = (double)sw - (double)cw;
-        for (int o = 16; o > 0; o >>= 1) {
-            du += __shfl_xor_sync(0xffffffffu, du, o);
-            dw += __shfl_xor_sync(0xffffffffu, dw, o);
-        }
-        if (lane == 0) {
-            float xl, zl;
+        if (i < n) {
+            q = part[i];
+            const float2 raw = vel[i];
             unpack_lo(q.w, xl, zl);
             float bu = 0.f, bw = 0.f;
             bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
-            const float u = fmaf((float)du + bu, inv2pi, uix), v = fmaf((float)dw + bw, inv2pi, uiz);
-            vel[i] = make_float2(u, v);
-            if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
+            for (int f = 0; f < nf; ++f) {
+                const float4 s = w.fresh[f];
+                const float dx = q.x - s.x, dz = q.y - s.y;
+                const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+                bu = fmaf(-dz, g, bu);
+                bw = fmaf(dx, g, bw);
+            }
+            v = make_float2(fmaf(raw.x + bu, inv2pi, uix), fmaf(raw.y + bw, inv2pi, uiz));
+        } else {
+            q = w.fresh[i - n];
+            v = w.fresh_vel[i - n];
+            unpack_lo(q.w, xl, zl);
         }
+        if (probe_vel) { probe_vel[2 * i] = v.x; probe_vel[2 * i + 1] = v.y; }
+        bad |= !(isfinite(v.x) && isfinite(v.y));
+        const float ddx = fmaf(v.x, dth, fmaf(v.x, dtl, xl));
+        const float ddz = fmaf(v.y, dth, fmaf(v.y, dtl, zl));
+        float sx, ex, sz, ez;
+        two_sum(q.x, ddx, sx, ex);
+        two_sum(q.y, ddz, sz, ez);
+        q.x = sx;
+        q.y = sz;
+        q.z = fmaf(q.z, dcl, q.z * dch);
+        q.w = pack_lo(ex, ez);
+        part[i] = q;
     }
+    if (bad) atomicOr(&w.flag, (int)kStNonFinite);
 }
 
 template <int KER>
@@ -445,33 +614,7 @@ __device__ void convect_f64(const DevParams &p, const Work &w, const Part64 *par
     }
 }
 
-// Phase D: explicit Euler advection (double-length positions on the binary32 path) and the
-// exact decay Gamma <- Gamma exp(-gamma dt) of Eq. 17.
-__device__ void advect_f32(const DevParams &p, Work &w, float4 *part, const float2 *vel, int n)
-{
-    const float dth = (float)p.dt, dtl = (float)(p.dt - (double)dth);
-    const float dch = (float)p.decay, dcl = (float)(p.decay - (double)dch);
-    bool bad = false;
-    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) {
-        float4 q = part[i];
-        const float2 v = vel[i];
-        bad |= !(isfinite(v.x) && isfinite(v.y));
-        float xl, zl;
-        unpack_lo(q.w, xl, zl);
-        const float ddx = fmaf(v.x, dth, fmaf(v.x, dtl, xl));
-        const float ddz = fmaf(v.y, dth, fmaf(v.y, dtl, zl));
-        float sx, ex, sz, ez;
-        two_sum(q.x, ddx, sx, ex);
-        two_sum(q.y, ddz, sz, ez);
-        q.x = sx;
-        q.y = sz;
-        q.z = fmaf(q.z, dcl, q.z * dch);
-        q.w = pack_lo(ex, ez);
-        part[i] = q;
-    }
-    if (bad) atomicOr(&w.flag, (int)kStNonFinite);
-}
-
+// Phase D on the binary64 path: explicit Euler advection and the exact decay of Eq. 17.
 __device__ void advect_f64(const DevParams &p, Work &w, Part64 *part, const double2 *vel, int n)
 {
     bool bad = false;
@@ -525,60 +668,64 @@ __device__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int 
     return nn;
 }
 
-// One full step of one rollout. All threads call it; returns with the block synchronised.
+// One full step of one rollout. All threads call it with the same particle count n (updated
+// here) and chunk-claim base; returns with the block synchronised.
 template <class R, int KER>
 __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *part,
                           typename Store<R>::V *vel, double u_ctrl, const RolloutArgs &a,
-                          bool probe)
+                          bool probe, int &n, int &claim_base)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int n = w.n;
     int n1;
     if constexpr (sizeof(R) == 4) {
-        // warp 0: plate geometry, plate sums, surface solve, loads, glider, shedding;
-        // meanwhile (and afterwards for warp 0) every warp works on the old-old pair sums
+        // warp 0: plate geometry, plate sums, surface solve, loads, glider, shedding and the
+        // shed particles' velocities; meanwhile (and afterwards for warp 0) every warp works
+        // on the old-old pair sums
         if (warp == 0) {
             const int lane = tid & 31;
-            if (lane == 0) plate_geometry(p, w);
-            __syncwarp();
+            plate_geometry(p, w);
             if (lane < p.n_b) bound_point_f32(p, w, lane);
-            plate_sums<R, KER>(p, w, part, n, 0, 1);
+            plate_sums_f32<KER>(p, w, part, n);
             __syncwarp();
-            if (lane == 0) w.n = plate_solve<R>(p, w, part, n, u_ctrl);
-            __syncwarp();
+            const int m = plate_solve<R>(p, w, part, n, u_ctrl, 1);
+            if (lane == 0) w.n = m;
+            fresh_velocities_f32<KER>(p, w, part, n, m);
         }
-        old_pairs_f32<KER>(p, w, part, vel, n);
+        const ChunkPlan cp = chunk_plan(n);
+        old_pairs_f32<KER>(p, w, part, vel, n, cp, claim_base);
+        claim_base += cp.nchunks + (int)(blockDim.x >> 5);
         __syncthreads();
         n1 = w.n;
-        finalize_f32<KER>(p, w, part, vel, n, n1, probe ? a.probe_vel : nullptr);
+        if (probe) {
+            const int M = p.n_c + p.n_b;
+            if (a.probe_vt) for (int t = tid; t < 2 * M; t += (int)blockDim.x) a.probe_vt[t] = w.vt[t];
+            if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += (int)blockDim.x) a.probe_gs[t] = w.gs[t];
+            if (a.probe_fm && tid < 3) a.probe_fm[tid] = w.fm[tid];
+        }
+        finalize_advect_f32<KER>(p, w, part, vel, n, n1, probe ? a.probe_vel : nullptr);
     } else {
-        if (tid == 0) plate_geometry(p, w);
+        if (warp == 0) plate_geometry(p, w);
         __syncthreads();
-        plate_sums<R, KER>(p, w, part, n, 0, (int)(blockDim.x >> 5));
+        plate_sums_f64<KER>(p, w, part, n);
         __syncthreads();
-        if (tid == 0) w.n = plate_solve<R>(p, w, part, n, u_ctrl);
+        if (warp == 0) {
+            const int m = plate_solve<R>(p, w, part, n, u_ctrl, (int)(blockDim.x >> 5));
+            if (tid == 0) w.n = m;
+        }
         __syncthreads();
         n1 = w.n;
         convect_f64<KER>(p, w, part, vel, n1, probe ? a.probe_vel : nullptr);
-    }
-    if (probe) {
-        const int M = p.n_c + p.n_b;
-        if (a.probe_vt) for (int t = tid; t < 2 * M; t += (int)blockDim.x) a.probe_vt[t] = w.vt[t];
-        if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += (int)blockDim.x) a.probe_gs[t] = w.gs[t];
-        if (a.probe_fm && tid < 3) a.probe_fm[tid] = w.fm[tid];
-    }
-    __syncthreads();
-    if constexpr (sizeof(R) == 4)
-        advect_f32(p, w, part, vel, n1);
-    else
+        if (probe) {
+            const int M = p.n_c + p.n_b;
+            if (a.probe_vt) for (int t = tid; t < 2 * M; t += (int)blockDim.x) a.probe_vt[t] = w.vt[t];
+            if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += (int)blockDim.x) a.probe_gs[t] = w.gs[t];
+            if (a.probe_fm && tid < 3) a.probe_fm[tid] = w.fm[tid];
+        }
+        __syncthreads();
         advect_f64(p, w, part, vel, n1);
-    __syncthreads();
-    const int nm = merge_oldest<R>(p, part, n1);
-    if (tid == 0) {
-        w.n = nm;
-        w.chunk_next = 0;
     }
     __syncthreads();
+    n = merge_oldest<R>(p, part, n1);
 }
 
 template <class R>
@@ -647,13 +794,16 @@ __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P 
                             typename Store<R>::V *vel, int rid)
 {
     load_state<R>(a, w, part, rid);
+    int n = w.n, claim_base = 0;
     for (int k = 0; k < a.H; ++k) {
         const double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k]
                                     : a.u_const;
-        step_once<R, KER>(a.p, w, part, vel, u, a, a.H == 1);
+        step_once<R, KER>(a.p, w, part, vel, u, a, a.H == 1, n, claim_base);
         if (a.traj && threadIdx.x < 7)
             a.traj[((size_t)rid * a.H + k) * 7 + threadIdx.x] = w.xg[threadIdx.x];
     }
+    if (threadIdx.x == 0) w.n = n;
+    __syncthreads();
     if (a.out_part) store_state<R>(a, w, part, rid);
     finish<R>(a, w, part, rid);
 }
