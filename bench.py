@@ -401,6 +401,43 @@ def run_freefield(args):
         "clocks": clk.summary()}), flush=True)
 
 
+def run_alu(args):
+    """Measured ceilings of the binary32 pair kernels: FP32 FMA, MUFU rsqrt and ex2 rates, and the
+    rollout kernel's own pair loop (1, 2, 4 targets per lane) alone, 1 and 7 blocks per SM."""
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    V.probe_rate(V.PROBE_FFMA, 7)          # first-launch warm-up
+    with ClockSampler(0) as clk:
+        rates = {
+            "ffma_per_s": V.probe_rate(V.PROBE_FFMA, 7),
+            "mufu_rsqrt_per_s": V.probe_rate(V.PROBE_RSQRT, 7),
+            "mufu_ex2_per_s": V.probe_rate(V.PROBE_EX2, 7),
+        }
+        loop = {}
+        for name, pr in (("t1", V.PROBE_PAIRS_T1), ("t2", V.PROBE_PAIRS_T2), ("t4", V.PROBE_PAIRS_T4)):
+            for bps in (1, 7):
+                loop["%s_%dblk" % (name, bps)] = V.probe_rate(pr, bps)
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz") or PEAK_SM_MHZ
+    per_clk = lambda r: r / (N_SM * mhz * 1e6)
+    fp32_ops_per_pair = 8          # 2 FADD, 2 FMUL, 4 FFMA
+    ceiling = min(rates["ffma_per_s"] / fp32_ops_per_pair, rates["mufu_rsqrt_per_s"])
+    best = max(loop.values())
+    print(json.dumps({
+        "metric": "pair-loop ceiling (pair-interactions/s)", "value": best, "unit": "pair-interactions/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "throughput probes: 8 independent chains per thread, 128-thread blocks; "
+                               "pair loop over a 1024-particle field in shared memory"},
+        "unit_rates": rates,
+        "unit_rates_per_sm_per_clock": {k: per_clk(v) for k, v in rates.items()},
+        "pair_loop_rates": loop,
+        "issue_free_ceiling_pairs_per_s": ceiling,
+        "loop_fraction_of_issue_free_ceiling": best / ceiling,
+        "fp32_peak_tflops": fp32_peak_tflops(),
+        "clocks": clocks}), flush=True)
+
+
 def run_northstar(args):
     """Replan latency at K = 1024 rollouts x H = 100 steps with ~2000-particle fields (1900 -> 2100),
     persistent form against the one-rollout-per-launch form. The latter issues K x H single-block
@@ -621,7 +658,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
@@ -643,6 +680,8 @@ def main():
         run_uneven(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "alu":
+        run_alu(args)
     else:
         run_gpu(args)
 

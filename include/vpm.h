@@ -349,6 +349,31 @@ vpm_status vpm_server_destroy(vpm_server *server);
 vpm_status vpm_freefield_heun_noalloc(float *d_particles, int n, int kernel, double r_core,
                                       double dt, int steps, cudaStream_t stream);
 
+/*
+ * Throughput probe. The paper has no counterpart: it is a measurement aid that states, from
+ * this device, the ceiling the pair kernels run against. One timed launch of blocks_per_sm x
+ * (SM count) blocks of 128 threads writes to *h_rate:
+ *   VPM_PROBE_FFMA      binary32 fused multiply-adds per second (lane operations),
+ *   VPM_PROBE_RSQRT     MUFU reciprocal square roots per second,
+ *   VPM_PROBE_EX2       MUFU base-2 exponentials per second,
+ *   VPM_PROBE_PAIRS_T1/T2/T4  pair interactions per second of the rollout kernel's binary32
+ *                       pair loop (Vatistas kernel) with 1, 2 or 4 targets per lane, every block
+ *                       summing a 1024-particle field held in its shared memory.
+ * blocks_per_sm must lie in 1..7. The call allocates and frees its own device scratch, runs on
+ * the legacy default stream of the current device and synchronises it. Errors:
+ * VPM_ERR_INVALID for an unknown probe or block count, VPM_ERR_CUDA for a CUDA failure.
+ */
+typedef enum {
+    VPM_PROBE_FFMA = 0,
+    VPM_PROBE_RSQRT = 1,
+    VPM_PROBE_EX2 = 2,
+    VPM_PROBE_PAIRS_T1 = 3,
+    VPM_PROBE_PAIRS_T2 = 4,
+    VPM_PROBE_PAIRS_T4 = 5
+} vpm_probe;
+
+vpm_status vpm_probe_rate(int probe, int blocks_per_sm, double *h_rate);
+
 #ifdef __cplusplus
 }
 #endif

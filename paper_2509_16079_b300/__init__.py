@@ -83,6 +83,7 @@ _SIGNATURES = {
     "vpm_freefield_velocity": ([_VP, _I, _I, _D, _VP, _VP], _I),
     "vpm_freefield_heun": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
     "vpm_freefield_heun_noalloc": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
+    "vpm_probe_rate": ([_I, _I, C.POINTER(_D)], _I),
     "vpm_batch_create": ([C.POINTER(Params), _I, _VP, _VP, _VP, _I, C.POINTER(_VP), _VP], _I),
     "vpm_batch_destroy": ([_VP], _I),
     "vpm_batch_rollout": ([_VP, _I, _VP, _VP, _VP, _VP, _I, _VP], _I),
@@ -420,6 +421,17 @@ def mppi_perturb(mu, eps, out=None, stream=None):
     c = out if out is not None else torch.empty_like(eps)
     check(lib().mppi_perturb(ptr(mu), ptr(eps), K, H, ptr(c), stream_handle(stream)))
     return c
+
+
+PROBE_FFMA, PROBE_RSQRT, PROBE_EX2, PROBE_PAIRS_T1, PROBE_PAIRS_T2, PROBE_PAIRS_T4 = range(6)
+
+
+def probe_rate(probe: int, blocks_per_sm: int = 7) -> float:
+    """Measured device rate of one probe (see vpm_probe_rate): FP32 FMAs/s, MUFU results/s or
+    pair interactions/s of the rollout kernel's pair loop. Synchronises the device."""
+    r = C.c_double(0.0)
+    check(lib().vpm_probe_rate(int(probe), int(blocks_per_sm), C.byref(r)))
+    return r.value
 
 
 def freefield_velocity(particles, kernel: int, r_core: float, out=None, stream=None):

@@ -982,4 +982,38 @@ int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem)
 #undef VPM_OCC
 }
 
+// ------------------------------------------------------------------ pair-loop throughput probe
+
+template <int T>
+__global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) pair_probe_kernel(const float4 *src,
+                                                                            float2 *out, int n,
+                                                                            int reps, float rc4)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *part = reinterpret_cast<float4 *>(smem);
+    float2 *vel = reinterpret_cast<float2 *>(smem + sizeof(float4) * (size_t)n);
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) part[i] = src[i];
+    __syncthreads();
+    DevParams p = {};
+    p.rc4 = rc4;
+    const int warp = threadIdx.x >> 5, nwarps = (int)blockDim.x >> 5;
+    for (int r = 0; r < reps; ++r)
+        for (int base = 32 * T * warp; base < n; base += 32 * T * nwarps)
+            old_pairs_chunk<VPM_KERNEL_VATISTAS, T>(p, part, vel, n, base, n);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) out[(size_t)blockIdx.x * n + i] = vel[i];
+}
+
+cudaError_t launch_pair_probe(int t, int grid, int n, int reps, double r_core, const float4 *d_src,
+                              float2 *d_out, cudaStream_t s)
+{
+    const size_t smem = (size_t)n * (sizeof(float4) + sizeof(float2));
+    const float rc4 = (float)(r_core * r_core * r_core * r_core);
+    auto k = t == 4 ? pair_probe_kernel<4> : (t == 2 ? pair_probe_kernel<2> : pair_probe_kernel<1>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, s>>>(d_src, d_out, n, reps, rc4);
+    return cudaGetLastError();
+}
+
 }  // namespace vpm

@@ -46,5 +46,11 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
 cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, cudaStream_t s);
 // Resident blocks per SM of the persistent kernel for this configuration (0 if it cannot run).
 int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem);
+// Throughput probe of the binary32 pair loop (Vatistas kernel, core radius r_core): `grid`
+// blocks of 128 threads each load the n records of d_src into shared memory and form every
+// target's sum over all n sources `reps` times with t targets per lane (1, 2 or 4); block b
+// writes its raw sums to d_out[b n ...].
+cudaError_t launch_pair_probe(int t, int grid, int n, int reps, double r_core, const float4 *d_src,
+                              float2 *d_out, cudaStream_t s);
 
 }  // namespace vpm

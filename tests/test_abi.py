@@ -62,6 +62,10 @@ def test_host_side_rejections(vlib):
     assert vlib.mppi_weights(None, 4, 1.0, None, None) == V.VPM_ERR_INVALID
     assert vlib.vpm_rollout_batch(None, 1, 1, None, None, None, None, None, None, None) == V.VPM_ERR_INVALID
     assert b"null" in vlib.vpm_last_error()
+    r = C.c_double(0.0)
+    assert vlib.vpm_probe_rate(99, 1, C.byref(r)) == V.VPM_ERR_INVALID
+    assert vlib.vpm_probe_rate(V.PROBE_FFMA, 0, C.byref(r)) == V.VPM_ERR_INVALID
+    assert vlib.vpm_probe_rate(V.PROBE_FFMA, 8, C.byref(r)) == V.VPM_ERR_INVALID
 
 
 def test_no_silent_cpu_fallback(vlib):
