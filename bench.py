@@ -438,6 +438,49 @@ def run_alu(args):
         "clocks": clocks}), flush=True)
 
 
+def run_table1(args):
+    """The perch benchmark's shape (Table I): clean wake, merging above N_max = 60 particles, 80
+    steps at dt = 0.01, batch sizes 1 ... 1024; wall time of one batched rollout launch."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    p = dict(W.glider_params(), n_wake_max=60)
+    Hh = 80
+    root = V.State(p, np.zeros((0, 3)), W.GLIDER_X0, 62, V.FP32)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    rows = {}
+    with ClockSampler(0) as clk:
+        for K in (1, 128, 256, 512, 1024):
+            eps = torch.tensor(W.mppi_noise(40 + K, K, Hh, W.MPPI_SIGMA_U), device="cuda")
+            for _ in range(3):
+                root.rollout_batch(eps, want_final=False)
+            ts = []
+            for _ in range(20):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                out = root.rollout_batch(eps, want_final=False)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            assert bool(torch.isfinite(out["costs"]).all())
+            pairs = K * sum(min(2 * k, 60) * 17 + (min(2 * k, 60) + 2) * (min(2 * k, 60) + 2 + 8)
+                            for k in range(Hh))
+            rows[str(K)] = {"ms_p50": statistics.median(ts), "ms_min": min(ts),
+                            "pairs_per_s": pairs / (statistics.median(ts) / 1e3)}
+    paper = {"1": 8.0, "128": 10.3, "256": 12.2, "512": 16.3, "1024": 27.2}
+    print(json.dumps({
+        "metric": "batched rollout wall time (ms)", "value": rows["1024"]["ms_p50"], "unit": "ms",
+        "n_gpus": 1, "steps": 20, "higher_is_better": False, "dtype": "f32 pair sums (f64 plate work)",
+        "data": "synthetic",
+        "config": {"workload": "perch benchmark shape: clean wake, merging above 60 particles, 80 steps, "
+                               "dt 0.01, batch 1..1024", "l2": "flushed between timed launches (256 MB)"},
+        "by_batch": rows,
+        "paper_rtx5080_ms_context_only": paper,
+        "clocks": clk.summary()}), flush=True)
+
+
 def run_northstar(args):
     """Replan latency at K = 1024 rollouts x H = 100 steps with ~2000-particle fields (1900 -> 2100),
     persistent form against the one-rollout-per-launch form. The latter issues K x H single-block
@@ -658,7 +701,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
@@ -682,6 +725,8 @@ def main():
         run_serving(args)
     elif args.workload == "alu":
         run_alu(args)
+    elif args.workload == "table1":
+        run_table1(args)
     else:
         run_gpu(args)
 

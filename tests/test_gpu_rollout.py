@@ -88,7 +88,7 @@ def _binary32_envelope(ora, p, parts, xg, u, checkpoints, cap):
     return out
 
 
-@pytest.mark.parametrize("case", ["c1", "c2"])
+@pytest.mark.parametrize("case", ["c1", "c2", "table1"])
 def test_fp32_within_model_sensitivity(ora, case):
     """On the chaotic workloads the binary32 path is held to the envelope of the model's own
     sensitivity: after H steps its distance from the FP64 oracle must be below
@@ -100,11 +100,17 @@ def test_fp32_within_model_sensitivity(ora, case):
         parts, xg, cap = W.plate_c1_initial(0)
         u = np.zeros(200)
         checkpoints = [50, 100, 200]
-    else:
+    elif case == "c2":
         p, parts, xg, eps = W.mppi_c2(0, K=1, H=100, n=1000)
         u = eps[0].astype(np.float64)
         cap = 1200
         checkpoints = [25, 50, 100]
+    else:
+        p = dict(W.glider_params(), n_wake_max=60)
+        parts, xg = np.zeros((0, 3)), np.array(W.GLIDER_X0)
+        u = W.mppi_noise(11, 1, 80, W.MPPI_SIGMA_U)[0].astype(np.float64)
+        cap = 62
+        checkpoints = [30, 60, 80]
     env = _binary32_envelope(ora, p, parts, xg, u, checkpoints, cap)
     for H in checkpoints:
         ref, spread = env[H]
@@ -122,6 +128,19 @@ def test_fp64_merging_and_gate(ora):
         q = dict(p, **over)
         res = _run_gpu(V, torch, q, field, xg0, eps, V.FP64, 300 + 2 * 60)
         _check_rollouts(ora, q, field, xg0, eps, res, [0, 3], POS_TOL, 1e-6, 1e-6)
+
+
+def test_table1_shape_merging_dominated_fp64(ora):
+    """The perch benchmark's shape: clean wake, at most 60 particles (merging every step after
+    the 30th), 80 steps, binary64 path pointwise against the oracle. (The binary32 path on
+    this shape is held to the model's sensitivity envelope below.)"""
+    torch, V = cuda()
+    p = dict(W.glider_params(), n_wake_max=60)
+    field = np.zeros((0, 3))
+    eps = W.mppi_noise(11, 8, 80, W.MPPI_SIGMA_U)
+    res = _run_gpu(V, torch, p, field, np.array(W.GLIDER_X0), eps, V.FP64, 62)
+    assert (res["count"] == 60).all()
+    _check_rollouts(ora, p, field, np.array(W.GLIDER_X0), eps, res, [0, 5], 1e-9, 1e-9, 1e-9)
 
 
 def test_batch_invariance_and_per_launch_form():

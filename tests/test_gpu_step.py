@@ -30,6 +30,9 @@ def _cases():
         "nb2": (dict(c2, n_b=2), W.background_field(4, 300), np.array(W.GLIDER_X0), [0, 7, 30]),
         "nb32": (dict(c2, n_b=32), W.background_field(5, 300), np.array(W.GLIDER_X0), [0, 7, 30]),
         "empty_wake": (c2, np.zeros((0, 3)), np.array(W.GLIDER_X0), [0, 1, 2]),
+        # the perch benchmark's shape (Table I): clean start, merging above 60 particles
+        "table1_merging": (dict(c2, n_wake_max=60), np.zeros((0, 3)), np.array(W.GLIDER_X0),
+                           [0, 29, 30, 31, 55, 79]),
     }
 
 
