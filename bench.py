@@ -481,6 +481,50 @@ def run_table1(args):
         "clocks": clk.summary()}), flush=True)
 
 
+def run_policy(args):
+    """Policy construction of §IV-B at the NMPC settings of §V-A (batch 256, 77-step nominal
+    trajectory, perch wake with merging above 60 particles): perturbed rollouts with their
+    trajectories, least-squares Jacobians and TVLQR gains, each timed with CUDA events."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    p = dict(W.glider_params(), n_wake_max=60)
+    K, Hh = 256, 77
+    root = V.State(p, np.zeros((0, 3)), W.GLIDER_X0, 62, V.FP32)
+    ubar = W.mppi_noise(51, 1, Hh, 2.0)[0]
+    x0, u = W.policy_samples(52, K, W.GLIDER_X0, ubar)
+    d_x0, d_u, d_ub = (torch.tensor(a, device="cuda") for a in (x0, u, ubar))
+    nom = root.rollout_batch(d_ub[None, :], want_traj=True)
+    xbar = torch.cat([torch.tensor([W.GLIDER_X0], dtype=torch.float64, device="cuda"), nom["traj"][0]])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    times = {"rollouts": [], "least_squares": [], "tvlqr": [], "total": []}
+    with ClockSampler(0) as clk:
+        for it in range(args.warmup + args.steps):
+            ev[0].record()
+            out = root.rollout_batch(d_u, want_final=False, want_traj=True, x0=d_x0)
+            ev[1].record()
+            A, B, info = V.ls_jacobians(d_x0, out["traj"], d_u, xbar, d_ub, p["dt"])
+            ev[2].record()
+            g, s0 = V.tvlqr(A, B, p["dt"], W.TVLQR_QC, W.TVLQR_QF, W.TVLQR_RC)
+            ev[3].record()
+            ev[3].synchronize()
+            if it >= args.warmup:
+                times["rollouts"].append(ev[0].elapsed_time(ev[1]))
+                times["least_squares"].append(ev[1].elapsed_time(ev[2]))
+                times["tvlqr"].append(ev[2].elapsed_time(ev[3]))
+                times["total"].append(ev[0].elapsed_time(ev[3]))
+    assert not bool(info.any()) and bool(torch.isfinite(g).all())
+    med = {k: statistics.median(v) for k, v in times.items()}
+    print(json.dumps({
+        "metric": "policy construction time (ms)", "value": med["total"], "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "dtype": "f32 pair sums (f64 plate work, least squares and Riccati in f64)", "data": "synthetic",
+        "config": {"workload": "policy synthesis: K=256 perturbed rollouts x 77 steps (perch wake, merging "
+                               "above 60 particles), least squares per step, TVLQR with the weights of §V-A"},
+        "median_ms": med, "paper_ms_context_only": 9.0, "clocks": clk.summary()}), flush=True)
+
+
 def run_northstar(args):
     """Replan latency at K = 1024 rollouts x H = 100 steps with ~2000-particle fields (1900 -> 2100),
     persistent form against the one-rollout-per-launch form. The latter issues K x H single-block
@@ -701,7 +745,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1", "policy"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
@@ -727,6 +771,8 @@ def main():
         run_alu(args)
     elif args.workload == "table1":
         run_table1(args)
+    elif args.workload == "policy":
+        run_policy(args)
     else:
         run_gpu(args)
 

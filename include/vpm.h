@@ -173,6 +173,52 @@ vpm_status vpm_rollout_batch(const vpm_state *root, int K, int H, const float *d
                              double *d_field, int *d_count, cudaStream_t stream);
 
 /*
+ * vpm_rollout_batch with a separate initial glider state per rollout: d_x0[K*7] (binary64,
+ * row i = rollout i) replaces the root's glider state; the wake and the previous circulations
+ * are the root's. These are the perturbed initial states X^0 of the policy synthesis of §IV-B.
+ * Errors as vpm_rollout_batch, and VPM_ERR_INVALID for a null d_x0.
+ */
+vpm_status vpm_rollout_batch_x0(const vpm_state *root, int K, int H, const double *d_x0,
+                                const float *d_controls, float *d_costs, double *d_final_glider,
+                                double *d_traj, double *d_field, int *d_count,
+                                cudaStream_t stream);
+
+/*
+ * Least-squares synthesis of the glider's time-varying Jacobians from perturbed rollouts
+ * (§IV-B, the least-squares problem for df/dx, df/du). For each step k < H:
+ *   rows i < K:  regressors (x^i_k - xbar_k) at (theta, phi, xdot, zdot, thetadot) and
+ *                u^i_k - ubar_k;  targets the deviation of the accelerations
+ *                (xddot, zddot, thetaddot) from the nominal, the derivative of every trajectory
+ *                being its explicit-Euler increment (x_{k+1} - x_k) / dt;
+ *   solution:    A_hat_k (3 x 5) and B_hat_k (3 x 1), the unknown blocks of A_k and B_k.
+ * Inputs (device, binary64 unless stated): d_x0[K*7] initial states x^i_0, d_traj[K*H*7] the
+ * states after every step (as written by vpm_rollout_batch_x0), d_controls[K*H] binary32 the
+ * rollouts' controls, d_xbar[(H+1)*7] nominal states, d_ubar[H] binary32 nominal controls.
+ * Outputs: d_ahat[H*15] (row-major 3 x 5 per step), d_bhat[H*3], and d_info[H] (or null):
+ * 0, or 1 where the normal equations are singular (that step's outputs are NaN). Solved in
+ * binary64 by the normal equations with column equilibration and Cholesky factorisation.
+ * Errors: VPM_ERR_INVALID (K < 6, H < 1, dt <= 0, a null input or output), VPM_ERR_CUDA.
+ */
+vpm_status vpm_ls_jacobians(int K, int H, double dt, const double *d_x0, const double *d_traj,
+                            const float *d_controls, const double *d_xbar, const float *d_ubar,
+                            double *d_ahat, double *d_bhat, int *d_info, cudaStream_t stream);
+
+/*
+ * TVLQR gains of §IV-B from identified Jacobians: A_k, B_k are assembled from A_hat_k, B_hat_k
+ * with the known structure (kinematic rows on the velocity columns, phidot = u), discretised by
+ * explicit Euler (I + dt A_k, dt B_k), and the discrete Riccati recursion runs backwards from
+ * S_H = Q_f with S_k formed from S_{k+1}; the gain is
+ *   H_k = (R_c + B_k' S_{k+1} B_k)^-1 B_k' S_{k+1} A_k,   u_k = ubar_k - H_k (x_k - xbar_k).
+ * h_qc[7], h_qf[7]: host diagonals of Q_c and Q_f; rc > 0 the scalar R_c. Outputs (device,
+ * binary64): d_gains[H*7], d_s0[49] (S_0 row-major) or null. One warp, binary64.
+ * Errors: VPM_ERR_INVALID (H < 1, dt <= 0, rc <= 0, null or non-finite weights, null gains),
+ * VPM_ERR_CUDA.
+ */
+vpm_status vpm_tvlqr(int H, double dt, const double *d_ahat, const double *d_bhat,
+                     const double *h_qc, const double *h_qf, double rc, double *d_gains,
+                     double *d_s0, cudaStream_t stream);
+
+/*
  * Same results as vpm_rollout_batch computed in the plain one-rollout-per-launch form: every
  * step of every rollout is its own single-block launch (H x K launches) and each rollout's
  * field lives in global memory between launches. Kept as the comparison baseline for the

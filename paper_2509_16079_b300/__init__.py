@@ -76,6 +76,9 @@ _SIGNATURES = {
     "vpm_state_load": ([_VP, _VP, C.c_size_t, _VP], _I),
     "vpm_step": ([_VP, _D, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_rollout_batch": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_rollout_batch_x0": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_ls_jacobians": ([_I, _I, _D, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_tvlqr": ([_I, _D, _VP, _VP, _VP, _VP, _D, _VP, _VP, _VP], _I),
     "vpm_rollout_batch_per_launch": ([_VP, _I, _I, _VP, _VP, _VP, _VP], _I),
     "mppi_weights": ([_VP, _I, _F, _VP, _VP], _I),
     "mppi_update": ([_VP, _VP, _I, _I, _VP, _VP], _I),
@@ -221,8 +224,9 @@ class State:
         return out
 
     def rollout_batch(self, controls, want_final: bool = True, want_traj: bool = False,
-                      want_field: bool = False, costs=None, stream=None):
-        """K rollouts of H steps under controls (K, H) float32 CUDA tensor."""
+                      want_field: bool = False, costs=None, stream=None, x0=None):
+        """K rollouts of H steps under controls (K, H) float32 CUDA tensor; x0 (K, 7) float64
+        CUDA tensor gives each rollout its own initial glider state (else the root's)."""
         import torch
         controls = _dev_tensor(controls, torch.float32)
         K, H = controls.shape
@@ -235,10 +239,19 @@ class State:
         if want_field:
             out["field"] = torch.zeros((K, self.capacity, 3), dtype=torch.float64, device=dev)
             out["count"] = torch.zeros(K, dtype=torch.int32, device=dev)
-        check(lib().vpm_rollout_batch(self._h, K, H, ptr(controls), ptr(out["costs"]),
-                                      ptr(out.get("final_glider")), ptr(out.get("traj")),
-                                      ptr(out.get("field")), ptr(out.get("count")),
-                                      stream_handle(stream)))
+        if x0 is not None:
+            x0 = _dev_tensor(x0, torch.float64)
+            if tuple(x0.shape) != (K, 7):
+                raise ValueError("x0 must be (K, 7)")
+            check(lib().vpm_rollout_batch_x0(self._h, K, H, ptr(x0), ptr(controls), ptr(out["costs"]),
+                                             ptr(out.get("final_glider")), ptr(out.get("traj")),
+                                             ptr(out.get("field")), ptr(out.get("count")),
+                                             stream_handle(stream)))
+        else:
+            check(lib().vpm_rollout_batch(self._h, K, H, ptr(controls), ptr(out["costs"]),
+                                          ptr(out.get("final_glider")), ptr(out.get("traj")),
+                                          ptr(out.get("field")), ptr(out.get("count")),
+                                          stream_handle(stream)))
         return out
 
     def rollout_batch_per_launch(self, controls, stream=None):
@@ -421,6 +434,42 @@ def mppi_perturb(mu, eps, out=None, stream=None):
     c = out if out is not None else torch.empty_like(eps)
     check(lib().mppi_perturb(ptr(mu), ptr(eps), K, H, ptr(c), stream_handle(stream)))
     return c
+
+
+def ls_jacobians(x0, traj, controls, xbar, ubar, dt: float, stream=None):
+    """Least-squares Jacobian blocks of §IV-B (see vpm_ls_jacobians). x0 (K, 7), traj (K, H, 7),
+    xbar (H + 1, 7) float64 and controls (K, H), ubar (H,) float32 CUDA tensors.
+    Returns A_hat (H, 3, 5), B_hat (H, 3) float64 and info (H,) int32 (1: singular step)."""
+    import torch
+    x0 = _dev_tensor(x0, torch.float64)
+    traj = _dev_tensor(traj, torch.float64)
+    controls = _dev_tensor(controls, torch.float32)
+    xbar = _dev_tensor(xbar, torch.float64)
+    ubar = _dev_tensor(ubar, torch.float32)
+    K, H = controls.shape
+    dev = controls.device
+    ahat = torch.empty((H, 3, 5), dtype=torch.float64, device=dev)
+    bhat = torch.empty((H, 3), dtype=torch.float64, device=dev)
+    info = torch.empty(H, dtype=torch.int32, device=dev)
+    check(lib().vpm_ls_jacobians(K, H, float(dt), ptr(x0), ptr(traj), ptr(controls), ptr(xbar),
+                                 ptr(ubar), ptr(ahat), ptr(bhat), ptr(info), stream_handle(stream)))
+    return ahat, bhat, info
+
+
+def tvlqr(ahat, bhat, dt: float, qc, qf, rc: float, stream=None):
+    """TVLQR gains of §IV-B (see vpm_tvlqr). Returns gains (H, 7) and S_0 (7, 7) float64."""
+    import torch
+    ahat = _dev_tensor(ahat, torch.float64)
+    bhat = _dev_tensor(bhat, torch.float64)
+    H = ahat.shape[0]
+    qc = np.ascontiguousarray(qc, np.float64)
+    qf = np.ascontiguousarray(qf, np.float64)
+    gains = torch.empty((H, 7), dtype=torch.float64, device=ahat.device)
+    s0 = torch.empty((7, 7), dtype=torch.float64, device=ahat.device)
+    check(lib().vpm_tvlqr(H, float(dt), ptr(ahat), ptr(bhat), qc.ctypes.data_as(C.c_void_p),
+                          qf.ctypes.data_as(C.c_void_p), float(rc), ptr(gains), ptr(s0),
+                          stream_handle(stream)))
+    return gains, s0
 
 
 PROBE_FFMA, PROBE_RSQRT, PROBE_EX2, PROBE_PAIRS_T1, PROBE_PAIRS_T2, PROBE_PAIRS_T4 = range(6)

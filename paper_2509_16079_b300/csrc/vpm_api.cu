@@ -531,9 +531,9 @@ extern "C" vpm_status vpm_step(vpm_state *s, double u, double *d_fm, double *d_g
     return VPM_OK;
 }
 
-extern "C" vpm_status vpm_rollout_batch(const vpm_state *s, int K, int H, const float *d_controls,
-                                        float *d_costs, double *d_final_glider, double *d_traj,
-                                        double *d_field, int *d_count, cudaStream_t stream)
+static vpm_status rollout_batch(const vpm_state *s, int K, int H, const double *d_x0,
+                                const float *d_controls, float *d_costs, double *d_final_glider,
+                                double *d_traj, double *d_field, int *d_count, cudaStream_t stream)
 {
     if (!s || !d_controls || !d_costs) return fail(VPM_ERR_INVALID, "null argument");
     if (K < 1 || H < 1) return fail(VPM_ERR_INVALID, "K and H must be positive");
@@ -544,12 +544,31 @@ extern "C" vpm_status vpm_rollout_batch(const vpm_state *s, int K, int H, const 
     base_args(s, a);
     a.H = H; a.K = K;
     a.cap = (int)(need > 0 ? need : 1);
+    a.x0 = d_x0;
     a.controls = d_controls; a.ctrl_stride = H;
     a.costs = d_costs; a.final_glider = d_final_glider; a.traj = d_traj;
     a.field = d_field; a.field_cap = s->capacity; a.count = d_count;
     cudaError_t e = launch_rollout(s->params.precision, a, K, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vpm_rollout_batch launch");
     return VPM_OK;
+}
+
+extern "C" vpm_status vpm_rollout_batch(const vpm_state *s, int K, int H, const float *d_controls,
+                                        float *d_costs, double *d_final_glider, double *d_traj,
+                                        double *d_field, int *d_count, cudaStream_t stream)
+{
+    return rollout_batch(s, K, H, nullptr, d_controls, d_costs, d_final_glider, d_traj, d_field,
+                         d_count, stream);
+}
+
+extern "C" vpm_status vpm_rollout_batch_x0(const vpm_state *s, int K, int H, const double *d_x0,
+                                           const float *d_controls, float *d_costs,
+                                           double *d_final_glider, double *d_traj,
+                                           double *d_field, int *d_count, cudaStream_t stream)
+{
+    if (!d_x0) return fail(VPM_ERR_INVALID, "null initial states");
+    return rollout_batch(s, K, H, d_x0, d_controls, d_costs, d_final_glider, d_traj, d_field,
+                         d_count, stream);
 }
 
 // One-rollout-per-launch comparison form: the field of every rollout lives in global memory

@@ -736,7 +736,7 @@ __device__ void load_state(const RolloutArgs &a, Work &w, typename Store<R>::P *
     const P *rp = static_cast<const P *>(a.root_part) + off;
     const int n = a.root_n[(a.root_stride || a.root_offset) ? rid : 0];
     for (int i = threadIdx.x; i < n; i += (int)blockDim.x) part[i] = rp[i];
-    const double *g = a.root_glider + (size_t)rid * a.state_stride;
+    const double *g = a.x0 ? a.x0 + (size_t)rid * 7 : a.root_glider + (size_t)rid * a.state_stride;
     const double *h = a.root_hist + (size_t)rid * a.state_stride;
     if (threadIdx.x < 7) w.xg[threadIdx.x] = g[threadIdx.x];
     if (threadIdx.x < a.p.n_b + 2) w.hist[threadIdx.x] = h[threadIdx.x];

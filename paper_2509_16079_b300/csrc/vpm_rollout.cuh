@@ -37,6 +37,8 @@ struct RolloutArgs {
     const int *order;
     int *counter;
     int n_items;
+    // per-rollout initial glider states (K x 7, overrides root_glider; null: the root's)
+    const double *x0;
 };
 
 size_t rollout_smem_bytes(int precision, int cap);

@@ -171,3 +171,36 @@ def poisson_arrivals(seed: int, rate_hz: float, duration_s: float, n_streams: in
 
 def request_sizes(seed: int, n: int, choices=(256, 1024, 4096)) -> np.ndarray:
     return _rng(seed).choice(np.asarray(choices), n)
+
+
+# ------------------------------------------------------------------ tracking policy (§IV-B)
+
+# TVLQR weights of the experiments (§V-A): diagonals of Q_c and Q_f, and R_c.
+TVLQR_QC = (0.1, 0.1, 5.0, 0.1, 0.1, 0.1, 5.0)
+TVLQR_QF = (400.0, 400.0, 10.0, 1.0, 1.0, 1.0, 1.0)
+TVLQR_RC = 0.01
+# Perturbation scales of the synthesis rollouts (the paper tuned its covariances by sweeps and
+# does not print them; these are this build's choice): initial state (x, z, theta, phi, xdot,
+# zdot, thetadot) and elevator rate.
+POLICY_SIGMA_X = (0.01, 0.01, 0.01, 0.01, 0.05, 0.05, 0.05)
+POLICY_SIGMA_U = 1.0
+
+
+def policy_samples(seed: int, K: int, x0bar, ubar, sigma_x=POLICY_SIGMA_X, sigma_u=POLICY_SIGMA_U):
+    """Perturbed initial states x0[K, 7] ~ N(x0bar, diag(sigma_x^2)) (float64) and control
+    trajectories u[K, H] ~ N(ubar, sigma_u^2) rounded to float32 once."""
+    r = _rng(seed)
+    x0 = np.asarray(x0bar, np.float64)[None, :] + r.normal(0.0, 1.0, (K, 7)) * np.asarray(sigma_x)
+    ubar = np.asarray(ubar, np.float64)
+    u = (ubar[None, :] + r.normal(0.0, sigma_u, (K, len(ubar)))).astype(np.float32)
+    return x0, u
+
+
+def policy_random_data(seed: int, K: int, H: int):
+    """Unstructured inputs of the least-squares synthesis (for comparing implementations of a
+    pure function): x0 (K, 7), traj (K, H, 7), xbar (H + 1, 7) float64, controls (K, H) and
+    ubar (H,) float32."""
+    r = _rng(seed)
+    return (r.normal(0.0, 1.0, (K, 7)), r.normal(0.0, 1.0, (K, H, 7)),
+            r.normal(0.0, 1.0, (K, H)).astype(np.float32), r.normal(0.0, 1.0, (H + 1, 7)),
+            r.normal(0.0, 1.0, H).astype(np.float32))
