@@ -104,3 +104,23 @@ def tvlqr(Ahat, Bhat, dt, qc, qf, rc):
 def policy_control(gains, xbar, ubar, x, k):
     """Control of the tracking policy at step k: u^d_k - H_k (x - x^d_k)."""
     return float(ubar[k]) - float(np.asarray(gains)[k] @ (np.asarray(x, np.float64) - np.asarray(xbar)[k]))
+
+
+def rollout_closed_loop(params, parts, x0, gains, xbar, ubar, offset, H, capacity=None,
+                        controls=None, gb_prev=None, glev_prev=0.0, has_prev=0):
+    """One rollout of H steps under the tracking policy: at step k the control is
+    ubar_j - H_j . (x_k - xbar_j), j = offset + k (plus controls[k] if given), x_k the rollout's
+    own glider state. Returns dict(xg, cost, traj, state) with the final oracle State."""
+    from . import State, terminal_cost
+    parts = np.asarray(parts, np.float64).reshape(-1, 3)
+    cap = capacity if capacity is not None else len(parts) + 2 * H
+    s = State(params, parts, x0, cap, gb_prev, glev_prev, has_prev)
+    traj = np.zeros((H, STATE))
+    for k in range(H):
+        j = offset + k
+        u = float(ubar[j]) - float(np.asarray(gains[j]) @ (s.xg - np.asarray(xbar[j])))
+        if controls is not None:
+            u += float(controls[k])
+        s.step(u)
+        traj[k] = s.xg
+    return dict(xg=s.xg.copy(), cost=terminal_cost(params, s.xg), traj=traj, state=s)

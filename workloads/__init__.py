@@ -204,3 +204,18 @@ def policy_random_data(seed: int, K: int, H: int):
     return (r.normal(0.0, 1.0, (K, 7)), r.normal(0.0, 1.0, (K, H, 7)),
             r.normal(0.0, 1.0, (K, H)).astype(np.float32), r.normal(0.0, 1.0, (H + 1, 7)),
             r.normal(0.0, 1.0, H).astype(np.float32))
+
+
+def nmpc_noise(seed: int, n_plans: int, iterations: int, K: int, N: int,
+               sigma_mppi: float = MPPI_SIGMA_U, sigma_x=POLICY_SIGMA_X, sigma_u=POLICY_SIGMA_U):
+    """Random draws of a closed-loop run, per plan: MPPI perturbations eps (iterations, K, N)
+    ~ N(0, sigma_mppi^2) (binary32), synthesis initial-state perturbations xi (K, 7) ~
+    N(0, diag(sigma_x^2)) and control perturbations zeta (K, N) ~ N(0, sigma_u^2) (binary32)."""
+    r = _rng(seed)
+    out = []
+    for _ in range(n_plans):
+        eps = r.normal(0.0, sigma_mppi, (iterations, K, N)).astype(np.float32)
+        xi = r.normal(0.0, 1.0, (K, 7)) * np.asarray(sigma_x)
+        zeta = r.normal(0.0, sigma_u, (K, N)).astype(np.float32)
+        out.append((eps, xi, zeta))
+    return out
