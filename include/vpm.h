@@ -128,6 +128,29 @@ vpm_status vpm_state_set_history(vpm_state *state, const double *h_gb_prev, doub
 vpm_status vpm_state_read(const vpm_state *state, double *h_particles, int *n_out,
                           double *h_glider7, double *h_hist, cudaStream_t stream);
 
+/* Replaces the glider state (x, z, theta, phi, xdot, zdot, thetadot) by h_x7, e.g. with an
+ * observed one (the tracking instance of §IV-C follows the observed rigid-body state).
+ * Synchronises `stream`. Errors: VPM_ERR_INVALID (null), VPM_ERR_NONFINITE. */
+vpm_status vpm_state_set_glider(vpm_state *state, const double *h_x7, cudaStream_t stream);
+
+/* Copies the glider state to h_x7 (synchronises `stream`). */
+vpm_status vpm_state_get_glider(const vpm_state *state, double *h_x7, cudaStream_t stream);
+
+/* Device-side copy of src (particles, count, glider state, previous circulations) into dst,
+ * asynchronous on `stream`. Both states must have the same precision and n_b, and dst's
+ * capacity must hold src's particles. Errors: VPM_ERR_INVALID. */
+vpm_status vpm_state_copy(vpm_state *dst, const vpm_state *src, cudaStream_t stream);
+
+/*
+ * Advances the state in place by `steps` steps under the tracking policy of §IV-B: at step k
+ * the control is ubar_j - H_j . (x_k - xbar_j), j = offset + k, x_k the state's own glider
+ * state (one launch; the projection over the replanning time of §IV-C). Policy arrays as in
+ * vpm_rollout_batch_policy. Errors: VPM_ERR_INVALID, VPM_ERR_CAPACITY, VPM_ERR_CUDA.
+ */
+vpm_status vpm_state_advance_policy(vpm_state *state, int steps, const double *d_gains,
+                                    const double *d_xbar, const float *d_ubar, int offset,
+                                    cudaStream_t stream);
+
 /* Reads and clears the state's latched device error word (synchronises `stream`). */
 vpm_status vpm_state_status(vpm_state *state, cudaStream_t stream);
 
@@ -182,6 +205,22 @@ vpm_status vpm_rollout_batch_x0(const vpm_state *root, int K, int H, const doubl
                                 const float *d_controls, float *d_costs, double *d_final_glider,
                                 double *d_traj, double *d_field, int *d_count,
                                 cudaStream_t stream);
+
+/*
+ * Closed-loop rollouts under the tracking policy of §IV-B: at step k of rollout i the control is
+ *   u = ubar_j - H_j . (x_k - xbar_j),  j = offset + k  (+ d_controls[i*H + k] if given),
+ * with x_k the rollout's own glider state. d_gains[(offset+H)*7], d_xbar[(offset+H)*7] (binary64)
+ * and d_ubar[offset+H] (binary32) hold the policy (as from vpm_tvlqr and the nominal
+ * trajectory); d_x0[K*7] per-rollout initial states or null (the root's). Outputs as
+ * vpm_rollout_batch. Used to project the state over the replanning time and to evaluate a policy
+ * over perturbed initial conditions. Errors: VPM_ERR_INVALID (null policy or costs, K, H < 1,
+ * offset < 0), VPM_ERR_CAPACITY, VPM_ERR_CUDA.
+ */
+vpm_status vpm_rollout_batch_policy(const vpm_state *root, int K, int H, const double *d_x0,
+                                    const double *d_gains, const double *d_xbar,
+                                    const float *d_ubar, int offset, const float *d_controls,
+                                    float *d_costs, double *d_final_glider, double *d_traj,
+                                    cudaStream_t stream);
 
 /*
  * Least-squares synthesis of the glider's time-varying Jacobians from perturbed rollouts
@@ -394,6 +433,70 @@ vpm_status vpm_server_destroy(vpm_server *server);
  */
 vpm_status vpm_freefield_heun_noalloc(float *d_particles, int n, int kernel, double r_core,
                                       double dt, int steps, cudaStream_t stream);
+
+/*
+ * Feedback NMPC of §IV-C over a manoeuvre of `horizon` steps. A tracking instance of the model
+ * (created from h_particles, h_x0) follows the observed glider state. At creation a plan runs
+ * from the initial state; then every `replan_every` steps (t > 0, t + latency < horizon, while
+ * draws remain) a plan starts from a copy of the tracking instance with the observed glider
+ * state, projected `latency` steps ahead under the current policy. A plan is `iterations` MPPI
+ * reweightings (Eq. 25) of `rollouts` rollouts over the remaining steps, warm-started from the
+ * previous nominal controls, and the least-squares / TVLQR synthesis (§IV-B) around the new
+ * nominal; its policy takes effect `latency` steps after the replan started.
+ * threaded = 0: the plan runs inside vpm_nmpc_control (deterministic);
+ * threaded = 1: a planning thread with its own stream runs it while control continues (the
+ *               two-thread split of §IV-C); a replan that falls due while the planner is still
+ *               busy is skipped.
+ */
+typedef struct {
+    int horizon;          /* N: steps of the manoeuvre */
+    int replan_every;     /* P: steps between replans */
+    int latency;          /* L: projection steps (the replanning time) */
+    int rollouts;         /* K: MPPI and synthesis rollouts per plan (>= 6) */
+    int iterations;       /* MPPI iterations per plan */
+    float lambda;         /* MPPI temperature */
+    double qc[7], qf[7];  /* TVLQR weights (diagonals) */
+    double rc;            /* TVLQR control weight */
+    int threaded;
+} vpm_nmpc_config;
+
+typedef struct vpm_nmpc vpm_nmpc;
+
+/*
+ * Random draws are inputs (host arrays, copied): for plan p < n_plans (plan 0 is the initial
+ * one), MPPI perturbations h_eps[p][iterations][rollouts][horizon] (binary32; a plan from step t0
+ * uses the first horizon - t0 columns), synthesis initial-state perturbations
+ * h_xi[p][rollouts][7] and control perturbations h_zeta[p][rollouts][horizon] (binary32).
+ * h_mu0[horizon]: initial nominal controls. The model's precision is params->precision.
+ * Errors: VPM_ERR_INVALID (null, horizon < 2, rollouts < 6, lambda or rc <= 0, ...), those of
+ * vpm_state_create, VPM_ERR_SINGULAR (a least-squares step singular), VPM_ERR_OOM,
+ * VPM_ERR_CUDA.
+ */
+vpm_status vpm_nmpc_create(const vpm_nmpc_config *cfg, const vpm_params *params,
+                           const double *h_particles, int n, int capacity, const double *h_x0,
+                           const float *h_mu0, int n_plans, const float *h_eps,
+                           const double *h_xi, const float *h_zeta, vpm_nmpc **out);
+
+/*
+ * Control step t (0 <= t < horizon, called in order) with the observed glider state h_x_obs[7]:
+ * starts a replan if one is due, installs a finished plan whose first step has come, writes the
+ * control *h_u = ubar_t - H_t (x_obs - xbar_t), and advances the tracking instance by one step
+ * under it from the observed state. Errors: VPM_ERR_INVALID, and any error of a plan.
+ */
+vpm_status vpm_nmpc_control(vpm_nmpc *nmpc, int t, const double *h_x_obs, double *h_u);
+
+/* The policy in effect: its first step *t0, h_gains[horizon*7] and h_ubar[horizon] by absolute
+ * step, h_xbar[(horizon+1)*7] (rows before t0 unused). Any pointer may be null. */
+vpm_status vpm_nmpc_policy(vpm_nmpc *nmpc, int *t0, double *h_gains, double *h_xbar,
+                           float *h_ubar);
+
+/* Plans finished (the initial one included), replans skipped while the planner was busy, and the
+ * wall time of the last and the longest replan (projection + MPPI + synthesis) in ms. */
+vpm_status vpm_nmpc_stats(vpm_nmpc *nmpc, int *plans_done, int *plans_skipped,
+                          double *last_plan_ms, double *max_plan_ms);
+
+/* Stops the planner, waits for the device, frees everything. */
+vpm_status vpm_nmpc_destroy(vpm_nmpc *nmpc);
 
 /*
  * Throughput probe. The paper has no counterpart: it is a measurement aid that states, from

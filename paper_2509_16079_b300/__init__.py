@@ -77,6 +77,16 @@ _SIGNATURES = {
     "vpm_step": ([_VP, _D, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_rollout_batch": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_rollout_batch_x0": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_state_set_glider": ([_VP, _VP, _VP], _I),
+    "vpm_state_get_glider": ([_VP, _VP, _VP], _I),
+    "vpm_state_copy": ([_VP, _VP, _VP], _I),
+    "vpm_state_advance_policy": ([_VP, _I, _VP, _VP, _VP, _I, _VP], _I),
+    "vpm_rollout_batch_policy": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_nmpc_create": ([_VP, _VP, _VP, _I, _I, _VP, _VP, _I, _VP, _VP, _VP, C.POINTER(_VP)], _I),
+    "vpm_nmpc_control": ([_VP, _I, _VP, C.POINTER(_D)], _I),
+    "vpm_nmpc_policy": ([_VP, C.POINTER(_I), _VP, _VP, _VP], _I),
+    "vpm_nmpc_stats": ([_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D), C.POINTER(_D)], _I),
+    "vpm_nmpc_destroy": ([_VP], _I),
     "vpm_ls_jacobians": ([_I, _I, _D, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_tvlqr": ([_I, _D, _VP, _VP, _VP, _VP, _D, _VP, _VP, _VP], _I),
     "vpm_rollout_batch_per_launch": ([_VP, _I, _I, _VP, _VP, _VP, _VP], _I),
@@ -196,6 +206,47 @@ class State:
 
     def status(self, stream=None):
         check(lib().vpm_state_status(self._h, stream_handle(stream)))
+
+    def glider(self, stream=None) -> np.ndarray:
+        xg = np.zeros(7)
+        check(lib().vpm_state_get_glider(self._h, xg.ctypes.data_as(_VP), stream_handle(stream)))
+        return xg
+
+    def set_glider(self, x7, stream=None):
+        xg = np.ascontiguousarray(np.asarray(x7, dtype=np.float64))
+        check(lib().vpm_state_set_glider(self._h, xg.ctypes.data_as(_VP), stream_handle(stream)))
+
+    def copy_from(self, other: "State", stream=None):
+        check(lib().vpm_state_copy(self._h, other._h, stream_handle(stream)))
+
+    def advance_policy(self, steps: int, gains, xbar, ubar, offset: int, stream=None):
+        """In-place closed-loop steps under a tracking policy (device tensors, absolute index)."""
+        import torch
+        gains, xbar = _dev_tensor(gains, torch.float64), _dev_tensor(xbar, torch.float64)
+        ubar = _dev_tensor(ubar, torch.float32)
+        check(lib().vpm_state_advance_policy(self._h, int(steps), ptr(gains), ptr(xbar), ptr(ubar),
+                                             int(offset), stream_handle(stream)))
+
+    def rollout_policy(self, K: int, H: int, gains, xbar, ubar, offset: int = 0, x0=None,
+                       controls=None, want_traj: bool = False, stream=None):
+        """K closed-loop rollouts under a tracking policy (see vpm_rollout_batch_policy)."""
+        import torch
+        gains, xbar = _dev_tensor(gains, torch.float64), _dev_tensor(xbar, torch.float64)
+        ubar = _dev_tensor(ubar, torch.float32)
+        dev = gains.device
+        if x0 is not None:
+            x0 = _dev_tensor(x0, torch.float64)
+        if controls is not None:
+            controls = _dev_tensor(controls, torch.float32)
+        out = dict(costs=torch.empty(K, dtype=torch.float32, device=dev),
+                   final_glider=torch.empty((K, 7), dtype=torch.float64, device=dev))
+        if want_traj:
+            out["traj"] = torch.empty((K, H, 7), dtype=torch.float64, device=dev)
+        check(lib().vpm_rollout_batch_policy(self._h, int(K), int(H), ptr(x0), ptr(gains), ptr(xbar),
+                                             ptr(ubar), int(offset), ptr(controls), ptr(out["costs"]),
+                                             ptr(out["final_glider"]), ptr(out.get("traj")),
+                                             stream_handle(stream)))
+        return out
 
     def save(self, stream=None) -> bytes:
         size = C.c_size_t()
@@ -434,6 +485,72 @@ def mppi_perturb(mu, eps, out=None, stream=None):
     c = out if out is not None else torch.empty_like(eps)
     check(lib().mppi_perturb(ptr(mu), ptr(eps), K, H, ptr(c), stream_handle(stream)))
     return c
+
+
+class NmpcConfig(C.Structure):
+    _fields_ = [("horizon", C.c_int), ("replan_every", C.c_int), ("latency", C.c_int),
+                ("rollouts", C.c_int), ("iterations", C.c_int), ("lam", C.c_float),
+                ("qc", C.c_double * 7), ("qf", C.c_double * 7), ("rc", C.c_double),
+                ("threaded", C.c_int)]
+
+
+class NMPC:
+    """Feedback NMPC of §IV-C (see vpm_nmpc_* in include/vpm.h). noise: list over plans of
+    (eps (iterations, K, N) float32, xi (K, 7) float64, zeta (K, N) float32)."""
+
+    def __init__(self, params: dict, particles, capacity: int, x0, mu0, noise, horizon: int,
+                 replan_every: int, latency: int, rollouts: int, iterations: int, lam: float,
+                 qc, qf, rc: float, threaded: bool = False, precision: int = FP32):
+        cfg = NmpcConfig()
+        cfg.horizon, cfg.replan_every, cfg.latency = int(horizon), int(replan_every), int(latency)
+        cfg.rollouts, cfg.iterations, cfg.lam = int(rollouts), int(iterations), float(lam)
+        for i in range(7):
+            cfg.qc[i], cfg.qf[i] = float(qc[i]), float(qf[i])
+        cfg.rc, cfg.threaded = float(rc), int(bool(threaded))
+        self._P = make_params(params, precision)
+        parts = np.ascontiguousarray(np.asarray(particles, dtype=np.float64).reshape(-1, 3))
+        xg = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+        mu = np.ascontiguousarray(np.asarray(mu0, dtype=np.float32))
+        eps = np.ascontiguousarray(np.stack([z[0] for z in noise]).astype(np.float32))
+        xi = np.ascontiguousarray(np.stack([z[1] for z in noise]).astype(np.float64))
+        zeta = np.ascontiguousarray(np.stack([z[2] for z in noise]).astype(np.float32))
+        self.horizon = int(horizon)
+        h = C.c_void_p()
+        check(lib().vpm_nmpc_create(C.byref(cfg), C.byref(self._P), parts.ctypes.data_as(_VP),
+                                    len(parts), int(capacity), xg.ctypes.data_as(_VP),
+                                    mu.ctypes.data_as(_VP), len(noise), eps.ctypes.data_as(_VP),
+                                    xi.ctypes.data_as(_VP), zeta.ctypes.data_as(_VP), C.byref(h)))
+        self._h = h
+
+    def control(self, t: int, x_obs) -> float:
+        x = np.ascontiguousarray(np.asarray(x_obs, dtype=np.float64))
+        u = C.c_double()
+        check(lib().vpm_nmpc_control(self._h, int(t), x.ctypes.data_as(_VP), C.byref(u)))
+        return u.value
+
+    def policy(self):
+        t0 = C.c_int()
+        N = self.horizon
+        g, xb, ub = np.zeros((N, 7)), np.zeros((N + 1, 7)), np.zeros(N, np.float32)
+        check(lib().vpm_nmpc_policy(self._h, C.byref(t0), g.ctypes.data_as(_VP),
+                                    xb.ctypes.data_as(_VP), ub.ctypes.data_as(_VP)))
+        return t0.value, g, xb, ub
+
+    def stats(self):
+        d, s_, a, b = C.c_int(), C.c_int(), C.c_double(), C.c_double()
+        check(lib().vpm_nmpc_stats(self._h, C.byref(d), C.byref(s_), C.byref(a), C.byref(b)))
+        return dict(plans_done=d.value, plans_skipped=s_.value, last_plan_ms=a.value, max_plan_ms=b.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vpm_nmpc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ls_jacobians(x0, traj, controls, xbar, ubar, dt: float, stream=None):

@@ -382,6 +382,41 @@ extern "C" vpm_status vpm_state_set_history(vpm_state *s, const double *h_gb_pre
     return VPM_OK;
 }
 
+extern "C" vpm_status vpm_state_set_glider(vpm_state *s, const double *h_x7, cudaStream_t stream)
+{
+    if (!s || !h_x7) return fail(VPM_ERR_INVALID, "null argument");
+    if (!finite_all(h_x7, 7)) return fail(VPM_ERR_NONFINITE, "non-finite glider state");
+    CUDA_TRY(cudaMemcpyAsync(s->d_glider, h_x7, sizeof(double) * 7, cudaMemcpyHostToDevice, stream), "set_glider");
+    CUDA_TRY(cudaStreamSynchronize(stream), "set_glider sync");
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_state_get_glider(const vpm_state *s, double *h_x7, cudaStream_t stream)
+{
+    if (!s || !h_x7) return fail(VPM_ERR_INVALID, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(h_x7, s->d_glider, sizeof(double) * 7, cudaMemcpyDeviceToHost, stream), "get_glider");
+    CUDA_TRY(cudaStreamSynchronize(stream), "get_glider sync");
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_state_copy(vpm_state *dst, const vpm_state *src, cudaStream_t stream)
+{
+    if (!dst || !src) return fail(VPM_ERR_INVALID, "null argument");
+    if (dst == src) return VPM_OK;
+    if (dst->params.precision != src->params.precision || dst->params.n_b != src->params.n_b ||
+        dst->capacity < src->n_upper)
+        return fail(VPM_ERR_INVALID, "states differ in precision or n_b, or the capacity is too small");
+    CUDA_TRY(cudaMemcpyAsync(dst->d_part, src->d_part, src->rec_bytes * (size_t)src->capacity <
+                             dst->rec_bytes * (size_t)dst->capacity ? src->rec_bytes * (size_t)src->capacity
+                             : dst->rec_bytes * (size_t)dst->capacity,
+                             cudaMemcpyDeviceToDevice, stream), "state copy");
+    CUDA_TRY(cudaMemcpyAsync(dst->d_n, src->d_n, sizeof(int), cudaMemcpyDeviceToDevice, stream), "state copy");
+    CUDA_TRY(cudaMemcpyAsync(dst->d_glider, src->d_glider, sizeof(double) * 7, cudaMemcpyDeviceToDevice, stream), "state copy");
+    CUDA_TRY(cudaMemcpyAsync(dst->d_hist, src->d_hist, sizeof(double) * (kMaxB + 2), cudaMemcpyDeviceToDevice, stream), "state copy");
+    dst->n_upper = src->n_upper;
+    return VPM_OK;
+}
+
 static vpm_status take_status(vpm_state *s, cudaStream_t stream)
 {
     int st = 0;
@@ -559,6 +594,55 @@ extern "C" vpm_status vpm_rollout_batch(const vpm_state *s, int K, int H, const 
 {
     return rollout_batch(s, K, H, nullptr, d_controls, d_costs, d_final_glider, d_traj, d_field,
                          d_count, stream);
+}
+
+extern "C" vpm_status vpm_state_advance_policy(vpm_state *s, int steps, const double *d_gains,
+                                                const double *d_xbar, const float *d_ubar,
+                                                int offset, cudaStream_t stream)
+{
+    if (!s || !d_gains || !d_xbar || !d_ubar) return fail(VPM_ERR_INVALID, "null argument");
+    if (steps < 0 || offset < 0) return fail(VPM_ERR_INVALID, "steps and offset must be >= 0");
+    if (steps == 0) return VPM_OK;
+    const long long need = grown(s, steps);
+    if (need > s->capacity)
+        return fail(VPM_ERR_CAPACITY, "advance may reach %lld particles, capacity %d", need, s->capacity);
+    RolloutArgs a;
+    base_args(s, a);
+    a.H = steps; a.K = 1; a.cap = s->capacity;
+    a.out_part = s->d_part; a.out_n = s->d_n; a.out_glider = s->d_glider; a.out_hist = s->d_hist;
+    a.pol_gains = d_gains; a.pol_xbar = d_xbar; a.pol_ubar = d_ubar; a.pol_offset = offset;
+    cudaError_t e = launch_rollout(s->params.precision, a, 1, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_state_advance_policy launch");
+    long long g = (long long)s->n_upper + 2LL * steps;   // merging ends every step at <= n_wake_max
+    if (s->params.n_wake_max > 0 && g > s->params.n_wake_max)
+        g = s->params.n_wake_max > s->n_upper ? s->params.n_wake_max : s->n_upper;
+    s->n_upper = (int)g;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_rollout_batch_policy(const vpm_state *s, int K, int H, const double *d_x0,
+                                               const double *d_gains, const double *d_xbar,
+                                               const float *d_ubar, int offset,
+                                               const float *d_controls, float *d_costs,
+                                               double *d_final_glider, double *d_traj,
+                                               cudaStream_t stream)
+{
+    if (!s || !d_gains || !d_xbar || !d_ubar || !d_costs) return fail(VPM_ERR_INVALID, "null argument");
+    if (K < 1 || H < 1 || offset < 0) return fail(VPM_ERR_INVALID, "K, H must be positive, offset >= 0");
+    const long long need = grown(s, H);
+    if (need > s->capacity)
+        return fail(VPM_ERR_CAPACITY, "rollout may reach %lld particles, capacity %d", need, s->capacity);
+    RolloutArgs a;
+    base_args(s, a);
+    a.H = H; a.K = K;
+    a.cap = (int)(need > 0 ? need : 1);
+    a.x0 = d_x0;
+    a.controls = d_controls; a.ctrl_stride = H;
+    a.pol_gains = d_gains; a.pol_xbar = d_xbar; a.pol_ubar = d_ubar; a.pol_offset = offset;
+    a.costs = d_costs; a.final_glider = d_final_glider; a.traj = d_traj;
+    cudaError_t e = launch_rollout(s->params.precision, a, K, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_rollout_batch_policy launch");
+    return VPM_OK;
 }
 
 extern "C" vpm_status vpm_rollout_batch_x0(const vpm_state *s, int K, int H, const double *d_x0,

@@ -796,8 +796,17 @@ __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P 
     load_state<R>(a, w, part, rid);
     int n = w.n, claim_base = 0;
     for (int k = 0; k < a.H; ++k) {
-        const double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k]
-                                    : a.u_const;
+        double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k]
+                              : a.u_const;
+        if (a.pol_gains && threadIdx.x < 32) {
+            // the feedback control from the glider state in shared memory, formed by warp 0,
+            // the only warp that uses the control (the other warps never read it)
+            const size_t j = (size_t)a.pol_offset + k;
+            double fb = (double)a.pol_ubar[j];
+            for (int c = 0; c < 7; ++c)
+                fb -= a.pol_gains[j * 7 + c] * (w.xg[c] - a.pol_xbar[j * 7 + c]);
+            u = (a.controls ? u : 0.0) + fb;
+        }
         step_once<R, KER>(a.p, w, part, vel, u, a, a.H == 1, n, claim_base);
         if (a.traj && threadIdx.x < 7)
             a.traj[((size_t)rid * a.H + k) * 7 + threadIdx.x] = w.xg[threadIdx.x];

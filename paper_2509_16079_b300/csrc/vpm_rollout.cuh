@@ -39,6 +39,12 @@ struct RolloutArgs {
     int n_items;
     // per-rollout initial glider states (K x 7, overrides root_glider; null: the root's)
     const double *x0;
+    // tracking policy of §IV-B applied inside the rollout (null gains: open loop): at step k the
+    // control is pol_ubar[j] - pol_gains[j] . (x_k - pol_xbar[j]), j = pol_offset + k, plus the
+    // open-loop control if `controls` is also given
+    const double *pol_gains, *pol_xbar;
+    const float *pol_ubar;
+    int pol_offset;
 };
 
 size_t rollout_smem_bytes(int precision, int cap);
