@@ -84,9 +84,10 @@ def lib():
                                _DP, C.POINTER(C.c_int), C.c_double,
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(C.c_int)]
+        L.ora_step_dist.argtypes = L.ora_step.argtypes + [C.POINTER(C.c_int)]
         L.ora_rollout.argtypes = [C.POINTER(Params), C.c_int, C.c_int, _D, _D, _D, _D, C.c_void_p,
                                   C.c_double, C.c_int, C.c_int, _D, _D, _DP, C.c_void_p,
-                                  C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]
+                                  C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         L.ora_mppi_weights.argtypes = [C.c_int, _D, C.c_double, _D]
         L.ora_mppi_update.argtypes = [C.c_int, C.c_int, _D, _D, _D]
         _lib = L
@@ -179,7 +180,7 @@ class State:
     """Coupled glider + wake state advanced by `step` (one call of the C oracle per step)."""
 
     def __init__(self, params: dict, parts, xg, capacity: int, gb_prev=None, glev_prev=0.0,
-                 has_prev=0):
+                 has_prev=0, n_dist=0):
         self.params = dict(params)
         self._P = make_params(params)
         parts = _f64(parts).reshape(-1, 3)
@@ -193,6 +194,7 @@ class State:
         self.gb_prev = np.zeros(nb) if gb_prev is None else _f64(gb_prev).copy()
         self.glev_prev = float(glev_prev)
         self.has_prev = int(has_prev)
+        self.n_dist = int(n_dist)       # 2: the first two particles are the disturbance pair
 
     @property
     def particles(self):
@@ -200,8 +202,21 @@ class State:
 
     def copy(self):
         s = State(self.params, self.particles, self.xg, self.capacity, self.gb_prev,
-                  self.glev_prev, self.has_prev)
+                  self.glev_prev, self.has_prev, self.n_dist)
         return s
+
+    def inject_pair(self, x1, z1, g1, x2, z2, g2):
+        """Puts a disturbance pair (§V) in front of the wake: particles 0 and 1, left out of
+        merging and removed once their segment crosses the offset chord line."""
+        if self.n_dist:
+            raise ValueError("a disturbance pair is already present")
+        if self.n + 2 > self.capacity:
+            raise ValueError("capacity exceeded")
+        for arr, a, b in ((self.x, x1, x2), (self.z, z1, z2), (self.g, g1, g2)):
+            arr[2:self.n + 2] = arr[:self.n].copy()
+            arr[0], arr[1] = a, b
+        self.n += 2
+        self.n_dist = 2
 
     def step(self, u: float = 0.0):
         """One step; returns dict(gamma_s, fm, vel, vtilde, alpha)."""
@@ -211,20 +226,23 @@ class State:
         vel = np.zeros(2 * (self.n + 2)); vt = np.zeros(2 * (nc + nb)); al = np.zeros(1)
         n = C.c_int(self.n); gl = C.c_double(self.glev_prev); hp = C.c_int(self.has_prev)
         shed = C.c_int(0)
+        nd = C.c_int(self.n_dist)
         n_before = self.n
-        rc = lib().ora_step(C.byref(self._P), self.capacity, C.byref(n), self.x, self.z, self.g,
-                            self.xg, self.gb_prev, C.byref(gl), C.byref(hp), float(u),
-                            _ptr(gs), _ptr(fm), _ptr(vel), _ptr(vt), _ptr(al), C.byref(shed))
+        rc = lib().ora_step_dist(C.byref(self._P), self.capacity, C.byref(n), self.x, self.z, self.g,
+                                 self.xg, self.gb_prev, C.byref(gl), C.byref(hp), float(u),
+                                 _ptr(gs), _ptr(fm), _ptr(vel), _ptr(vt), _ptr(al), C.byref(shed),
+                                 C.byref(nd))
         if rc != 0:
             raise RuntimeError("oracle step failed with status %d" % rc)
         self.n, self.glev_prev, self.has_prev = n.value, gl.value, hp.value
+        self.n_dist = nd.value
         m = n_before + shed.value
         return dict(gamma_s=gs, fm=fm, vel=vel[:2 * m].reshape(-1, 2),
                     vtilde=vt.reshape(-1, 2), alpha=al[0], shed=shed.value)
 
 
 def rollout(params: dict, parts, xg0, controls, capacity=None, gb_prev=None, glev_prev=0.0,
-            has_prev=0, want_traj=False, want_field=False):
+            has_prev=0, want_traj=False, want_field=False, n_dist=0):
     """One rollout of len(controls) steps; returns dict(xg, cost, traj?, field?)."""
     parts = _f64(parts).reshape(-1, 3)
     H = len(controls)
@@ -240,7 +258,8 @@ def rollout(params: dict, parts, xg0, controls, capacity=None, gb_prev=None, gle
     P = make_params(params)
     rc = lib().ora_rollout(C.byref(P), cap, len(x), x, z, g, _f64(xg0), _ptr(gbp),
                            float(glev_prev), int(has_prev), H, _f64(controls), xg,
-                           C.byref(cost), _ptr(traj), C.byref(nout), _ptr(fx), _ptr(fz), _ptr(fg))
+                           C.byref(cost), _ptr(traj), C.byref(nout), _ptr(fx), _ptr(fz), _ptr(fg),
+                           int(n_dist))
     if rc != 0:
         raise RuntimeError("oracle rollout failed with status %d" % rc)
     out = dict(xg=xg, cost=cost.value)

@@ -350,10 +350,58 @@ double ora_terminal_cost(const ora_params *p, const double *xg) { return termina
  *   out_alpha      : angle of attack used by the separation gate
  *   out_shed       : number of vortices shed this step (0, 1 or 2)
  */
+/* Orientation of c relative to the directed line a -> b (twice the signed triangle area). */
+static double orient(double ax, double az, double bx, double bz, double cx, double cz)
+{
+    return (bx - ax) * (cz - az) - (bz - az) * (cx - ax);
+}
+
+/* Whether segments p0-p1 and a-b cross (each segment's ends strictly on opposite sides of the
+ * other's line; touching and collinear overlap do not count). */
+static int segments_cross(double p0x, double p0z, double p1x, double p1z, double ax, double az,
+                          double bx, double bz)
+{
+    double o1 = orient(ax, az, bx, bz, p0x, p0z), o2 = orient(ax, az, bx, bz, p1x, p1z);
+    double o3 = orient(p0x, p0z, p1x, p1z, ax, az), o4 = orient(p0x, p0z, p1x, p1z, bx, bz);
+    return ((o1 > 0.0 && o2 < 0.0) || (o1 < 0.0 && o2 > 0.0)) &&
+           ((o3 > 0.0 && o4 < 0.0) || (o3 < 0.0 && o4 > 0.0));
+}
+
+static int step_impl(const ora_params *p, int capacity, int *n_io, double *x, double *z, double *g,
+                     double *xg, double *gb_prev, double *glev_prev, int *has_prev, double u,
+                     double *out_gs, double *out_fm, double *out_vel, double *out_vt,
+                     double *out_alpha, int *out_shed, int *n_dist);
+
 int ora_step(const ora_params *p, int capacity, int *n_io, double *x, double *z, double *g,
              double *xg, double *gb_prev, double *glev_prev, int *has_prev, double u,
              double *out_gs, double *out_fm, double *out_vel, double *out_vt, double *out_alpha,
              int *out_shed)
+{
+    int nd = 0;
+    return step_impl(p, capacity, n_io, x, z, g, xg, gb_prev, glev_prev, has_prev, u, out_gs,
+                     out_fm, out_vel, out_vt, out_alpha, out_shed, &nd);
+}
+
+/*
+ * ora_step with a disturbance pair (§V): when *n_dist is 2 the first two particles are the
+ * pair of opposite vortices standing for the vortex ring. They are convected with the wake
+ * and are left out of merging. After the glider update, the pair is removed (*n_dist becomes
+ * 0) once the segment joining it crosses the chord line offset by 2 % of the chord against
+ * the normal, with the plate in its updated position.
+ */
+int ora_step_dist(const ora_params *p, int capacity, int *n_io, double *x, double *z, double *g,
+                  double *xg, double *gb_prev, double *glev_prev, int *has_prev, double u,
+                  double *out_gs, double *out_fm, double *out_vel, double *out_vt,
+                  double *out_alpha, int *out_shed, int *n_dist)
+{
+    return step_impl(p, capacity, n_io, x, z, g, xg, gb_prev, glev_prev, has_prev, u, out_gs,
+                     out_fm, out_vel, out_vt, out_alpha, out_shed, n_dist);
+}
+
+static int step_impl(const ora_params *p, int capacity, int *n_io, double *x, double *z, double *g,
+                     double *xg, double *gb_prev, double *glev_prev, int *has_prev, double u,
+                     double *out_gs, double *out_fm, double *out_vel, double *out_vt,
+                     double *out_alpha, int *out_shed, int *n_dist)
 {
     int n = *n_io;
     int nb = p->n_b, nc = p->n_b + 1;
@@ -482,13 +530,29 @@ int ora_step(const ora_params *p, int capacity, int *n_io, double *x, double *z,
         for (int k = 0; k < 7; ++k) xg[k] += dt * f[k];
     }
 
-    /* merge the two oldest particles while the wake is over its limit */
+    /* disturbance termination: the pair's segment against the offset chord line */
+    if (*n_dist == 2 && n >= 2) {
+        ora_geom G2;
+        plate_geometry(p, xg, &G2);
+        double off = 0.02 * p->chord;
+        double ax = G2.cx[0] - off * G2.nx, az = G2.cz[0] - off * G2.nz;
+        double bx = G2.cx[nc - 1] - off * G2.nx, bz = G2.cz[nc - 1] - off * G2.nz;
+        if (segments_cross(x[0], z[0], x[1], z[1], ax, az, bx, bz)) {
+            for (int v = 0; v + 2 < n; ++v) { x[v] = x[v + 2]; z[v] = z[v + 2]; g[v] = g[v + 2]; }
+            n -= 2;
+            *n_dist = 0;
+        }
+    }
+
+    /* merge the two oldest wake particles (after the disturbance pair, which is left alone)
+     * while the wake is over its limit */
     if (p->n_wake_max > 0) {
-        while (n > p->n_wake_max && n >= 2) {
-            x[0] = 0.5 * (x[0] + x[1]);
-            z[0] = 0.5 * (z[0] + z[1]);
-            g[0] = g[0] + g[1];
-            for (int v = 1; v + 1 < n; ++v) { x[v] = x[v + 1]; z[v] = z[v + 1]; g[v] = g[v + 1]; }
+        int d = *n_dist;
+        while (n - d > p->n_wake_max && n - d >= 2) {
+            x[d] = 0.5 * (x[d] + x[d + 1]);
+            z[d] = 0.5 * (z[d] + z[d + 1]);
+            g[d] = g[d] + g[d + 1];
+            for (int v = d + 1; v + 1 < n; ++v) { x[v] = x[v + 1]; z[v] = z[v + 1]; g[v] = g[v + 1]; }
             n -= 1;
         }
     }
@@ -508,8 +572,10 @@ int ora_step(const ora_params *p, int capacity, int *n_io, double *x, double *z,
 int ora_rollout(const ora_params *p, int capacity, int n0, const double *x0, const double *z0,
                 const double *g0, const double *xg0, const double *gb_prev0, double glev_prev0,
                 int has_prev0, int H, const double *controls, double *out_xg, double *out_cost,
-                double *out_traj, int *out_n, double *out_x, double *out_z, double *out_g)
+                double *out_traj, int *out_n, double *out_x, double *out_z, double *out_g,
+                int n_dist0)
 {
+    int nd = n_dist0;
     double *x = malloc(sizeof(double) * capacity);
     double *z = malloc(sizeof(double) * capacity);
     double *g = malloc(sizeof(double) * capacity);
@@ -521,8 +587,8 @@ int ora_rollout(const ora_params *p, int capacity, int n0, const double *x0, con
     memcpy(xg, xg0, sizeof(xg));
     for (int j = 0; j < p->n_b; ++j) gbp[j] = gb_prev0 ? gb_prev0[j] : 0.0;
     for (int k = 0; k < H && rc == ORA_OK; ++k) {
-        rc = ora_step(p, capacity, &n, x, z, g, xg, gbp, &glp, &hp, controls[k], NULL, NULL,
-                      NULL, NULL, NULL, NULL);
+        rc = step_impl(p, capacity, &n, x, z, g, xg, gbp, &glp, &hp, controls[k], NULL, NULL,
+                       NULL, NULL, NULL, NULL, &nd);
         if (out_traj) memcpy(out_traj + 7 * k, xg, sizeof(xg));
     }
     if (out_xg) memcpy(out_xg, xg, sizeof(xg));
