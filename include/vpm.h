@@ -133,6 +133,20 @@ vpm_status vpm_state_read(const vpm_state *state, double *h_particles, int *n_ou
  * Synchronises `stream`. Errors: VPM_ERR_INVALID (null), VPM_ERR_NONFINITE. */
 vpm_status vpm_state_set_glider(vpm_state *state, const double *h_x7, cudaStream_t stream);
 
+/*
+ * Puts a disturbance pair (§V: two opposite vortices standing for a vortex ring) in front of the
+ * state's wake: h_pair = (x1, z1, Gamma1, x2, z2, Gamma2). The pair occupies the first two
+ * slots, is convected with the wake by every step and rollout, is left out of merging, and is
+ * removed when, after a step's glider update, the segment joining it crosses the chord line
+ * moved by 2 % of the chord against the normal (the termination at the wing of §V).
+ * Errors: VPM_ERR_INVALID (null, a pair already present), VPM_ERR_NONFINITE,
+ * VPM_ERR_CAPACITY (no room for two more particles), VPM_ERR_CUDA.
+ */
+vpm_status vpm_state_inject_pair(vpm_state *state, const double *h_pair, cudaStream_t stream);
+
+/* *h_n_dist = 2 while the state's disturbance pair is present, else 0 (synchronises). */
+vpm_status vpm_state_disturbance(const vpm_state *state, int *h_n_dist, cudaStream_t stream);
+
 /* Copies the glider state to h_x7 (synchronises `stream`). */
 vpm_status vpm_state_get_glider(const vpm_state *state, double *h_x7, cudaStream_t stream);
 

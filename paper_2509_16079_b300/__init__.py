@@ -78,6 +78,8 @@ _SIGNATURES = {
     "vpm_rollout_batch": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_rollout_batch_x0": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_state_set_glider": ([_VP, _VP, _VP], _I),
+    "vpm_state_inject_pair": ([_VP, _VP, _VP], _I),
+    "vpm_state_disturbance": ([_VP, C.POINTER(_I), _VP], _I),
     "vpm_state_get_glider": ([_VP, _VP, _VP], _I),
     "vpm_state_copy": ([_VP, _VP, _VP], _I),
     "vpm_state_advance_policy": ([_VP, _I, _VP, _VP, _VP, _I, _VP], _I),
@@ -215,6 +217,16 @@ class State:
     def set_glider(self, x7, stream=None):
         xg = np.ascontiguousarray(np.asarray(x7, dtype=np.float64))
         check(lib().vpm_state_set_glider(self._h, xg.ctypes.data_as(_VP), stream_handle(stream)))
+
+    def inject_pair(self, x1, z1, g1, x2, z2, g2, stream=None):
+        """Disturbance pair in front of the wake (see vpm_state_inject_pair)."""
+        a = np.array([x1, z1, g1, x2, z2, g2], dtype=np.float64)
+        check(lib().vpm_state_inject_pair(self._h, a.ctypes.data_as(_VP), stream_handle(stream)))
+
+    def disturbance(self, stream=None) -> int:
+        v = C.c_int()
+        check(lib().vpm_state_disturbance(self._h, C.byref(v), stream_handle(stream)))
+        return v.value
 
     def copy_from(self, other: "State", stream=None):
         check(lib().vpm_state_copy(self._h, other._h, stream_handle(stream)))

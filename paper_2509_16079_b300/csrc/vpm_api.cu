@@ -64,6 +64,7 @@ struct vpm_state {
     DevParams dp;
     int capacity;
     int n_upper;          // host-side upper bound of the resident count
+    int pair_slots;       // 2 once a disturbance pair was injected (kept after its termination)
     int device;
     size_t rec_bytes;     // bytes of one particle record
     void *d_part;
@@ -330,7 +331,7 @@ extern "C" vpm_status vpm_state_create(const vpm_params *params, const double *h
     double hist[kMaxB + 2] = {0};
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&s->d_part, s->rec_bytes * capacity)) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_n, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_n, sizeof(int) * 2)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_glider, sizeof(double) * 7)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_hist, sizeof(double) * (kMaxB + 2))) != cudaSuccess ||
         (e = cudaMalloc(&s->d_kinv, sizeof(double) * 4 * kMaxS * kMaxS)) != cudaSuccess ||
@@ -342,7 +343,8 @@ extern "C" vpm_status vpm_state_create(const vpm_params *params, const double *h
     }
     s->dp.kinv = s->d_kinv;
     e = cudaMemcpyAsync(s->d_part, host_rec, s->rec_bytes * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_n, &n, sizeof(int), cudaMemcpyHostToDevice, stream);
+    const int n_pair[2] = {n, 0};         // count, disturbance pair count
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_n, n_pair, sizeof n_pair, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_glider, h_glider7, sizeof(double) * 7, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_hist, hist, sizeof hist, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_kinv, kinv, sizeof(double) * 4 * kMaxS * kMaxS, cudaMemcpyHostToDevice, stream);
@@ -410,10 +412,35 @@ extern "C" vpm_status vpm_state_copy(vpm_state *dst, const vpm_state *src, cudaS
                              dst->rec_bytes * (size_t)dst->capacity ? src->rec_bytes * (size_t)src->capacity
                              : dst->rec_bytes * (size_t)dst->capacity,
                              cudaMemcpyDeviceToDevice, stream), "state copy");
-    CUDA_TRY(cudaMemcpyAsync(dst->d_n, src->d_n, sizeof(int), cudaMemcpyDeviceToDevice, stream), "state copy");
+    CUDA_TRY(cudaMemcpyAsync(dst->d_n, src->d_n, sizeof(int) * 2, cudaMemcpyDeviceToDevice, stream), "state copy");
     CUDA_TRY(cudaMemcpyAsync(dst->d_glider, src->d_glider, sizeof(double) * 7, cudaMemcpyDeviceToDevice, stream), "state copy");
     CUDA_TRY(cudaMemcpyAsync(dst->d_hist, src->d_hist, sizeof(double) * (kMaxB + 2), cudaMemcpyDeviceToDevice, stream), "state copy");
     dst->n_upper = src->n_upper;
+    dst->pair_slots = src->pair_slots > dst->pair_slots ? src->pair_slots : dst->pair_slots;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_state_inject_pair(vpm_state *s, const double *h_pair, cudaStream_t stream)
+{
+    if (!s || !h_pair) return fail(VPM_ERR_INVALID, "null argument");
+    if (!finite_all(h_pair, 6)) return fail(VPM_ERR_NONFINITE, "non-finite disturbance pair");
+    if (s->n_upper + 2 > s->capacity)
+        return fail(VPM_ERR_CAPACITY, "no room for the pair: capacity %d", s->capacity);
+    int cnt[2];
+    CUDA_TRY(cudaMemcpyAsync(cnt, s->d_n, sizeof cnt, cudaMemcpyDeviceToHost, stream), "inject");
+    CUDA_TRY(cudaStreamSynchronize(stream), "inject");
+    if (cnt[1] != 0) return fail(VPM_ERR_INVALID, "a disturbance pair is already present");
+    CUDA_TRY(launch_inject_pair(s->params.precision, s->d_part, s->d_n, h_pair, stream), "inject launch");
+    s->n_upper += 2;
+    s->pair_slots = 2;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_state_disturbance(const vpm_state *s, int *h_n_dist, cudaStream_t stream)
+{
+    if (!s || !h_n_dist) return fail(VPM_ERR_INVALID, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(h_n_dist, s->d_n + 1, sizeof(int), cudaMemcpyDeviceToHost, stream), "disturbance");
+    CUDA_TRY(cudaStreamSynchronize(stream), "disturbance");
     return VPM_OK;
 }
 
@@ -465,7 +492,7 @@ extern "C" vpm_status vpm_state_read(const vpm_state *cs, double *h_particles, i
 // capacity records of the particle array.
 struct SaveHeader {
     uint32_t magic, precision, n_b, capacity;
-    int32_t n, pad;
+    int32_t n, pad;          // count, disturbance pair count
     double glider[7];
     double hist[kMaxB + 2];
 };
@@ -486,7 +513,7 @@ extern "C" vpm_status vpm_state_save(const vpm_state *cs, void *h_buf, size_t *b
     h.n_b = s->params.n_b;
     h.capacity = s->capacity;
     char *dst = static_cast<char *>(h_buf);
-    cudaError_t e = cudaMemcpyAsync(&h.n, s->d_n, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    cudaError_t e = cudaMemcpyAsync(&h.n, s->d_n, sizeof(int) * 2, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.glider, s->d_glider, sizeof h.glider, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.hist, s->d_hist, sizeof h.hist, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst + sizeof h, s->d_part, s->rec_bytes * s->capacity, cudaMemcpyDeviceToHost, stream);
@@ -506,31 +533,45 @@ extern "C" vpm_status vpm_state_load(vpm_state *s, const void *h_buf, size_t byt
     memcpy(&h, h_buf, sizeof h);
     if (h.magic != kSaveMagic || h.precision != (uint32_t)s->params.precision ||
         h.n_b != (uint32_t)s->params.n_b || h.capacity != (uint32_t)s->capacity ||
-        bytes < sizeof h + s->rec_bytes * s->capacity || h.n < 0 || h.n > s->capacity)
+        bytes < sizeof h + s->rec_bytes * s->capacity || h.n < 0 || h.n > s->capacity ||
+        (h.pad != 0 && h.pad != 2))
         return fail(VPM_ERR_INVALID, "saved state does not match this state");
     const char *src = static_cast<const char *>(h_buf);
     CUDA_TRY(cudaMemcpyAsync(s->d_part, src + sizeof h, s->rec_bytes * s->capacity, cudaMemcpyHostToDevice, stream), "load records");
-    CUDA_TRY(cudaMemcpyAsync(s->d_n, &h.n, sizeof(int), cudaMemcpyHostToDevice, stream), "load n");
+    CUDA_TRY(cudaMemcpyAsync(s->d_n, &h.n, sizeof(int) * 2, cudaMemcpyHostToDevice, stream), "load n");
     CUDA_TRY(cudaMemcpyAsync(s->d_glider, h.glider, sizeof h.glider, cudaMemcpyHostToDevice, stream), "load glider");
     CUDA_TRY(cudaMemcpyAsync(s->d_hist, h.hist, sizeof h.hist, cudaMemcpyHostToDevice, stream), "load hist");
     CUDA_TRY(cudaStreamSynchronize(stream), "load sync");
     s->n_upper = h.n;
+    if (h.pad) s->pair_slots = 2;
     return VPM_OK;
 }
 
 // ------------------------------------------------------------------ stepping and rollouts
 
-// Largest count a rollout of H steps can reach from the state's current upper bound.
+// Largest count a rollout of H steps can reach from the state's current upper bound. Merging
+// holds the wake (the disturbance pair excluded) at n_wake_max after each step, and two records
+// are appended before each merge.
 static long long grown(const vpm_state *s, int H)
 {
     long long n = (long long)s->n_upper + 2LL * H;
     if (s->params.n_wake_max > 0) {
-        // after merging the count never exceeds max(n_wake_max, current); two records are
-        // appended before each merge
-        long long cap = (s->params.n_wake_max > s->n_upper ? s->params.n_wake_max : s->n_upper) + 2;
+        const long long lim = (long long)s->params.n_wake_max + s->pair_slots;
+        long long cap = (lim > s->n_upper ? lim : s->n_upper) + 2;
         if (n > cap) n = cap;
     }
     return n;
+}
+
+// Upper bound of the count after `steps` committed steps (merging done).
+static int after_steps(const vpm_state *s, int steps)
+{
+    long long g = (long long)s->n_upper + 2LL * steps;
+    if (s->params.n_wake_max > 0) {
+        const long long lim = (long long)s->params.n_wake_max + s->pair_slots;
+        if (g > lim) g = lim > s->n_upper ? lim : s->n_upper;
+    }
+    return (int)g;
 }
 
 static void base_args(const vpm_state *s, RolloutArgs &a)
@@ -539,6 +580,7 @@ static void base_args(const vpm_state *s, RolloutArgs &a)
     a.p = s->dp;
     a.root_part = s->d_part;
     a.root_n = s->d_n;
+    a.root_ndist = s->d_n + 1;
     a.root_glider = s->d_glider;
     a.root_hist = s->d_hist;
     a.status = s->d_status;
@@ -556,13 +598,11 @@ extern "C" vpm_status vpm_step(vpm_state *s, double u, double *d_fm, double *d_g
     a.H = 1; a.K = 1; a.cap = s->capacity;
     a.u_const = u;
     a.out_part = s->d_part; a.out_n = s->d_n; a.out_glider = s->d_glider; a.out_hist = s->d_hist;
+    a.out_ndist = s->d_n + 1;
     a.probe_fm = d_fm; a.probe_gs = d_gamma_s; a.probe_vel = d_vel; a.probe_vt = d_vtilde;
     cudaError_t e = launch_rollout(s->params.precision, a, 1, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vpm_step launch");
-    long long g = (long long)s->n_upper + 2;
-    if (s->params.n_wake_max > 0 && g > s->params.n_wake_max)
-        g = s->params.n_wake_max > s->n_upper ? s->params.n_wake_max : s->n_upper;
-    s->n_upper = (int)g;
+    s->n_upper = after_steps(s, 1);
     return VPM_OK;
 }
 
@@ -610,13 +650,11 @@ extern "C" vpm_status vpm_state_advance_policy(vpm_state *s, int steps, const do
     base_args(s, a);
     a.H = steps; a.K = 1; a.cap = s->capacity;
     a.out_part = s->d_part; a.out_n = s->d_n; a.out_glider = s->d_glider; a.out_hist = s->d_hist;
+    a.out_ndist = s->d_n + 1;
     a.pol_gains = d_gains; a.pol_xbar = d_xbar; a.pol_ubar = d_ubar; a.pol_offset = offset;
     cudaError_t e = launch_rollout(s->params.precision, a, 1, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vpm_state_advance_policy launch");
-    long long g = (long long)s->n_upper + 2LL * steps;   // merging ends every step at <= n_wake_max
-    if (s->params.n_wake_max > 0 && g > s->params.n_wake_max)
-        g = s->params.n_wake_max > s->n_upper ? s->params.n_wake_max : s->n_upper;
-    s->n_upper = (int)g;
+    s->n_upper = after_steps(s, steps);
     return VPM_OK;
 }
 
@@ -673,7 +711,7 @@ extern "C" vpm_status vpm_rollout_batch_per_launch(const vpm_state *s, int K, in
     int *ns = nullptr;
     double *gl = nullptr, *hi = nullptr;
     CUDA_TRY(cudaMallocAsync(&parts, rec * (size_t)cap * K, stream), "per-launch scratch");
-    CUDA_TRY(cudaMallocAsync((void **)&ns, sizeof(int) * K, stream), "per-launch scratch");
+    CUDA_TRY(cudaMallocAsync((void **)&ns, sizeof(int) * 2 * K, stream), "per-launch scratch");
     CUDA_TRY(cudaMallocAsync((void **)&gl, sizeof(double) * stride * K, stream), "per-launch scratch");
     CUDA_TRY(cudaMallocAsync((void **)&hi, sizeof(double) * stride * K, stream), "per-launch scratch");
     // replicate the root into every rollout's slot (a zero-step launch of the rollout kernel)
@@ -682,9 +720,11 @@ extern "C" vpm_status vpm_rollout_batch_per_launch(const vpm_state *s, int K, in
     a.H = 0; a.K = K; a.cap = cap;
     a.out_stride = cap; a.out_state_stride = stride;
     a.out_part = parts; a.out_n = ns; a.out_glider = gl; a.out_hist = hi;
+    a.out_ndist = ns + K;
     cudaError_t e = launch_rollout(s->params.precision, a, K, stream);
     // then every step of every rollout is its own launch, state in global memory in between
     a.root_part = parts; a.root_n = ns; a.root_glider = gl; a.root_hist = hi;
+    a.root_ndist = ns + K;
     a.root_stride = cap; a.state_stride = stride;
     a.H = 1;
     a.controls = d_controls; a.ctrl_stride = H;

@@ -42,6 +42,7 @@ struct Work {
     int n;
     int flag;
     int chunk_next;                  // next unclaimed target chunk of the pair sums
+    int ndist;                       // 2 while the first two records are the disturbance pair
 };
 
 // ------------------------------------------------------------------ geometry (warp 0)
@@ -630,32 +631,34 @@ __device__ void advect_f64(const DevParams &p, Work &w, Part64 *part, const doub
     if (bad) atomicOr(&w.flag, (int)kStNonFinite);
 }
 
-// Merging (§III-A): while N > N_w,max the two oldest particles become one at their mean
-// position with the summed circulation; the merged particle stays the oldest. Applying it
-// m = N - N_w,max times merges records 0..m in order and shifts the rest down by m.
+// Merging (§III-A): while N > N_w,max the two oldest wake particles become one at their mean
+// position with the summed circulation; the merged particle stays the oldest. The first d
+// records (the disturbance pair, if present) are not part of the wake budget and are left
+// alone. Applying it m = N - d - N_w,max times merges records d..d+m in order and shifts the
+// rest down by m.
 template <class R>
-__device__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int n)
+__device__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int n, int d)
 {
     using P = typename Store<R>::P;
-    if (p.n_wake_max <= 0 || n <= p.n_wake_max) return n;
-    const int m = n - p.n_wake_max;
+    if (p.n_wake_max <= 0 || n - d <= p.n_wake_max) return n;
+    const int m = n - d - p.n_wake_max;
     __shared__ P s_merged;
     if (threadIdx.x == 0) {
         double x, z;
-        Store<R>::xz(part[0], x, z);
-        double g = Store<R>::gam(part[0]);
+        Store<R>::xz(part[d], x, z);
+        double g = Store<R>::gam(part[d]);
         for (int q = 1; q <= m; ++q) {
             double x2, z2;
-            Store<R>::xz(part[q], x2, z2);
+            Store<R>::xz(part[d + q], x2, z2);
             x = 0.5 * (x + x2);
             z = 0.5 * (z + z2);
-            g = g + Store<R>::gam(part[q]);
+            g = g + Store<R>::gam(part[d + q]);
         }
         s_merged = Store<R>::make(x, z, g);
     }
     __syncthreads();
     const int nn = n - m;
-    for (int base = 1; base < nn; base += (int)blockDim.x) {
+    for (int base = d + 1; base < nn; base += (int)blockDim.x) {
         const int i = base + threadIdx.x;
         P tmp;
         if (i < nn) tmp = part[i + m];
@@ -663,9 +666,59 @@ __device__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int 
         if (i < nn) part[i] = tmp;
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[0] = s_merged;
+    if (threadIdx.x == 0) part[d] = s_merged;
     __syncthreads();
     return nn;
+}
+
+// Disturbance termination (§V): with the plate at its updated position, the pair in records 0
+// and 1 is removed once the segment joining it crosses the chord line (leading to trailing
+// collocation point) moved by 2 % of the chord against the normal. A crossing needs each
+// segment's ends strictly on opposite sides of the other's line (signed areas, binary64).
+__device__ __forceinline__ double side_of(double ax, double az, double bx, double bz, double px,
+                                          double pz)
+{
+    return (bx - ax) * (pz - az) - (bz - az) * (px - ax);
+}
+
+template <class R>
+__device__ int terminate_pair(const DevParams &p, Work &w, typename Store<R>::P *part, int n)
+{
+    __shared__ int s_cross;
+    if (threadIdx.x == 0) {
+        int cross = 0;
+        if (n >= 2) {
+            double x0, z0, x1, z1;
+            Store<R>::xz(part[0], x0, z0);
+            Store<R>::xz(part[1], x1, z1);
+            double sn, cs;
+            sincos(w.xg[2], &sn, &cs);
+            const double xw = w.xg[0] - p.l_w * cs, zw = w.xg[1] - p.l_w * sn;
+            const double tx = -cs, tz = -sn, nx = -sn, nz = cs, off = 0.02 * p.chord;
+            const double s0 = -0.5 * p.chord, s1 = -0.5 * p.chord + p.n_b * p.lb;
+            const double ax = xw + s0 * tx - off * nx, az = zw + s0 * tz - off * nz;
+            const double bx = xw + s1 * tx - off * nx, bz = zw + s1 * tz - off * nz;
+            const double o1 = side_of(ax, az, bx, bz, x0, z0), o2 = side_of(ax, az, bx, bz, x1, z1);
+            const double o3 = side_of(x0, z0, x1, z1, ax, az), o4 = side_of(x0, z0, x1, z1, bx, bz);
+            cross = ((o1 > 0.0 && o2 < 0.0) || (o1 < 0.0 && o2 > 0.0)) &&
+                    ((o3 > 0.0 && o4 < 0.0) || (o3 < 0.0 && o4 > 0.0));
+        }
+        s_cross = cross;
+    }
+    __syncthreads();
+    if (!s_cross) return n;
+    using P = typename Store<R>::P;
+    for (int base = 0; base < n - 2; base += (int)blockDim.x) {
+        const int i = base + threadIdx.x;
+        P tmp;
+        if (i < n - 2) tmp = part[i + 2];
+        __syncthreads();
+        if (i < n - 2) part[i] = tmp;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) w.ndist = 0;
+    __syncthreads();
+    return n - 2;
 }
 
 // One full step of one rollout. All threads call it with the same particle count n (updated
@@ -725,7 +778,8 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
         advect_f64(p, w, part, vel, n1);
     }
     __syncthreads();
-    n = merge_oldest<R>(p, part, n1);
+    if (w.ndist == 2) n1 = terminate_pair<R>(p, w, part, n1);
+    n = merge_oldest<R>(p, part, n1, w.ndist);
 }
 
 template <class R>
@@ -740,7 +794,10 @@ __device__ void load_state(const RolloutArgs &a, Work &w, typename Store<R>::P *
     const double *h = a.root_hist + (size_t)rid * a.state_stride;
     if (threadIdx.x < 7) w.xg[threadIdx.x] = g[threadIdx.x];
     if (threadIdx.x < a.p.n_b + 2) w.hist[threadIdx.x] = h[threadIdx.x];
-    if (threadIdx.x == 0) { w.n = n; w.flag = 0; w.chunk_next = 0; }
+    if (threadIdx.x == 0) {
+        w.n = n; w.flag = 0; w.chunk_next = 0;
+        w.ndist = a.root_ndist ? a.root_ndist[(a.root_stride || a.root_offset) ? rid : 0] : 0;
+    }
     __syncthreads();
 }
 
@@ -757,6 +814,7 @@ __device__ void store_state(const RolloutArgs &a, Work &w, const typename Store<
     if (threadIdx.x < 7) g[threadIdx.x] = w.xg[threadIdx.x];
     if (threadIdx.x < a.p.n_b + 2) h[threadIdx.x] = w.hist[threadIdx.x];
     if (threadIdx.x == 0) a.out_n[a.out_stride ? rid : 0] = n;
+    if (threadIdx.x == 0 && a.out_ndist) a.out_ndist[a.out_stride ? rid : 0] = w.ndist;
 }
 
 template <class R>
@@ -989,6 +1047,44 @@ int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem)
     if (kernel == VPM_KERNEL_SINGULAR) { VPM_OCC(VPM_KERNEL_SINGULAR) }
     VPM_OCC(VPM_KERNEL_VATISTAS)
 #undef VPM_OCC
+}
+
+// ------------------------------------------------------------------ disturbance injection
+
+template <class R>
+__global__ void __launch_bounds__(kThreads) inject_pair_kernel(typename Store<R>::P *part, int *d_n,
+                                                              double x1, double z1, double g1,
+                                                              double x2, double z2, double g2)
+{
+    using P = typename Store<R>::P;
+    const int n = d_n[0];
+    // move records up by two, top chunk first (each chunk's targets are read before written)
+    for (int top = n; top > 0; top -= (int)blockDim.x) {
+        const int i = top - 1 - (int)threadIdx.x;
+        P tmp;
+        if (i >= 0) tmp = part[i];
+        __syncthreads();
+        if (i >= 0) part[i + 2] = tmp;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[0] = Store<R>::make(x1, z1, g1);
+        part[1] = Store<R>::make(x2, z2, g2);
+        d_n[0] = n + 2;
+        d_n[1] = 2;
+    }
+}
+
+cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, const double *pair,
+                               cudaStream_t s)
+{
+    if (precision == VPM_FP64)
+        inject_pair_kernel<double><<<1, kThreads, 0, s>>>(static_cast<Part64 *>(d_part), d_n, pair[0],
+                                                          pair[1], pair[2], pair[3], pair[4], pair[5]);
+    else
+        inject_pair_kernel<float><<<1, kThreads, 0, s>>>(static_cast<float4 *>(d_part), d_n, pair[0],
+                                                         pair[1], pair[2], pair[3], pair[4], pair[5]);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ pair-loop throughput probe

@@ -45,7 +45,15 @@ struct RolloutArgs {
     const double *pol_gains, *pol_xbar;
     const float *pol_ubar;
     int pol_offset;
+    // disturbance pair count (0 or 2: the first two records are the pair) of the roots and of
+    // the written-back states, indexed like root_n and out_n (null: none)
+    const int *root_ndist;
+    int *out_ndist;
 };
+// Puts a disturbance pair in front of the n records of a state (one block): records move up by
+// two, the pair takes slots 0 and 1, the count and the pair count are updated on the device.
+cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, const double *pair,
+                               cudaStream_t s);
 
 size_t rollout_smem_bytes(int precision, int cap);
 cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s);
