@@ -450,8 +450,8 @@ vpm_status vpm_freefield_heun_noalloc(float *d_particles, int n, int kernel, dou
 
 /*
  * Feedback NMPC of §IV-C over a manoeuvre of `horizon` steps. A tracking instance of the model
- * (created from h_particles, h_x0) follows the observed glider state. At creation a plan runs
- * from the initial state; then every `replan_every` steps (t > 0, t + latency < horizon, while
+ * (created from h_particles, h_x0) follows the observed glider state. The first control call
+ * plans from the tracking instance (with any pair injected before it); then every `replan_every` steps (t > 0, t + latency < horizon, while
  * draws remain) a plan starts from a copy of the tracking instance with the observed glider
  * state, projected `latency` steps ahead under the current policy. A plan is `iterations` MPPI
  * reweightings (Eq. 25) of `rollouts` rollouts over the remaining steps, warm-started from the
@@ -499,8 +499,13 @@ vpm_status vpm_nmpc_create(const vpm_nmpc_config *cfg, const vpm_params *params,
  */
 vpm_status vpm_nmpc_control(vpm_nmpc *nmpc, int t, const double *h_x_obs, double *h_u);
 
-/* The policy in effect: its first step *t0, h_gains[horizon*7] and h_ubar[horizon] by absolute
- * step, h_xbar[(horizon+1)*7] (rows before t0 unused). Any pointer may be null. */
+/* Puts a disturbance pair (see vpm_state_inject_pair) into the tracking instance: plans started
+ * afterwards account for it (the compensated case of §V). */
+vpm_status vpm_nmpc_inject_pair(vpm_nmpc *nmpc, const double *h_pair);
+
+/* The policy in effect: its first step *t0 (-1 before the first control call), h_gains[horizon*7]
+ * and h_ubar[horizon] by absolute step, h_xbar[(horizon+1)*7] (rows before t0 unused). Any
+ * pointer may be null. */
 vpm_status vpm_nmpc_policy(vpm_nmpc *nmpc, int *t0, double *h_gains, double *h_xbar,
                            float *h_ubar);
 

@@ -66,7 +66,7 @@ def plan(cfg: Config, params: dict, snap: State, mu, t0: int, noise) -> tuple:
     parts = snap.particles
     mu = np.array(mu, np.float64)
     kw = dict(capacity=snap.capacity, gb_prev=snap.gb_prev, glev_prev=snap.glev_prev,
-              has_prev=snap.has_prev)
+              has_prev=snap.has_prev, n_dist=snap.n_dist)
     for it in range(cfg.iterations):
         ctrl = _f32(mu[None, t0:] + eps[it][:, :Hr].astype(np.float64))
         J = np.array([rollout(params, parts, snap.xg, ctrl[i], **kw)["cost"] for i in range(cfg.rollouts)])
@@ -83,14 +83,19 @@ def plan(cfg: Config, params: dict, snap: State, mu, t0: int, noise) -> tuple:
     return mu, Policy(t0, mu.copy(), xbar, gains)
 
 
-def run(cfg: Config, params: dict, parts, x0, mu0, noise, capacity: int, plant_parts=None):
-    """Closed loop against a plant model (the same model; its wake may hold extra particles, a
-    disturbance the planner does not know of). Returns dict(x (N + 1, 7) plant states,
-    u (N,) applied controls, cost, plans (list of t0))."""
+def run(cfg: Config, params: dict, parts, x0, mu0, noise, capacity: int, pair=None,
+        compensate: bool = False):
+    """Closed loop against a plant model (the same model). With `pair` = (x1, z1, g1, x2, z2,
+    g2) the plant's wake holds that disturbance pair from the start; with `compensate` the
+    tracking instance holds it too, so the planner knows of it. Returns dict(x (N + 1, 7) plant
+    states, u (N,) applied controls, cost, plans (list of t0))."""
     N, Pn, L = cfg.horizon, cfg.replan_every, cfg.latency
     tracking = State(params, parts, x0, capacity)
-    pp = parts if plant_parts is None else plant_parts
-    plant = State(params, pp, x0, capacity + len(pp) - len(np.asarray(parts).reshape(-1, 3)))
+    plant = State(params, parts, x0, capacity)
+    if pair is not None:
+        plant.inject_pair(*pair)
+        if compensate:
+            tracking.inject_pair(*pair)
     mu, pol = plan(cfg, params, tracking.copy(), mu0, 0, noise[0])
     plans, pending, used = [0], None, 1
     xs, us = [plant.xg.copy()], []

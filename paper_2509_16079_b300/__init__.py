@@ -86,6 +86,7 @@ _SIGNATURES = {
     "vpm_rollout_batch_policy": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_nmpc_create": ([_VP, _VP, _VP, _I, _I, _VP, _VP, _I, _VP, _VP, _VP, C.POINTER(_VP)], _I),
     "vpm_nmpc_control": ([_VP, _I, _VP, C.POINTER(_D)], _I),
+    "vpm_nmpc_inject_pair": ([_VP, _VP], _I),
     "vpm_nmpc_policy": ([_VP, C.POINTER(_I), _VP, _VP, _VP], _I),
     "vpm_nmpc_stats": ([_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D), C.POINTER(_D)], _I),
     "vpm_nmpc_destroy": ([_VP], _I),
@@ -539,6 +540,10 @@ class NMPC:
         u = C.c_double()
         check(lib().vpm_nmpc_control(self._h, int(t), x.ctypes.data_as(_VP), C.byref(u)))
         return u.value
+
+    def inject_pair(self, x1, z1, g1, x2, z2, g2):
+        a = np.array([x1, z1, g1, x2, z2, g2], dtype=np.float64)
+        check(lib().vpm_nmpc_inject_pair(self._h, a.ctypes.data_as(_VP)))
 
     def policy(self):
         t0 = C.c_int()

@@ -66,6 +66,7 @@ struct vpm_nmpc {
     std::vector<float> mu;        // N, nominal controls by absolute step (planner-owned)
     Policy active, pending;
     bool has_pending = false;
+    bool planned = false;         // the initial plan runs at the first control step
     // threading
     std::thread planner;
     std::mutex m;
@@ -269,11 +270,7 @@ extern "C" vpm_status vpm_nmpc_create(const vpm_nmpc_config *cfg, const vpm_para
     vpm_status st = vpm_state_create(params, h_particles, n, capacity, h_x0, &nm->tracking, nm->ctl);
     if (st == VPM_OK) st = vpm_state_create(params, h_particles, n, capacity, h_x0, &nm->proj, nm->pln);
     if (st != VPM_OK) return cleanup(st);
-    // the first plan, from the initial state, with the draws of plan 0
     nm->next_plan = 1;
-    st = plan(nm, 0, 0, &nm->active);
-    if (st != VPM_OK) return cleanup(st);
-    nm->plans_done = 1;
     if (cfg->threaded) nm->planner = std::thread(planner_loop, nm);
     *out = nm;
     return VPM_OK;
@@ -283,6 +280,21 @@ extern "C" vpm_status vpm_nmpc_control(vpm_nmpc *nm, int t, const double *h_x_ob
 {
     if (!nm || !h_x_obs || !h_u) return fail(VPM_ERR_INVALID, "vpm_nmpc_control: null argument");
     if (t < 0 || t >= nm->N) return fail(VPM_ERR_INVALID, "vpm_nmpc_control: step outside the horizon");
+    if (!nm->planned) {
+        // the first plan, from the tracking instance as it stands (with any injected pair),
+        // with the draws of plan 0; a plan's projection needs none at step 0
+        NCUDA(cudaStreamSynchronize(nm->ctl), "control stream");
+        NTRY(vpm_state_copy(nm->proj, nm->tracking, nm->pln));
+        NTRY(vpm_state_set_glider(nm->proj, h_x_obs, nm->pln));
+        const auto t_start = std::chrono::steady_clock::now();
+        Policy first;
+        NTRY(plan(nm, t, 0, &first));
+        std::unique_lock<std::mutex> lk(nm->m, std::defer_lock);
+        if (nm->cfg.threaded) lk.lock();
+        nm->active = std::move(first);
+        nm->planned = true;
+        record_plan(nm, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count());
+    }
     if (due(nm, t)) {
         if (!nm->cfg.threaded) {
             NCUDA(cudaStreamSynchronize(nm->ctl), "control stream");
@@ -330,6 +342,13 @@ extern "C" vpm_status vpm_nmpc_control(vpm_nmpc *nm, int t, const double *h_x_ob
     NTRY(vpm_step(nm->tracking, u, nullptr, nullptr, nullptr, nullptr, nm->ctl));
     *h_u = u;
     return VPM_OK;
+}
+
+extern "C" vpm_status vpm_nmpc_inject_pair(vpm_nmpc *nm, const double *h_pair)
+{
+    if (!nm || !h_pair) return fail(VPM_ERR_INVALID, "vpm_nmpc_inject_pair: null argument");
+    NCUDA(cudaStreamSynchronize(nm->ctl), "control stream");
+    return vpm_state_inject_pair(nm->tracking, h_pair, nm->ctl);
 }
 
 extern "C" vpm_status vpm_nmpc_policy(vpm_nmpc *nm, int *t0, double *h_gains, double *h_xbar,

@@ -50,17 +50,24 @@ def _cfg(N, threaded=False):
                 qc=W.TVLQR_QC, qf=W.TVLQR_QF, rc=W.TVLQR_RC, threaded=threaded)
 
 
-def test_nmpc_synchronous_matches_oracle(ora):
+@pytest.mark.parametrize("pair", [None, "uncompensated", "compensated"])
+def test_nmpc_synchronous_matches_oracle(ora, pair):
     torch, V = cuda()
     p = dict(W.glider_params(), n_wake_max=60)
     N = 40
     c = _cfg(N)
     noise = W.nmpc_noise(41, 4, c["iterations"], c["rollouts"], N)
     field, x0, mu0 = np.zeros((0, 3)), np.array(W.GLIDER_X0), np.zeros(N, np.float32)
+    ring = (2.5, 0.3, -1.0, 2.5, -0.3, 1.0) if pair else None
     ref = ON.run(ON.Config(N, 10, 5, 16, 2, 10.0, W.TVLQR_QC, W.TVLQR_QF, W.TVLQR_RC),
-                 p, field, x0, mu0.astype(np.float64), noise, 62)
-    nm = V.NMPC(p, field, 62, x0, mu0, noise, precision=V.FP64, **c)
-    plant = V.State(p, field, x0, 62, V.FP64)
+                 p, field, x0, mu0.astype(np.float64), noise, 64, pair=ring,
+                 compensate=pair == "compensated")
+    nm = V.NMPC(p, field, 64, x0, mu0, noise, precision=V.FP64, **c)
+    plant = V.State(p, field, x0, 64, V.FP64)
+    if ring:
+        plant.inject_pair(*ring)
+        if pair == "compensated":
+            nm.inject_pair(*ring)
     xs, us = [plant.glider()], []
     for t in range(N):
         u = nm.control(t, xs[-1])
