@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import math
 import statistics
 import subprocess
 import sys
@@ -525,6 +526,124 @@ def run_policy(args):
         "median_ms": med, "paper_ms_context_only": 9.0, "clocks": clk.summary()}), flush=True)
 
 
+# vortex-ring disturbance of the perch experiments (§V): cores 0.28 apart, self-induced speed
+# 7.5 m/s toward the glider (upper core clockwise), centred ahead of the perch point
+RING_SPEED, RING_SEP, RING_CENTRE = 7.5, 0.28, (4.5, -0.4)
+
+
+def _ring():
+    g = RING_SPEED * 2.0 * math.pi * RING_SEP
+    x, z = RING_CENTRE
+    return (x, z + 0.5 * RING_SEP, -g, x, z - 0.5 * RING_SEP, g)
+
+
+def run_nmpc(args):
+    """Closed-loop perching in simulation with the NMPC of §IV-C at the settings of §V-A:
+    77-step manoeuvre, replanning every 10 steps (10 Hz at dt = 0.01) with a 10-step
+    projection, 256 rollouts x 3 MPPI iterations, TVLQR weights of §V-A, planning on its own
+    thread while the control loop runs paced at 100 Hz against a plant model. Scenarios: the
+    first plan's controls open loop, NMPC, NMPC with a vortex-ring disturbance in the plant
+    unknown to the planner, and with it known. Also the initial-condition sweep of §IV-B:
+    final cost and perch error over the initial forward speed, tracking policy against open
+    loop."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    p = dict(W.glider_params(), n_wake_max=60)
+    N, P_, L, K, IT = 77, 10, 10, 256, 3
+    cap = 64
+    x0 = np.array(W.GLIDER_X0)
+    mu0 = np.zeros(N, np.float32)
+    noise = W.nmpc_noise(61, 8, IT, K, N)
+    cfg = dict(horizon=N, replan_every=P_, latency=L, rollouts=K, iterations=IT, lam=LAMBDA,
+               qc=W.TVLQR_QC, qf=W.TVLQR_QF, rc=W.TVLQR_RC)
+    xd = np.array(p["x_d"])
+
+    def perch_error(x):
+        return float(np.hypot(x[0] - xd[0], x[1] - xd[1]))
+
+    def closed_loop(ring=None, compensate=False):
+        nm = V.NMPC(p, np.zeros((0, 3)), cap, x0, mu0, noise, threaded=True, **cfg)
+        plant = V.State(p, np.zeros((0, 3)), x0, cap)
+        if ring is not None:
+            plant.inject_pair(*ring)
+            if compensate:
+                nm.inject_pair(*ring)
+        ctl_ms = []
+        t_start = time.perf_counter()
+        for t in range(N):
+            wait = t_start + t * p["dt"] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            x = plant.glider()
+            c0 = time.perf_counter()
+            u = nm.control(t, x)
+            ctl_ms.append((time.perf_counter() - c0) * 1e3)
+            plant.step(u)
+        xf = plant.glider()
+        st = nm.stats()
+        first = nm.policy() if ring is None and not compensate else None
+        nm.close()
+        plant.close()
+        return dict(cost=float(np.dot((xf - xd) ** 2, p["q"])), perch_error=perch_error(xf),
+                    control_call_ms_p50=statistics.median(ctl_ms[1:]),
+                    control_call_ms_max=max(ctl_ms[1:]), first_plan_ms=ctl_ms[0], **st), xf
+
+    with ClockSampler(0) as clk:
+        res = {}
+        # the first plan alone, executed open loop
+        nm = V.NMPC(p, np.zeros((0, 3)), cap, x0, mu0, noise, **dict(cfg, replan_every=10 * N))
+        nm.control(0, x0)
+        t0, gains, xbar, ubar = nm.policy()
+        nm.close()
+        ol = V.State(p, np.zeros((0, 3)), x0, cap)
+        for t in range(N):
+            ol.step(float(ubar[t]))
+        xf = ol.glider()
+        ol.close()
+        res["open_loop_first_plan"] = dict(cost=float(np.dot((xf - xd) ** 2, p["q"])), perch_error=perch_error(xf))
+        res["nmpc"] = closed_loop()[0]
+        res["nmpc_ring_uncompensated"] = closed_loop(_ring())[0]
+        res["nmpc_ring_compensated"] = closed_loop(_ring(), True)[0]
+        # initial-condition sweep: forward speed 6 .. 8 m/s, first plan's policy vs open loop
+        root = V.State(p, np.zeros((0, 3)), x0, cap)
+        speeds = np.linspace(6.0, 8.0, 41)
+        X0 = np.tile(x0, (len(speeds), 1))
+        X0[:, 4] = speeds
+        dX0 = torch.tensor(X0, device="cuda")
+        dg, dxb, dub = (torch.tensor(a, device="cuda") for a in (gains, xbar, ubar))
+        cl = root.rollout_policy(len(speeds), N, dg, dxb, dub, 0, x0=dX0)
+        olr = root.rollout_batch(dub[None, :].repeat(len(speeds), 1).contiguous(), x0=dX0)
+        torch.cuda.synchronize()
+        root.close()
+        fcl = cl["final_glider"].cpu().numpy()
+        fol = olr["final_glider"].cpu().numpy()
+        xN = xbar[N]                                 # the nominal plan's final state
+
+        def region(f, ref):
+            ok = speeds[np.hypot(f[:, 0] - ref[0], f[:, 1] - ref[1]) < 0.05]
+            return [float(ok.min()), float(ok.max())] if len(ok) else None
+
+        sweep = dict(speeds=[float(v) for v in speeds[::5]],
+                     cost_policy=[float(v) for v in cl["costs"].cpu().numpy()[::5]],
+                     cost_open_loop=[float(v) for v in olr["costs"].cpu().numpy()[::5]],
+                     final_offset_from_nominal_policy=[float(v) for v in np.hypot(fcl[:, 0] - xN[0], fcl[:, 1] - xN[1])[::5]],
+                     final_offset_from_nominal_open_loop=[float(v) for v in np.hypot(fol[:, 0] - xN[0], fol[:, 1] - xN[1])[::5]],
+                     speeds_within_5cm_of_nominal_end_policy=region(fcl, xN),
+                     speeds_within_5cm_of_nominal_end_open_loop=region(fol, xN),
+                     speeds_within_5cm_of_perch_policy=region(fcl, xd),
+                     speeds_within_5cm_of_perch_open_loop=region(fol, xd))
+    print(json.dumps({
+        "metric": "NMPC closed-loop terminal cost", "value": res["nmpc"]["cost"], "unit": "cost (Eq. 24)",
+        "n_gpus": 1, "higher_is_better": False, "dtype": "f32 pair sums (f64 plate work, policy in f64)",
+        "data": "synthetic",
+        "config": {"workload": "perch manoeuvre in simulation: 77 steps at dt 0.01, replan every 10 steps with a "
+                               "10-step projection, 256 rollouts x 3 MPPI iterations, planner thread, control "
+                               "paced at 100 Hz; ring: cores 0.28 apart moving 7.5 m/s toward the glider"},
+        "scenarios": res, "initial_condition_sweep": sweep, "clocks": clk.summary()}), flush=True)
+
+
 def run_northstar(args):
     """Replan latency at K = 1024 rollouts x H = 100 steps with ~2000-particle fields (1900 -> 2100),
     persistent form against the one-rollout-per-launch form. The latter issues K x H single-block
@@ -745,7 +864,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1", "policy"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1", "policy", "nmpc"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
@@ -773,6 +892,8 @@ def main():
         run_table1(args)
     elif args.workload == "policy":
         run_policy(args)
+    elif args.workload == "nmpc":
+        run_nmpc(args)
     else:
         run_gpu(args)
 
