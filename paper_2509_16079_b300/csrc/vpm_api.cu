@@ -192,6 +192,10 @@ static void fill_dev_params(const vpm_params *p, DevParams &d)
     d.fixed_plate = p->fixed_plate;
     d.chord = p->chord;
     d.lb = p->chord / p->n_b;
+    d.inv_lb = p->n_b / p->chord;
+    d.inv_dt = 1.0 / p->dt;
+    d.inv_mass = 1.0 / p->mass;
+    d.inv_inertia = 1.0 / p->inertia;
     d.span = p->span;
     d.rho = p->rho;
     d.r_core = p->r_core;

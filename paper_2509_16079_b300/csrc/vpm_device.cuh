@@ -34,6 +34,7 @@ struct DevParams {
     double u_inf_x, u_inf_z;
     double dt;
     double mass, inertia, g, l, l_w, l_e, s_e;
+    double inv_dt, inv_lb, inv_mass, inv_inertia;   // reciprocals: no divisions on the plate path
     double q[7], x_d[7];
     // Inverses of the body-frame surface matrix (Eq. 8) for the four shedding variants,
     // index (lev * 2 + tev); each is m x m row-major with m = n_b + lev + tev, stored with a

@@ -127,9 +127,9 @@ __device__ void glider_rhs(const DevParams &p, const double *xg, double ct, doub
     double ex = -p.l * ct - p.l_e * cp, ez = -p.l * st - p.l_e * sp;
     double tq = (wx * fwz - wz * fwx) + (ex * fez - ez * fex) + mw;
     f[0] = xd; f[1] = zd; f[2] = thd; f[3] = u;
-    f[4] = (fwx + fex) / p.mass;
-    f[5] = (fwz + fez) / p.mass - p.g;
-    f[6] = tq / p.inertia;
+    f[4] = (fwx + fex) * p.inv_mass;
+    f[5] = (fwz + fez) * p.inv_mass - p.g;
+    f[6] = tq * p.inv_inertia;
 }
 
 // ------------------------------------------------------------------ step phases
@@ -234,6 +234,17 @@ __device__ void plate_sums_f32(const DevParams &p, Work &w, const float4 *part, 
     if (lane == 0) w.red[0] = gsum;
 }
 
+// Pulls lane i's row of this step's inverse surface matrix into L1 while the plate sums run,
+// so that the solve's row products do not wait on L2.
+__device__ __forceinline__ void prefetch_solve_rows(const DevParams &p, const Geo &G)
+{
+    const int lane = threadIdx.x & 31, m = p.n_b + G.lev + G.tev;
+    const double *ki = p.kinv + (size_t)(G.lev * 2 + G.tev) * kMaxS * kMaxS;
+    for (int i = lane; i < m; i += 32)
+        for (int j = 0; j < m + 15; j += 16)                 // every 128-byte line of the row
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(ki + i * kMaxS + min(j, m - 1)));
+}
+
 // Phase B by one warp (all 32 lanes call it): relative velocity at the plate points (Eq. 12),
 // the surface solve Gamma_S = K^-1 b (Eq. 11), unsteady Bernoulli loads (Eqs. 13-15), the
 // glider's explicit Euler update (Eqs. 18-22) and shedding. Rows of the solve and panels of
@@ -284,7 +295,7 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
     // unsteady Bernoulli pressure (Eq. 13) and panel loads (Eqs. 14-15), one panel per lane;
     // the running sums of Gamma_b up to the panel are formed as in a serial pass
     const bool hp = w.hist[nb + 1] != 0.0;
-    const double dlev = hp ? (w.gs[nb] - w.hist[nb]) / p.dt : 0.0;
+    const double dlev = hp ? (w.gs[nb] - w.hist[nb]) * p.inv_dt : 0.0;
     for (int i = lane; i < nb; i += 32) {
         double cum = 0.0, cum_prev = 0.0;
         for (int k = 0; k <= i; ++k) {
@@ -292,8 +303,8 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
             cum_prev += w.hist[k];
         }
         const double *vb = &w.vt[2 * (nc + i)];
-        double tang = (w.gs[i] / p.lb) * (vb[0] * G.tx + vb[1] * G.tz);
-        double dsum = hp ? (cum - cum_prev) / p.dt : 0.0;
+        double tang = (w.gs[i] * p.inv_lb) * (vb[0] * G.tx + vb[1] * G.tz);
+        double dsum = hp ? (cum - cum_prev) * p.inv_dt : 0.0;
         double dp = p.rho * (tang + dsum + dlev);
         double fx = p.lb * p.span * dp * G.nx, fz = p.lb * p.span * dp * G.nz;
         double si = -0.5 * p.chord + (i + 0.5) * p.lb;
@@ -636,8 +647,10 @@ __device__ void advect_f64(const DevParams &p, Work &w, Part64 *part, const doub
 // records (the disturbance pair, if present) are not part of the wake budget and are left
 // alone. Applying it m = N - d - N_w,max times merges records d..d+m in order and shifts the
 // rest down by m.
+// Kept out of line, as is terminate_pair: inlined into the step, these rarely-taken paths
+// changed the code generated for the pair loop and cost 15 % on large fields (measured).
 template <class R>
-__device__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int n, int d)
+__device__ __noinline__ int merge_oldest(const DevParams &p, typename Store<R>::P *part, int n, int d)
 {
     using P = typename Store<R>::P;
     if (p.n_wake_max <= 0 || n - d <= p.n_wake_max) return n;
@@ -682,7 +695,7 @@ __device__ __forceinline__ double side_of(double ax, double az, double bx, doubl
 }
 
 template <class R>
-__device__ int terminate_pair(const DevParams &p, Work &w, typename Store<R>::P *part, int n)
+__device__ __noinline__ int terminate_pair(const DevParams &p, Work &w, typename Store<R>::P *part, int n)
 {
     __shared__ int s_cross;
     if (threadIdx.x == 0) {
@@ -737,6 +750,7 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
         if (warp == 0) {
             const int lane = tid & 31;
             plate_geometry(p, w);
+            prefetch_solve_rows(p, w.geo);
             if (lane < p.n_b) bound_point_f32(p, w, lane);
             plate_sums_f32<KER>(p, w, part, n);
             __syncwarp();
