@@ -943,7 +943,7 @@ static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStr
     auto k = rollout_kernel<R, KER, NT>;
     // raise the kernel's dynamic shared-memory limit once per size increase (per process;
     // the library runs on one device per process)
-    static size_t granted = 48 * 1024;
+    static size_t granted = 0;          // the 48 KB default covers static + dynamic: always opt in
     if (smem > granted) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -988,7 +988,7 @@ template <class R, int KER, int NT>
 static cudaError_t launch_u(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
     auto k = uneven_kernel<R, KER, NT>;
-    static size_t granted = 48 * 1024;
+    static size_t granted = 0;          // the 48 KB default covers static + dynamic: always opt in
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
     if (smem > granted && cs == cudaStreamCaptureStatusNone) {

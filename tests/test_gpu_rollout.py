@@ -188,3 +188,25 @@ def test_full_size_batch_properties(ora):
     ref = o.step(0.3)
     vel = probe["vel"].cpu().numpy()[:2 * 1202].reshape(-1, 2)
     assert normwise(vel, ref["vel"]) <= VEL_TOL
+
+
+def test_launch_sizes_across_the_48k_default():
+    """Every field size launches in a fresh process, including those whose dynamic shared memory
+    is under 48 KB but whose dynamic + static memory is over it (the default limit covers both)."""
+    import subprocess
+    import sys
+    import textwrap
+    cuda()
+    script = textwrap.dedent("""
+        import numpy as np, torch, workloads as W, paper_2509_16079_b300 as V
+        p = W.glider_params()
+        for n in (1800, 1835, 1900, 1950, 2000, 2040, 1200, 2900, 3100):
+            st = V.State(p, W.background_field(n, n), W.GLIDER_X0, n + 4, V.FP32)
+            st.rollout_batch(torch.tensor(W.mppi_noise(1, 1, 2, 1.0), device="cuda"), want_final=False)
+            torch.cuda.synchronize()
+            st.close()
+        print("ok")
+    """)
+    root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", script], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
