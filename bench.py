@@ -147,15 +147,21 @@ def cpu_baseline(rollouts: int = 16, threads: int | None = None):
 
 
 # ------------------------------------------------------------------ distributed helpers
-def dist_setup(n_gpus: int):
+def dist_setup(n_gpus: int, backend: str = None):
+    """Rank, world size and local rank from the launcher's environment; for N > 1 a process
+    group over NCCL (one GPU per rank), or gloo where no GPU is present."""
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -170,9 +176,16 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job rate of independent replicas: every rank processes the same units, the job
+    ends with the slowest rank."""
+    return units_per_rank * world / max_seconds
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -240,7 +253,7 @@ def run_gpu(args):
     root.status()
 
     pairs_iter = pairs_per_rollout(N0, H) * K_ROLL
-    value = pairs_iter * args.steps * world / (total_ms / 1e3)
+    value = job_throughput(pairs_iter * args.steps, world, total_ms / 1e3)
 
     # replan latency: 3 iterations per replan, events per replan
     rep = []
@@ -275,7 +288,7 @@ def run_gpu(args):
         mu_host.copy_(mu, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = pairs_iter * e2e_steps * world / e2e_s
+    e2e_value = job_throughput(pairs_iter * e2e_steps, world, e2e_s)
 
     if rank != 0:
         return

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libvpm.so")
+# VPM_DEBUG_BOUNDS=1 selects the build with device-side bounds checks (build.py --debug-bounds)
+LIB_PATH = os.path.join(_HERE, "libvpm_debug.so" if os.environ.get("VPM_DEBUG_BOUNDS") == "1"
+                        else "libvpm.so")
 
 VPM_OK, VPM_ERR_INVALID, VPM_ERR_OOM, VPM_ERR_CAPACITY, VPM_ERR_NONFINITE, VPM_ERR_TIMEOUT, \
     VPM_ERR_CUDA, VPM_ERR_BUSY, VPM_ERR_SINGULAR = range(9)

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "vpm_rollout.cuh"
+#include "vpm_trace.cuh"
 
 namespace vpm {
 cudaError_t launch_mppi_weights(const float *J, int K, double lambda, float *w, cudaStream_t s);
@@ -434,7 +435,7 @@ extern "C" vpm_status vpm_state_inject_pair(vpm_state *s, const double *h_pair, 
     CUDA_TRY(cudaMemcpyAsync(cnt, s->d_n, sizeof cnt, cudaMemcpyDeviceToHost, stream), "inject");
     CUDA_TRY(cudaStreamSynchronize(stream), "inject");
     if (cnt[1] != 0) return fail(VPM_ERR_INVALID, "a disturbance pair is already present");
-    CUDA_TRY(launch_inject_pair(s->params.precision, s->d_part, s->d_n, h_pair, stream), "inject launch");
+    CUDA_TRY(launch_inject_pair(s->params.precision, s->d_part, s->d_n, s->capacity, h_pair, stream), "inject launch");
     s->n_upper += 2;
     s->pair_slots = 2;
     return VPM_OK;
@@ -593,6 +594,7 @@ static void base_args(const vpm_state *s, RolloutArgs &a)
 extern "C" vpm_status vpm_step(vpm_state *s, double u, double *d_fm, double *d_gamma_s,
                                double *d_vel, double *d_vtilde, cudaStream_t stream)
 {
+    vpm::TraceRange tr("vpm_step");
     if (!s) return fail(VPM_ERR_INVALID, "null state");
     if (!isfinite(u)) return fail(VPM_ERR_INVALID, "non-finite control");
     if (grown(s, 1) > s->capacity)
@@ -614,6 +616,7 @@ static vpm_status rollout_batch(const vpm_state *s, int K, int H, const double *
                                 const float *d_controls, float *d_costs, double *d_final_glider,
                                 double *d_traj, double *d_field, int *d_count, cudaStream_t stream)
 {
+    vpm::TraceRange tr("vpm_rollout_batch");
     if (!s || !d_controls || !d_costs) return fail(VPM_ERR_INVALID, "null argument");
     if (K < 1 || H < 1) return fail(VPM_ERR_INVALID, "K and H must be positive");
     const long long need = grown(s, H);

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "vpm_rollout.cuh"
+#include "vpm_trace.cuh"
 
 namespace vpm {
 vpm_status report_error(vpm_status st, const char *msg);
@@ -274,6 +275,7 @@ extern "C" vpm_status vpm_batch_rollout(vpm_batch *b, int H, const float *d_cont
                                         float *d_costs, int *d_count, double *d_final_glider,
                                         int use_graph, cudaStream_t stream)
 {
+    vpm::TraceRange tr("vpm_batch_rollout");
     if (!b || !d_controls || !d_costs) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: null argument");
     if (H < 1 || H > b->max_h) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: need 1 <= H <= %d", b->max_h);
     for (int c = 0; c < kNumClasses; ++c)

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/vpm.h"
+#include "vpm_trace.cuh"
 
 namespace vpm {
 vpm_status report_error(vpm_status st, const char *msg);
@@ -111,6 +112,7 @@ vpm_status upload_policy(vpm_nmpc *nm, const Policy &p, cudaStream_t s)
 // the draws of plan `pi`. Runs on the planner stream; returns the new policy in *out.
 vpm_status plan(vpm_nmpc *nm, int t0, int pi, Policy *out)
 {
+    vpm::TraceRange tr("nmpc: plan (MPPI + least squares + TVLQR)");
     const int N = nm->N, K = nm->K, Hr = N - t0, it_n = nm->cfg.iterations;
     cudaStream_t s = nm->pln;
     const double dt = nm->params.dt;
@@ -173,6 +175,7 @@ vpm_status plan(vpm_nmpc *nm, int t0, int pi, Policy *out)
 vpm_status replan(vpm_nmpc *nm, int t, const double *x_obs, const Policy &pol, int pi, Policy *out,
                   double *ms)
 {
+    vpm::TraceRange tr("nmpc: replan (projection + plan)");
     const auto t_start = std::chrono::steady_clock::now();
     const int L = nm->cfg.latency;
     NTRY(upload_policy(nm, pol, nm->pln));
@@ -280,6 +283,7 @@ extern "C" vpm_status vpm_nmpc_control(vpm_nmpc *nm, int t, const double *h_x_ob
 {
     if (!nm || !h_x_obs || !h_u) return fail(VPM_ERR_INVALID, "vpm_nmpc_control: null argument");
     if (t < 0 || t >= nm->N) return fail(VPM_ERR_INVALID, "vpm_nmpc_control: step outside the horizon");
+    vpm::TraceRange tr("nmpc: control step");
     if (!nm->planned) {
         // the first plan, from the tracking instance as it stands (with any injected pair),
         // with the draws of plan 0; a plan's projection needs none at step 0

@@ -14,6 +14,14 @@
 
 namespace vpm {
 
+// Device-side bounds checks (build with -DVPM_DEBUG_BOUNDS=1): a record written past the
+// block's capacity is skipped and the rollout's status gets the capacity flag (reported as
+// VPM_ERR_CAPACITY); nothing traps. Off by default: the host's count bounds make them redundant.
+#ifndef VPM_DEBUG_BOUNDS
+#define VPM_DEBUG_BOUNDS 0
+#endif
+constexpr bool kDebugBounds = VPM_DEBUG_BOUNDS;   // (the Work field it needs is compiled in too)
+
 struct Geo {
     double xw, zw, tx, tz, nx, nz, vx, vz, om;
     double ct, st;                   // cos and sin of the pitch angle
@@ -43,6 +51,9 @@ struct Work {
     int flag;
     int chunk_next;                  // next unclaimed target chunk of the pair sums
     int ndist;                       // 2 while the first two records are the disturbance pair
+#if VPM_DEBUG_BOUNDS
+    int cap;                         // records the shared arrays hold
+#endif
 };
 
 // ------------------------------------------------------------------ geometry (warp 0)
@@ -349,8 +360,15 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
             x += ds * G.tx; z += ds * G.tz; g = w.gs[nb + 1];
         }
         const int k = lane == 0 ? 0 : lev;
-        part[n + k] = Store<R>::make(x, z, g);
-        if constexpr (sizeof(R) == 4) w.fresh[k] = part[n + k];
+#if VPM_DEBUG_BOUNDS
+        if (n + k >= w.cap) {                        // the host's count bound was wrong
+            atomicOr(&w.flag, (int)kStCapacity);
+        } else
+#endif
+        {
+            part[n + k] = Store<R>::make(x, z, g);
+            if constexpr (sizeof(R) == 4) w.fresh[k] = part[n + k];
+        }
     }
     __syncwarp();
     return n + lev + tev;
@@ -811,6 +829,9 @@ __device__ void load_state(const RolloutArgs &a, Work &w, typename Store<R>::P *
     if (threadIdx.x == 0) {
         w.n = n; w.flag = 0; w.chunk_next = 0;
         w.ndist = a.root_ndist ? a.root_ndist[(a.root_stride || a.root_offset) ? rid : 0] : 0;
+#if VPM_DEBUG_BOUNDS
+        w.cap = a.cap;
+#endif
     }
     __syncthreads();
 }
@@ -1067,11 +1088,13 @@ int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem)
 
 template <class R>
 __global__ void __launch_bounds__(kThreads) inject_pair_kernel(typename Store<R>::P *part, int *d_n,
-                                                              double x1, double z1, double g1,
-                                                              double x2, double z2, double g2)
+                                                              int cap, double x1, double z1,
+                                                              double g1, double x2, double z2,
+                                                              double g2)
 {
     using P = typename Store<R>::P;
     const int n = d_n[0];
+    if (kDebugBounds && n + 2 > cap) return;         // the host checked the capacity
     // move records up by two, top chunk first (each chunk's targets are read before written)
     for (int top = n; top > 0; top -= (int)blockDim.x) {
         const int i = top - 1 - (int)threadIdx.x;
@@ -1089,15 +1112,15 @@ __global__ void __launch_bounds__(kThreads) inject_pair_kernel(typename Store<R>
     }
 }
 
-cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, const double *pair,
+cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, int cap, const double *pair,
                                cudaStream_t s)
 {
     if (precision == VPM_FP64)
-        inject_pair_kernel<double><<<1, kThreads, 0, s>>>(static_cast<Part64 *>(d_part), d_n, pair[0],
-                                                          pair[1], pair[2], pair[3], pair[4], pair[5]);
+        inject_pair_kernel<double><<<1, kThreads, 0, s>>>(static_cast<Part64 *>(d_part), d_n, cap,
+                                                          pair[0], pair[1], pair[2], pair[3], pair[4], pair[5]);
     else
-        inject_pair_kernel<float><<<1, kThreads, 0, s>>>(static_cast<float4 *>(d_part), d_n, pair[0],
-                                                         pair[1], pair[2], pair[3], pair[4], pair[5]);
+        inject_pair_kernel<float><<<1, kThreads, 0, s>>>(static_cast<float4 *>(d_part), d_n, cap,
+                                                         pair[0], pair[1], pair[2], pair[3], pair[4], pair[5]);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ struct RolloutArgs {
 };
 // Puts a disturbance pair in front of the n records of a state (one block): records move up by
 // two, the pair takes slots 0 and 1, the count and the pair count are updated on the device.
-cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, const double *pair,
+cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, int cap, const double *pair,
                                cudaStream_t s);
 
 size_t rollout_smem_bytes(int precision, int cap);

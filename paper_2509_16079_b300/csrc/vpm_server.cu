@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "../../include/vpm.h"
+#include "vpm_trace.cuh"
 
 namespace vpm {
 vpm_status report_error(vpm_status st, const char *msg);
@@ -105,6 +106,7 @@ static size_t request_bytes(int K, int H)
 // Enqueues one request on its slot's stream. Called by the worker with the lock held.
 static vpm_status start_request(vpm_server *s, Slot &sl, const Request &r)
 {
+    vpm::TraceRange tr("server: start request");
     const int K = r.K, H = r.H;
     float *pin = sl.pinned;
     memcpy(pin, r.eps.data(), sizeof(float) * (size_t)K * H);
