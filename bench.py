@@ -657,6 +657,58 @@ def run_nmpc(args):
         "scenarios": res, "initial_condition_sweep": sweep, "clocks": clk.summary()}), flush=True)
 
 
+def run_plate(args):
+    """Configuration 1: the fixed flat plate at 45 degrees in a unit stream with the disturbance pair
+    (Gaussian core 0.05 c, no decay, shedding every step), 200 steps in binary64 on the GPU, one
+    block; the FP64 oracle runs the same input on the host for the error and the CPU time."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    import oracle
+    build.build()
+    oracle.build()
+    p = W.plate_c1_params()
+    steps = 200
+    parts, xg, cap = W.plate_c1_initial(0, steps)
+    st = V.State(p, parts, xg, cap, V.FP64)
+    zero = torch.zeros((1, steps), dtype=torch.float32, device="cuda")
+    st.rollout_batch(zero, want_final=False)                      # warm-up
+    torch.cuda.synchronize()
+    ts = []
+    with ClockSampler(0) as clk:
+        for _ in range(max(3, args.steps // 4)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = st.rollout_batch(zero, want_final=False, want_field=True)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    n = int(out["count"][0])
+    field = out["field"][0, :n].cpu().numpy()
+    t0 = time.perf_counter()
+    ref = oracle.rollout(p, parts, xg, np.zeros(steps), capacity=cap, want_field=True)
+    cpu_s = time.perf_counter() - t0
+    err = float(np.abs(field[:, :2] - ref["field"][:, :2]).max())
+    pairs = 0
+    m = len(parts)
+    for _ in range(steps):
+        pairs += m * (2 * int(p["n_b"]) + 1)
+        m += 2
+        pairs += m * (m + int(p["n_b"]))
+    ms = statistics.median(ts)
+    print(json.dumps({
+        "metric": "Biot-Savart pair-interactions/s", "value": pairs / (ms / 1e3),
+        "unit": "pair-interactions/s", "n_gpus": 1, "steps": len(ts), "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fixed plate at 45 deg, unit stream, disturbance pair 2c upstream, Gaussian core "
+                               "0.05c, 200 steps (2 -> 402 particles), binary64, one rollout (one block)",
+                   "pairs_per_run": pairs},
+        "error_vs_fp64_oracle": {"max_position_difference": err, "particles": n},
+        "cpu_baseline": {"value": pairs / cpu_s, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+                         "sample": "the same 200-step run, FP64 C oracle, one thread, %.2f s" % cpu_s},
+        "clocks": clk.summary()}), flush=True)
+
+
 def run_northstar(args):
     """Replan latency at K = 1024 rollouts x H = 100 steps with ~2000-particle fields (1900 -> 2100),
     persistent form against the one-rollout-per-launch form. The latter issues K x H single-block
@@ -877,7 +929,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1", "policy", "nmpc"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1", "policy", "nmpc", "plate"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
@@ -907,6 +959,8 @@ def main():
         run_policy(args)
     elif args.workload == "nmpc":
         run_nmpc(args)
+    elif args.workload == "plate":
+        run_plate(args)
     else:
         run_gpu(args)
 
