@@ -701,7 +701,7 @@ def run_plate(args):
         "unit": "pair-interactions/s", "n_gpus": 1, "steps": len(ts), "ms_per_step": ms,
         "higher_is_better": True, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "fixed plate at 45 deg, unit stream, disturbance pair 2c upstream, Gaussian core "
-                               "0.05c, 200 steps (2 -> 402 particles), binary64, one rollout (one block)",
+                               "0.05c, 200 steps (2 -> 402 particles), binary64, one rollout (one cluster of SMs)",
                    "pairs_per_run": pairs},
         "error_vs_fp64_oracle": {"max_position_difference": err, "particles": n},
         "cpu_baseline": {"value": pairs / cpu_s, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",

@@ -155,8 +155,12 @@ template <> struct PairF64<VPM_KERNEL_VATISTAS> {
     }
 };
 template <> struct PairF64<VPM_KERNEL_GAUSSIAN> {
+    // Beyond r^2 / delta^2 = 50, e^(-r^2/delta^2) < 2e-22 and 1 - e^(-r^2/delta^2) is 1 to binary64
+    // precision: the exponential (the costly part on a narrow FP64 pipe) is skipped there.
     __device__ __forceinline__ static double q(double r2, double, double inv_rc2) {
-        return r2 > 0.0 ? -expm1(-r2 * inv_rc2) / r2 : 0.0;
+        const double x = r2 * inv_rc2;
+        if (x >= 50.0) return 1.0 / r2;
+        return r2 > 0.0 ? -expm1(-x) / r2 : 0.0;
     }
 };
 template <> struct PairF64<VPM_KERNEL_SINGULAR> {

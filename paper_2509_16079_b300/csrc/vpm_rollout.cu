@@ -10,6 +10,8 @@
 // 13-15); the glider's explicit Euler update (Eqs. 18-22); LEV/TEV appended to the wake;
 // convection velocities of Eq. 16 for every wake particle; explicit Euler advection and the
 // decay of Eq. 17; merging of the two oldest particles while N > N_w,max.
+#include <cooperative_groups.h>
+
 #include "vpm_rollout.cuh"
 
 namespace vpm {
@@ -991,11 +993,22 @@ size_t rollout_smem_bytes(int precision, int cap)
                                  : (size_t)cap * (sizeof(float4) + sizeof(float2));
 }
 
+// Rollouts per launch up to which the binary64 path uses one cluster per rollout.
+constexpr int kClusterRollouts = 9;
+template <int KER>
+static cudaError_t launch_cluster_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s);
+
 cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s)
 {
     const size_t smem = rollout_smem_bytes(precision, a.cap);
     const int ker = a.p.kernel;
     if (precision == VPM_FP64) {
+        // a few multi-step rollouts without single-step probes: one cluster of SMs per rollout
+        if (grid <= kClusterRollouts && a.H > 1 && !a.probe_fm && !a.probe_gs && !a.probe_vel && !a.probe_vt) {
+            if (ker == VPM_KERNEL_GAUSSIAN) return launch_cluster_t<VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
+            if (ker == VPM_KERNEL_SINGULAR) return launch_cluster_t<VPM_KERNEL_SINGULAR>(a, grid, smem, s);
+            return launch_cluster_t<VPM_KERNEL_VATISTAS>(a, grid, smem, s);
+        }
         if (ker == VPM_KERNEL_GAUSSIAN) return launch_t<double, VPM_KERNEL_GAUSSIAN, 128>(a, grid, smem, s);
         if (ker == VPM_KERNEL_SINGULAR) return launch_t<double, VPM_KERNEL_SINGULAR, 128>(a, grid, smem, s);
         return launch_t<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
@@ -1082,6 +1095,174 @@ int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem)
     if (kernel == VPM_KERNEL_SINGULAR) { VPM_OCC(VPM_KERNEL_SINGULAR) }
     VPM_OCC(VPM_KERNEL_VATISTAS)
 #undef VPM_OCC
+}
+
+// ------------------------------------------------------------------ one binary64 rollout per cluster
+
+// A few binary64 rollouts (a single simulation, configuration 1) spread over a thread-block
+// cluster: every CTA holds the whole field; the plate-point sums and the convection targets are
+// split across the CTAs, each CTA broadcasts its results (plate velocities, advected records) to
+// every CTA's shared memory through distributed shared memory, and hardware cluster barriers
+// separate the phases. The small serial plate work (geometry, solve, loads, glider, shedding,
+// termination, merging) runs redundantly on every CTA from identical data. Every target's sum is
+// formed in the same order as on the one-block path, so the results are the same bits.
+template <int KER>
+__global__ void __launch_bounds__(kThreads) cluster_rollout_kernel(const RolloutArgs a)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int rid = (int)(blockIdx.x / C) + a.rid0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Part64 *part = reinterpret_cast<Part64 *>(smem);
+    double2 *vel = reinterpret_cast<double2 *>(smem + sizeof(Part64) * (size_t)a.cap);
+    __shared__ Work w;
+    const DevParams &p = a.p;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
+    load_state<double>(a, w, part, rid);
+    int n = w.n;
+    cl.sync();
+    for (int k = 0; k < a.H; ++k) {
+        double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k] : a.u_const;
+        if (a.pol_gains && warp == 0) {
+            const size_t j = (size_t)a.pol_offset + k;
+            double fb = (double)a.pol_ubar[j];
+            for (int c = 0; c < 7; ++c) fb -= a.pol_gains[j * 7 + c] * (w.xg[c] - a.pol_xbar[j * 7 + c]);
+            u = (a.controls ? u : 0.0) + fb;
+        }
+        if (warp == 0) plate_geometry(p, w);
+        __syncthreads();
+        // plate-point sums (Eq. 12): target t on CTA t mod C, written into every CTA
+        const int M = p.n_c + p.n_b;
+        for (int t = rank + C * warp; t < M; t += C * nwarps) {
+            double tx, tz;
+            plate_point(p, w.geo, t, tx, tz);
+            double su = 0.0, sw = 0.0;
+            for (int j = lane; j < n; j += 32) {
+                const Part64 sj = part[j];
+                const double dx = tx - sj.x, dz = tz - sj.z;
+                const double g = sj.g * PairF64<KER>::q(fma(dx, dx, dz * dz), p.rc4, p.inv_rc2);
+                su = fma(-dz, g, su);
+                sw = fma(dx, g, sw);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                su += __shfl_xor_sync(0xffffffffu, su, o);
+                sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            }
+            if (lane < C) {
+                double *rv = cl.map_shared_rank(&w.vt[0], lane);
+                rv[2 * t] = su * kInv2Pi;
+                rv[2 * t + 1] = sw * kInv2Pi;
+            }
+        }
+        // Kelvin sum (Eq. 7), the same partition as the one-block path, on every CTA
+        double gsum = 0.0;
+        for (int j = tid; j < n; j += (int)blockDim.x) gsum += part[j].g;
+        for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+        if (lane == 0) w.red[warp] = gsum;
+        cl.sync();
+        if (warp == 0) {
+            const int m = plate_solve<double>(p, w, part, n, u, nwarps);
+            if (lane == 0) w.n = m;
+        }
+        __syncthreads();
+        const int n1 = w.n;
+        // convection of this CTA's slice of targets (Eq. 16), sources in the one-block order.
+        // Slots go round-robin over the warps first: binary64 throughput is per SM partition,
+        // so a small slice still keeps all four partitions busy.
+        const int per = (n1 + C - 1) / C, lo = min(n1, rank * per), hi = min(n1, lo + per);
+        const int slot0 = warp + nwarps * lane, slot_step = nwarps * 32;
+        const Geo &G = w.geo;
+        for (int i = lo + slot0; i < hi; i += slot_step) {
+            const Part64 pi = part[i];
+            double su = 0.0, sw = 0.0;
+            for (int j = 0; j < n1; ++j) {
+                const Part64 sj = part[j];
+                const double dx = pi.x - sj.x, dz = pi.z - sj.z;
+                const double g = sj.g * PairF64<KER>::q(fma(dx, dx, dz * dz), p.rc4, p.inv_rc2);
+                su = fma(-dz, g, su);
+                sw = fma(dx, g, sw);
+            }
+            for (int j = 0; j < p.n_b; ++j) {
+                const double sj = -0.5 * p.chord + (j + 0.5) * p.lb;
+                const double dx = pi.x - (G.xw + sj * G.tx), dz = pi.z - (G.zw + sj * G.tz);
+                const double r2 = fma(dx, dx, dz * dz);
+                const double q = r2 > 0.0 ? w.gs[j] / r2 : 0.0;
+                su = fma(-dz, q, su);
+                sw = fma(dx, q, sw);
+            }
+            vel[i] = make_double2(su * kInv2Pi + p.u_inf_x, sw * kInv2Pi + p.u_inf_z);
+        }
+        cl.sync();                                   // every CTA is done reading the positions
+        bool bad = false;
+        for (int i = lo + slot0; i < hi; i += slot_step) {
+            Part64 q = part[i];
+            const double2 v = vel[i];
+            bad |= !(isfinite(v.x) && isfinite(v.y));
+            q.x += p.dt * v.x;
+            q.z += p.dt * v.y;
+            q.g *= p.decay;
+            for (int r = 0; r < C; ++r) cl.map_shared_rank(part, r)[i] = q;
+        }
+        if (bad) atomicOr(&w.flag, (int)kStNonFinite);
+        cl.sync();                                   // the advected field is complete everywhere
+        int nn = n1;
+        if (w.ndist == 2) nn = terminate_pair<double>(p, w, part, nn);
+        n = merge_oldest<double>(p, part, nn, w.ndist);
+        if (rank == 0 && a.traj && tid < 7) a.traj[((size_t)rid * a.H + k) * 7 + tid] = w.xg[tid];
+    }
+    if (tid == 0) {
+        w.n = n;
+        if (rank != 0 && w.flag) atomicOr(cl.map_shared_rank(&w.flag, 0), w.flag);
+    }
+    cl.sync();
+    if (rank == 0) {
+        if (a.out_part) store_state<double>(a, w, part, rid);
+        finish<double>(a, w, part, rid);
+    }
+}
+
+template <int KER>
+static cudaError_t launch_cluster_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    auto k = cluster_rollout_kernel<KER>;
+    static size_t granted = 0;
+    static int csize = 0;
+    if (smem > granted) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        granted = smem;
+    }
+    if (!csize) {                                    // 16 CTAs where the part allows, else 8
+        csize = 8;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(16);
+            q.blockDim = dim3(kThreads);
+            q.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = 16; at.val.clusterDim.y = 1; at.val.clusterDim.z = 1;
+            q.attrs = &at;
+            q.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k, &q) == cudaSuccess && clusters > 0) csize = 16;
+        }
+        cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid * csize);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = csize; attr.val.clusterDim.y = 1; attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ disturbance injection

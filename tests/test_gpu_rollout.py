@@ -210,3 +210,27 @@ def test_launch_sizes_across_the_48k_default():
     root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", script], cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("case", ["plate", "glider"])
+def test_fp64_cluster_path_matches_one_block_bitwise(case):
+    """Up to 9 binary64 rollouts run one cluster of SMs each; 10 run one block each. The same
+    rollouts through both paths give the same bits."""
+    torch, V = cuda()
+    if case == "plate":
+        p = W.plate_c1_params()
+        field, xg, cap = W.plate_c1_initial(2, 60)
+        ctrl = np.zeros((10, 60), np.float32)
+    else:
+        p = dict(W.glider_params(), n_wake_max=150)
+        field, xg = W.background_field(12, 120), np.array(W.GLIDER_X0)
+        ctrl = W.mppi_noise(13, 10, 60, W.MPPI_SIGMA_U)
+        cap = 152
+    st = V.State(p, field, xg, cap, V.FP64)
+    c = torch.tensor(ctrl, device="cuda")
+    big = st.rollout_batch(c, want_traj=True, want_field=True)                   # one block each
+    small = st.rollout_batch(c[:9].contiguous(), want_traj=True, want_field=True)  # one cluster each
+    torch.cuda.synchronize()
+    for k in ("costs", "final_glider", "traj", "count", "field"):
+        assert torch.equal(big[k][:9], small[k]), k
+    st.close()
