@@ -230,14 +230,15 @@ __device__ void plate_sums_f32(const DevParams &p, Work &w, const float4 *part, 
                 v[g] += __shfl_xor_sync(0xffffffffu, v[g], o);
             }
         }
-        if (lane == 0) {
+        // every lane holds the full sums; lane g converts and scales target t0 + g (binary64
+        // instructions cost a full issue slot on the FP64 pipe however few lanes run them)
+        float ug = u[0], vg = v[0];
 #pragma unroll
-            for (int g = 0; g < kPlateG; ++g) {
-                if (t0 + g < M) {
-                    w.vt[2 * (t0 + g)] = (double)u[g] * kInv2Pi;
-                    w.vt[2 * (t0 + g) + 1] = (double)v[g] * kInv2Pi;
-                }
-            }
+        for (int g = 1; g < kPlateG; ++g)
+            if (lane == g) { ug = u[g]; vg = v[g]; }
+        if (lane < kPlateG && t0 + lane < M) {
+            w.vt[2 * (t0 + lane)] = (double)ug * kInv2Pi;
+            w.vt[2 * (t0 + lane) + 1] = (double)vg * kInv2Pi;
         }
     }
     float gs = 0.f, gc = 0.f;
