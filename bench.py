@@ -883,7 +883,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step = 8
+    per_step = max(8, os.cpu_count() or 1)      # one rollout per host core
     vals = []
     t_all = 0.0
     for j in range(args.warmup + args.steps):
