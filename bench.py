@@ -71,6 +71,26 @@ def profiled_traffic(summary: str, source: str):
     return int(m.group(1)) if digest == m.group(2) else None
 
 
+def profiled_pipes(summary: str, source: str):
+    """Pipe utilisation (% of peak) of the kernel's ncu full-set capture recorded in
+    profiles/<summary>, or None when the kernel source has changed since."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2509_16079_b300", "csrc", source)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    m = re.search(r"pipes_pct:\s*fma ([0-9.]+) xu ([0-9.]+) fp64 ([0-9.]+) issue ([0-9.]+) source ([0-9a-f]{16})",
+                  open(path).read())
+    if not m:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != m.group(5):
+        return None
+    return {"fma_pipe_pct": float(m.group(1)), "mufu_pipe_pct": float(m.group(2)),
+            "fp64_pipe_pct": float(m.group(3)), "issue_active_pct": float(m.group(4)),
+            "capture": "ncu --set full, K=1024, H=10 (profiles/%s)" % summary}
+
+
 # ------------------------------------------------------------------ clocks during the run
 class ClockSampler:
     def __init__(self, index: int):
@@ -297,6 +317,7 @@ def run_gpu(args):
     achieved = pairs_iter * FLOPS_PER_PAIR / roll_avg_s / 1e12
     peak = fp32_peak_tflops()
     traffic = profiled_traffic("rollout_kernel_mppi_c2.md", "vpm_rollout.cu")
+    pipes = profiled_pipes("rollout_kernel_mppi_c2.md", "vpm_rollout.cu")
     line = {
         "metric": "Biot-Savart pair-interactions/s",
         "value": value,
@@ -325,7 +346,7 @@ def run_gpu(args):
         "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "rollout_kernel<float, Vatistas>",
+                     "kernel": "rollout_kernel<float, Vatistas>", "pipes": pipes,
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (FMA = 2 flops)",
                      "rollout_ms": statistics.mean(roll_ms)},
         "clocks": clocks,
