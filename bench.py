@@ -160,10 +160,24 @@ def cpu_baseline(rollouts: int = 16, threads: int | None = None):
         list(ex.map(lambda i: oracle.rollout(p, field, xg0, eps[i].astype(np.float64)), range(rollouts)))
     dt = time.perf_counter() - t0
     pairs = pairs_per_rollout(N0, H) * rollouts
-    return {"value": pairs / dt, "unit": "pair-interactions/s", "cores": min(threads, rollouts),
+    cores = min(threads, rollouts)
+    return {"value": pairs / dt, "unit": "pair-interactions/s", "cores": cores,
             "kind": "oracle",
             "sample": "%d of the %d rollouts (1000 particles, 100 steps, FP64 C oracle), %.1f s wall"
-                      % (rollouts, K_ROLL, dt)}
+                      % (rollouts, K_ROLL, dt),
+            "per_core": pairs / dt / cores, "cpu_model": cpu_model(),
+            "hardware_threads": os.cpu_count(),
+            "iteration_s_extrapolated": dt * K_ROLL / rollouts}
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 # ------------------------------------------------------------------ distributed helpers
