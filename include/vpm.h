@@ -193,6 +193,15 @@ vpm_status vpm_step(vpm_state *state, double u, double *d_fm, double *d_gamma_s,
                     double *d_vtilde, cudaStream_t stream);
 
 /*
+ * Device bytes of the pair-sum scratch that a batch of K rollouts of H steps from this state
+ * allocates while it runs (0 for binary64 states and fields that stay within 128 particles).
+ * Each block of the binary32 rollout kernel keeps, per step, the sums formed when one
+ * evaluation of a particle pair serves both particles: about cap^2 / 256 float2 slots for a
+ * field that can reach cap particles. Errors: VPM_ERR_INVALID (null, K or H < 1).
+ */
+vpm_status vpm_rollout_scratch_bytes(const vpm_state *state, int K, int H, size_t *bytes);
+
+/*
  * K independent rollouts of H steps from the root model, which is not modified. Rollout i
  * applies elevator rates d_controls[i*H + k] (binary32, K x H row-major). One thread block
  * holds one rollout's field in shared memory for the whole horizon. Outputs (device):
@@ -202,6 +211,9 @@ vpm_status vpm_step(vpm_state *state, double u, double *d_fm, double *d_gamma_s,
  *   d_traj[K*H*7]            glider state after every step (binary64), or null
  *   d_field[K*capacity*3]    final wake (x, z, Gamma) per rollout (binary64), or null
  *   d_count[K]               final particle count per rollout, or null
+ * Binary32 roots whose field can grow past 128 particles need device scratch for the pair
+ * sums (vpm_rollout_scratch_bytes); it is allocated on `stream` from the device's default
+ * memory pool for the launch and freed after it (stream-ordered).
  * Errors: VPM_ERR_INVALID (K, H < 1, null controls/costs), VPM_ERR_CAPACITY (the count could
  * exceed the capacity within H steps), VPM_ERR_CUDA.
  */
@@ -419,6 +431,12 @@ vpm_status vpm_server_submit(vpm_server *server, int scenario, int K, int H, con
 vpm_status vpm_server_poll(vpm_server *server, long long ticket, int timeout_ms,
                            vpm_server_result *out, float *h_mu_out);
 
+/* Device bytes that admission counts for a request of K rollouts over H steps on `scenario`
+ * taken after advance_steps committed steps: its own buffers (noise, controls, costs, weights,
+ * reweighted controls) plus the rollouts' pair-sum scratch (vpm_rollout_scratch_bytes). */
+vpm_status vpm_server_request_bytes(vpm_server *server, int scenario, int K, int H,
+                                    int advance_steps, size_t *bytes);
+
 /* Rollouts completed so far, requests queued, requests and bytes on the device. */
 vpm_status vpm_server_stats(vpm_server *server, long long *completed_rollouts, int *queued,
                             int *in_flight, size_t *in_flight_bytes);
@@ -526,7 +544,11 @@ vpm_status vpm_nmpc_destroy(vpm_nmpc *nmpc);
  *   VPM_PROBE_EX2       MUFU base-2 exponentials per second,
  *   VPM_PROBE_PAIRS_T1/T2/T4  pair interactions per second of the rollout kernel's binary32
  *                       pair loop (Vatistas kernel) with 1, 2 or 4 targets per lane, every block
- *                       summing a 1024-particle field held in its shared memory.
+ *                       summing a 1024-particle field held in its shared memory, every pair
+ *                       evaluated once per target;
+ *   VPM_PROBE_PAIRS_SYM pair interactions per second (n^2 per field) of the rollout kernel's
+ *                       binary32 pair phase as it runs: one evaluation per particle pair across
+ *                       128-particle rows, diagonal groups, partial sums combined per particle.
  * blocks_per_sm must lie in 1..7. The call allocates and frees its own device scratch, runs on
  * the legacy default stream of the current device and synchronises it. Errors:
  * VPM_ERR_INVALID for an unknown probe or block count, VPM_ERR_CUDA for a CUDA failure.
@@ -537,7 +559,8 @@ typedef enum {
     VPM_PROBE_EX2 = 2,
     VPM_PROBE_PAIRS_T1 = 3,
     VPM_PROBE_PAIRS_T2 = 4,
-    VPM_PROBE_PAIRS_T4 = 5
+    VPM_PROBE_PAIRS_T4 = 5,
+    VPM_PROBE_PAIRS_SYM = 6
 } vpm_probe;
 
 vpm_status vpm_probe_rate(int probe, int blocks_per_sm, double *h_rate);

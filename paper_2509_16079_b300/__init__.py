@@ -78,6 +78,7 @@ _SIGNATURES = {
     "vpm_state_load": ([_VP, _VP, C.c_size_t, _VP], _I),
     "vpm_step": ([_VP, _D, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_rollout_batch": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "vpm_rollout_scratch_bytes": ([_VP, _I, _I, C.POINTER(C.c_size_t)], _I),
     "vpm_rollout_batch_x0": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_state_set_glider": ([_VP, _VP, _VP], _I),
     "vpm_state_inject_pair": ([_VP, _VP, _VP], _I),
@@ -112,6 +113,7 @@ _SIGNATURES = {
     "vpm_server_add_scenario": ([_VP, C.POINTER(Params), _VP, _I, _I, _VP, C.POINTER(_I)], _I),
     "vpm_server_submit": ([_VP, _I, _I, _I, _VP, _VP, _F, _I, _F, C.POINTER(C.c_longlong)], _I),
     "vpm_server_poll": ([_VP, C.c_longlong, _I, _VP, _VP], _I),
+    "vpm_server_request_bytes": ([_VP, _I, _I, _I, _I, C.POINTER(C.c_size_t)], _I),
     "vpm_server_stats": ([_VP, C.POINTER(C.c_longlong), C.POINTER(_I), C.POINTER(_I),
                           C.POINTER(C.c_size_t)], _I),
     "vpm_server_read_scenario": ([_VP, _I, _VP, C.POINTER(_I), _VP], _I),
@@ -320,6 +322,12 @@ class State:
                                           stream_handle(stream)))
         return out
 
+    def rollout_scratch_bytes(self, K: int, H: int) -> int:
+        """Device bytes of pair-sum scratch a batch of K rollouts of H steps allocates."""
+        b = C.c_size_t()
+        check(lib().vpm_rollout_scratch_bytes(self._h, int(K), int(H), C.byref(b)))
+        return b.value
+
     def rollout_batch_per_launch(self, controls, stream=None):
         import torch
         controls = _dev_tensor(controls, torch.float32)
@@ -397,6 +405,13 @@ class Server:
         check(st)
         res = {k: getattr(r, k) for k, _ in ServerResult._fields_}
         return res, mu[:r.H].copy()
+
+    def request_bytes(self, scenario: int, K: int, H: int, advance_steps: int = 0) -> int:
+        """Device bytes admission counts for such a request (buffers plus rollout scratch)."""
+        b = C.c_size_t()
+        check(lib().vpm_server_request_bytes(self._h, int(scenario), int(K), int(H),
+                                             int(advance_steps), C.byref(b)))
+        return b.value
 
     def stats(self):
         done, q, f, b = C.c_longlong(), C.c_int(), C.c_int(), C.c_size_t()
@@ -608,7 +623,7 @@ def tvlqr(ahat, bhat, dt: float, qc, qf, rc: float, stream=None):
     return gains, s0
 
 
-PROBE_FFMA, PROBE_RSQRT, PROBE_EX2, PROBE_PAIRS_T1, PROBE_PAIRS_T2, PROBE_PAIRS_T4 = range(6)
+PROBE_FFMA, PROBE_RSQRT, PROBE_EX2, PROBE_PAIRS_T1, PROBE_PAIRS_T2, PROBE_PAIRS_T4, PROBE_PAIRS_SYM = range(7)
 
 
 def probe_rate(probe: int, blocks_per_sm: int = 7) -> float:

@@ -579,6 +579,24 @@ static int after_steps(const vpm_state *s, int steps)
     return (int)g;
 }
 
+// Device bytes of the binary32 pair-sum scratch that a batch of K rollouts of H steps, taken
+// after `advance` more committed steps, allocates while it runs (the serving loop's admission).
+namespace vpm {
+size_t rollout_scratch_bytes(const vpm_state *s, int K, int H, int advance)
+{
+    long long cap = grown(s, H + advance);
+    if (cap > s->capacity) cap = s->capacity;
+    return sizeof(float2) * (size_t)K * (size_t)rollout_rev_slots(s->params.precision, (int)cap);
+}
+}  // namespace vpm
+
+extern "C" vpm_status vpm_rollout_scratch_bytes(const vpm_state *s, int K, int H, size_t *bytes)
+{
+    if (!s || !bytes || K < 1 || H < 1) return fail(VPM_ERR_INVALID, "vpm_rollout_scratch_bytes: null or K, H < 1");
+    *bytes = vpm::rollout_scratch_bytes(s, K, H, 0);
+    return VPM_OK;
+}
+
 static void base_args(const vpm_state *s, RolloutArgs &a)
 {
     memset(&a, 0, sizeof a);
@@ -721,6 +739,11 @@ extern "C" vpm_status vpm_rollout_batch_per_launch(const vpm_state *s, int K, in
     CUDA_TRY(cudaMallocAsync((void **)&ns, sizeof(int) * 2 * K, stream), "per-launch scratch");
     CUDA_TRY(cudaMallocAsync((void **)&gl, sizeof(double) * stride * K, stream), "per-launch scratch");
     CUDA_TRY(cudaMallocAsync((void **)&hi, sizeof(double) * stride * K, stream), "per-launch scratch");
+    // pair-sum scratch of the one block every launch runs, allocated once for all launches
+    const long long rev_slots = rollout_rev_slots(s->params.precision, cap);
+    float2 *rev = nullptr;
+    if (rev_slots > 0)
+        CUDA_TRY(cudaMallocAsync((void **)&rev, sizeof(float2) * (size_t)rev_slots, stream), "per-launch scratch");
     // replicate the root into every rollout's slot (a zero-step launch of the rollout kernel)
     RolloutArgs a;
     base_args(s, a);
@@ -736,6 +759,7 @@ extern "C" vpm_status vpm_rollout_batch_per_launch(const vpm_state *s, int K, in
     a.H = 1;
     a.controls = d_controls; a.ctrl_stride = H;
     a.costs = d_costs;
+    a.rev = rev; a.rev_stride = rev_slots;
     for (int k = 0; k < H && e == cudaSuccess; ++k) {
         a.step0 = k;
         for (int i = 0; i < K && e == cudaSuccess; ++i) {
@@ -751,6 +775,7 @@ extern "C" vpm_status vpm_rollout_batch_per_launch(const vpm_state *s, int K, in
     if (e2 == cudaSuccess) e2 = cudaFreeAsync(ns, stream);
     if (e2 == cudaSuccess) e2 = cudaFreeAsync(gl, stream);
     if (e2 == cudaSuccess) e2 = cudaFreeAsync(hi, stream);
+    if (e2 == cudaSuccess && rev) e2 = cudaFreeAsync(rev, stream);
     if (e != cudaSuccess) return cuda_fail(e, "per-launch rollout");
     if (e2 != cudaSuccess) return cuda_fail(e2, "per-launch scratch free");
     return VPM_OK;

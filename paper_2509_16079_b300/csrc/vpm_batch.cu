@@ -56,6 +56,8 @@ struct BatchClass {
     float tuned_ms = 0.f;
     std::vector<int> items;      // rollout indices, largest first
     int *d_order = nullptr;
+    float2 *d_rev = nullptr;     // pair-sum scratch of the persistent blocks (binary32)
+    size_t rev_blocks = 0;       // blocks it holds
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
 };
@@ -94,6 +96,7 @@ static void batch_free(vpm_batch *b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (auto &c : b->cls) {
         cudaFree(c.d_order);
+        cudaFree(c.d_rev);
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
     }
@@ -241,6 +244,19 @@ static cudaError_t prepare_class(vpm_batch *b, int c, int nt)
     const int per_sm = uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, smem);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     k.grid = std::min<int>((int)k.items.size(), per_sm * b->sms);
+    // scratch for the grid's blocks; a captured graph that holds the old buffer is dropped
+    const long long slots = rollout_rev_slots(b->params.precision, k.cap);
+    if (slots > 0 && (size_t)k.grid > k.rev_blocks) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return e;
+        cudaFree(k.d_rev);
+        k.d_rev = nullptr;
+        k.rev_blocks = 0;
+        e = cudaMalloc((void **)&k.d_rev, sizeof(float2) * (size_t)slots * (size_t)k.grid);
+        if (e != cudaSuccess) return e;
+        k.rev_blocks = (size_t)k.grid;
+    }
     return cudaSuccess;
 }
 
@@ -263,6 +279,8 @@ static cudaError_t enqueue_classes(vpm_batch *b, int H, const float *ctrl, float
         a.order = k.d_order;
         a.counter = b->d_counters + c;
         a.n_items = (int)k.items.size();
+        a.rev = k.d_rev;
+        a.rev_stride = rollout_rev_slots(b->params.precision, k.cap);
         e = cudaStreamWaitEvent(k.stream, b->fork, 0);
         if (!e) e = launch_uneven(b->params.precision, a, grid, nt, k.stream);
         if (!e) e = cudaEventRecord(k.done, k.stream);

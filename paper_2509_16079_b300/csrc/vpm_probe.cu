@@ -74,7 +74,7 @@ extern "C" vpm_status vpm_probe_rate(int probe, int blocks_per_sm, double *h_rat
     using vpm::report_error;
     char msg[160];
     if (!h_rate) return report_error(VPM_ERR_INVALID, "vpm_probe_rate: null rate pointer");
-    if (probe < VPM_PROBE_FFMA || probe > VPM_PROBE_PAIRS_T4)
+    if (probe < VPM_PROBE_FFMA || probe > VPM_PROBE_PAIRS_SYM)
         return report_error(VPM_ERR_INVALID, "vpm_probe_rate: unknown probe");
     if (blocks_per_sm < 1 || blocks_per_sm > 7)
         return report_error(VPM_ERR_INVALID, "vpm_probe_rate: blocks_per_sm must lie in 1..7");
@@ -123,20 +123,24 @@ extern "C" vpm_status vpm_probe_rate(int probe, int blocks_per_sm, double *h_rat
         for (int i = 0; i < n; ++i)
             h[i] = make_float4((float)(6.0 * next()), (float)(3.0 * next() - 1.5),
                                (float)(0.02 * next() - 0.01), 0.f);
+        const bool sym = probe == VPM_PROBE_PAIRS_SYM;
         float4 *d_src = nullptr;
-        float2 *d_out = nullptr;
+        float2 *d_out = nullptr, *d_scr = nullptr;
         e = cudaMalloc(&d_src, sizeof(float4) * n);
         if (!e) e = cudaMalloc(&d_out, sizeof(float2) * (size_t)n * grid);
+        if (!e && sym) e = cudaMalloc(&d_scr, sizeof(float2) * (size_t)vpm::rollout_rev_slots(VPM_FP32, n) * grid);
         if (!e) e = cudaMemcpy(d_src, h.data(), sizeof(float4) * n, cudaMemcpyHostToDevice);
         for (int pass = 0; pass < 2 && !e; ++pass) {
             if (pass == 1) cudaEventRecord(t.a);
-            e = vpm::launch_pair_probe(tpl, grid, n, pass ? reps : 1, 0.05, d_src, d_out, 0);
+            e = sym ? vpm::launch_pair_probe_sym(grid, n, pass ? reps : 1, 0.05, d_src, d_out, d_scr, 0)
+                    : vpm::launch_pair_probe(tpl, grid, n, pass ? reps : 1, 0.05, d_src, d_out, 0);
             if (pass == 1) cudaEventRecord(t.b);
         }
         if (!e) e = cudaEventSynchronize(t.b);
         if (!e) e = cudaEventElapsedTime(&ms, t.a, t.b);
         cudaFree(d_src);
         cudaFree(d_out);
+        cudaFree(d_scr);
         work = (double)grid * reps * (double)n * n;
     }
     if (e) {

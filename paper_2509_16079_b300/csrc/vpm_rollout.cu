@@ -12,6 +12,8 @@
 // decay of Eq. 17; merging of the two oldest particles while N > N_w,max.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "vpm_rollout.cuh"
 
 namespace vpm {
@@ -382,22 +384,44 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
 // Binary32 path. The sum over pairs of particles that existed before this step's shedding
 // does not depend on the surface solve, so it runs while warp 0 does the plate work; only the
 // bound vortices and the freshly shed vortices need Gamma_S, and their terms are added after.
-// The old-old sum is split into chunks of consecutive targets that the warps claim from a
-// shared counter; lane l of a chunk starting at b owns targets b + l + 32 k, k < T. Sources
-// stream from shared memory by broadcast loads, each serving T pairs; plain sums over tiles of
-// kTile sources are added into Kahan-compensated totals. Every target's sum is formed by one
-// lane in a fixed order, so the result does not depend on which warp claimed it or on T.
+//
+// The pair factor of every kernel (Eqs. 4-5, and the Gaussian core) depends on the distance
+// alone, and the displacement changes sign when the two particles swap roles, so one
+// evaluation of a pair serves both particles' sums. The n old particles form rows of kRow
+// (row a: particles kRow a .. kRow a + kRow - 1), and the work comes in two kinds of units:
+//   * off-diagonal row a: the row's particles (4 per lane) against every later particle, in
+//     blocks of 32 sources. A block takes 32 rounds; in round r lane l takes source
+//     (l + r) mod 32 for its 4 targets, adds the forward terms to its targets' sums and the
+//     reverse terms to the source's running sum, which then moves one lane down. After the 32
+//     rounds lane l holds source l's sum over the row's targets and stores it in the block's
+//     scratch slot of (row a, source); the targets' compensated sums over the later particles
+//     are kept in their own scratch slots;
+//   * diagonal group g: kDiagGroup targets against the kRow particles of their own row, every
+//     pair in both orders; written to vel.
+// Plain sums over 64 sources (two blocks) are added into Kahan-compensated totals. The
+// finalize phase adds, per particle, its diagonal sum, its row's forward sum and the reverse
+// sums of the earlier rows, in that order. Every partial sum is formed by one warp in a fixed
+// order, whichever warp claims it and however many warps the block has.
 constexpr int kTile = 64;
 #ifndef VPM_SRC_UNROLL
 #define VPM_SRC_UNROLL 4      // sources in flight per inner-loop iteration
 #endif
 constexpr int kSrcUnroll = VPM_SRC_UNROLL;
+#ifndef VPM_ROT_UNROLL
+#define VPM_ROT_UNROLL 8      // rounds in flight per iteration of the rotation loop
+#endif
+constexpr int kRotUnroll = VPM_ROT_UNROLL;
+constexpr int kRow = 128;     // targets of an off-diagonal row (4 per lane)
+#ifndef VPM_DIAG_T
+#define VPM_DIAG_T 2          // targets per lane of a diagonal group (1, 2 or 4)
+#endif
+constexpr int kDiagT = VPM_DIAG_T, kDiagGroup = 32 * kDiagT;
 
 
-// Sources 0 .. n-1; targets base + lane + 32 k below lim.
+// Sources s0 .. s1-1; targets base + lane + 32 k below lim.
 template <int KER, int T>
 __device__ __forceinline__ void old_pairs_chunk(const DevParams &p, const float4 *part,
-                                                float2 *vel, int n, int base, int lim)
+                                                float2 *vel, int s0, int s1, int base, int lim)
 {
     const int lane = threadIdx.x & 31;
     const float rc4s = (float)p.rc4, irc2 = (float)p.inv_rc2;
@@ -410,8 +434,8 @@ __device__ __forceinline__ void old_pairs_chunk(const DevParams &p, const float4
         tz[k] = q.y;
         su[k] = cu[k] = sw[k] = cw[k] = 0.f;
     }
-    for (int j0 = 0; j0 < n; j0 += kTile) {
-        const int je = min(n, j0 + kTile);
+    for (int j0 = s0; j0 < s1; j0 += kTile) {
+        const int je = min(s1, j0 + kTile);
         float au[T], aw[T];
 #pragma unroll
         for (int k = 0; k < T; ++k) au[k] = aw[k] = 0.f;
@@ -439,64 +463,168 @@ __device__ __forceinline__ void old_pairs_chunk(const DevParams &p, const float4
     }
 }
 
-// Guided chunk schedule over the n old targets: chunks of kBulk targets first (kBulk / 32
-// targets per lane, fewer shared-memory loads per pair), then 64-target chunks, and the last
-// kTail32 targets in 32-target chunks so that the warps finish the phase close together.
-// Every target's sum is formed by one lane in the same order whatever chunk holds it.
-#ifndef VPM_BULK
-#define VPM_BULK 128          // targets per bulk chunk: 128 (4 per lane) or 64 (2 per lane)
-#endif
-#ifndef VPM_TAIL32
-#define VPM_TAIL32 128        // targets at the end of the list served in 32-target chunks
-#endif
-#ifndef VPM_MID64
-#define VPM_MID64 256         // targets before the tail served in 64-target chunks
-#endif
-constexpr int kBulk = VPM_BULK, kTail32 = VPM_TAIL32, kMid64 = VPM_MID64;
+// Scratch of one block, in float2 slots (sized by the launch's capacity cap, cap32 = cap
+// rounded up to 32; an even count, so every block's scratch is 16-byte aligned): the
+// Kahan-compensated forward sums of the rows' targets as float4 (u sum, w sum, u compensation,
+// w compensation) at [0, 2 cap32), then for each row a < ceil(cap / kRow) - 1 the reverse sums
+// of sources kRow (a + 1) .. cap32 - 1.
+__host__ __device__ inline long long rev_row_base(int a, int cap32)
+{
+    return (long long)cap32 * (a + 2) - (long long)(kRow / 2) * a * (a + 1);
+}
 
-struct ChunkPlan {
-    int n_bulk, n_mid, c_bulk, c_mid, nchunks;
+__host__ __device__ inline long long rev_slots(int cap)
+{
+    if (cap <= kRow) return 0;                 // a single row: no off-diagonal work
+    const int cap32 = (cap + 31) & ~31, rows = (cap + kRow - 1) / kRow;
+    return (rev_row_base(rows - 1, cap32) + 1) & ~1LL;     // even: 16-byte aligned blocks
+}
+
+// One block of 32 sources b0 .. b0+31 (all below n when FULL; else the ones at or above n
+// take no part) against the 4 targets per lane of an off-diagonal row. On return lane l holds
+// the reverse sum of source b0 + l in (ru, rw).
+template <int KER, bool FULL>
+__device__ __forceinline__ void rotate_block(const DevParams &p, const float4 *part, int n, int b0,
+                                             const float (&tx)[4], const float (&tz)[4],
+                                             const float (&tg)[4], float (&fu)[4], float (&fw)[4],
+                                             float &ru, float &rw)
+{
+    const int lane = threadIdx.x & 31;
+    const float rc4s = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    ru = rw = 0.f;
+#pragma unroll kRotUnroll
+    for (int r = 0; r < 32; ++r) {
+        const int j = b0 + ((lane + r) & 31);
+        float4 s;
+        if (FULL) {
+            s = part[j];
+        } else {
+            s = part[j < n ? j : n - 1];
+            if (j >= n) s.z = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dx = tx[k] - s.x, dz = tz[k] - s.y;
+            const float q = PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4s, irc2);
+            const float gs = s.z * q, gt = tg[k] * q;
+            fu[k] = fmaf(-dz, gs, fu[k]);
+            fw[k] = fmaf(dx, gs, fw[k]);
+            ru = fmaf(dz, gt, ru);
+            rw = fmaf(-dx, gt, rw);
+        }
+        ru = __shfl_sync(0xffffffffu, ru, (lane + 1) & 31);
+        rw = __shfl_sync(0xffffffffu, rw, (lane + 1) & 31);
+    }
+}
+
+// Adds the plain sums of the last 64 sources (fu, fw) into the compensated forward sums of row
+// a's targets, kept in the block's scratch rather than in registers (the rotation loop needs
+// them); `first` starts them from zero.
+__device__ __forceinline__ void fold_row(float4 *kst, int a, float (&fu)[4], float (&fw)[4], bool first)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4 st = first ? make_float4(0.f, 0.f, 0.f, 0.f) : kst[kRow * a + 32 * k + lane];
+        kahan_add(st.x, st.z, fu[k]);
+        kahan_add(st.y, st.w, fw[k]);
+        kst[kRow * a + 32 * k + lane] = st;
+        fu[k] = fw[k] = 0.f;
+    }
+}
+
+// Off-diagonal row a (kRow (a + 1) < n, so all of its targets exist).
+template <int KER>
+__device__ void offdiag_row(const DevParams &p, const float4 *part, float2 *scr, int cap32, int n,
+                            int a)
+{
+    const int lane = threadIdx.x & 31;
+    float tx[4], tz[4], tg[4], fu[4], fw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 q = part[kRow * a + 32 * k + lane];
+        tx[k] = q.x;
+        tz[k] = q.y;
+        tg[k] = q.z;
+        fu[k] = fw[k] = 0.f;
+    }
+    float4 *kst = reinterpret_cast<float4 *>(scr);
+    float2 *rrow = scr + (rev_row_base(a, cap32) - (long long)kRow * (a + 1));   // by source index
+    int b0 = kRow * (a + 1);                   // a multiple of 64: fold after every odd block
+    bool first = true;
+    for (; b0 + 32 <= n; b0 += 32) {
+        float ru, rw;
+        rotate_block<KER, true>(p, part, n, b0, tx, tz, tg, fu, fw, ru, rw);
+        rrow[b0 + lane] = make_float2(ru, rw);
+        if (b0 & 32) {
+            fold_row(kst, a, fu, fw, first);
+            first = false;
+        }
+    }
+    if (b0 < n) {
+        float ru, rw;
+        rotate_block<KER, false>(p, part, n, b0, tx, tz, tg, fu, fw, ru, rw);
+        if (b0 + lane < n) rrow[b0 + lane] = make_float2(ru, rw);
+    }
+    fold_row(kst, a, fu, fw, first);
+}
+
+struct PairPlan {
+    int rows_off;   // off-diagonal rows (units 0 .. rows_off - 1, longest first)
+    int nunits;     // then the diagonal groups of kDiagGroup targets
 };
 
-__device__ __forceinline__ ChunkPlan chunk_plan(int n)
+__device__ __forceinline__ PairPlan pair_plan(int n)
 {
-    ChunkPlan c;
-    const int head = max(0, n - kTail32 - kMid64);
-    c.n_bulk = (head / kBulk) * kBulk;
-    c.n_mid = max(0, n - kTail32 - c.n_bulk);
-    c.c_bulk = c.n_bulk / kBulk;
-    c.c_mid = (c.n_mid + 63) / 64;
-    c.nchunks = c.c_bulk + c.c_mid + (n - c.n_bulk - c.n_mid + 31) / 32;
+    PairPlan c;
+    const int rows = (n + kRow - 1) / kRow;
+    c.rows_off = rows > 1 ? rows - 1 : 0;
+    c.nunits = c.rows_off + (n + kDiagGroup - 1) / kDiagGroup;
     return c;
 }
 
-// Chunks are claimed from a counter that is never reset within a rollout: every warp makes
-// exactly one failing claim per step, so a step consumes nchunks + nwarps claims and every
+// Units are claimed from a counter that is never reset within a rollout: every warp makes
+// exactly one failing claim per step, so a step consumes nunits + nwarps claims and every
 // thread can track the counter's base for the next step without a barrier.
 template <int KER>
-__device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, float2 *vel, int n,
-                              const ChunkPlan &cp, int claim_base)
+__device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, float2 *vel,
+                              float2 *scr, int cap32, int n, const PairPlan &pp, int claim_base)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
         int c = 0;
         if (lane == 0) c = atomicAdd(&w.chunk_next, 1) - claim_base;
         c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= cp.nchunks) break;
-        if (c < cp.c_bulk) {
-            old_pairs_chunk<KER, kBulk / 32>(p, part, vel, n, c * kBulk, n);
-        } else if (c < cp.c_bulk + cp.c_mid) {
-            const int base = cp.n_bulk + 64 * (c - cp.c_bulk);
-            const int lim = cp.n_bulk + cp.n_mid;
-            if (lim - base > 32)
-                old_pairs_chunk<KER, 2>(p, part, vel, n, base, lim);
-            else
-                old_pairs_chunk<KER, 1>(p, part, vel, n, base, lim);
+        if (c >= pp.nunits) break;
+        if (c < pp.rows_off) {
+            offdiag_row<KER>(p, part, scr, cap32, n, c);
         } else {
-            const int base = cp.n_bulk + cp.n_mid + 32 * (c - cp.c_bulk - cp.c_mid);
-            old_pairs_chunk<KER, 1>(p, part, vel, n, base, n);
+            const int g = c - pp.rows_off, t0 = kDiagGroup * g, r0 = (t0 / kRow) * kRow;
+            old_pairs_chunk<KER, kDiagT>(p, part, vel, r0, min(r0 + kRow, n), t0, n);
         }
     }
+}
+
+// The old-old sum of target i < n: its diagonal sum (in vel), then its row's forward sum and
+// the reverse sums of the earlier rows (scratch).
+__device__ __forceinline__ float2 old_sum(const float2 *vel, const float2 *scr, int cap32,
+                                          int rows_off, int i)
+{
+    const int row = i / kRow;
+    float2 v = vel[i];
+    if (row == 0 && rows_off == 0) return v;
+    float cu = 0.f, cw = 0.f;
+    if (row < rows_off) {
+        const float4 f = reinterpret_cast<const float4 *>(scr)[i];
+        kahan_add(v.x, cu, f.x - f.z);
+        kahan_add(v.y, cw, f.y - f.w);
+    }
+    for (int a = 0; a < row; ++a) {
+        const float2 r = scr[rev_row_base(a, cap32) + i - (long long)kRow * (a + 1)];
+        kahan_add(v.x, cu, r.x);
+        kahan_add(v.y, cw, r.y);
+    }
+    return make_float2(v.x - cu, v.y - cw);
 }
 
 // Bound vortices (singular kernel, Eq. 4) at a target with double-length displacements.
@@ -570,7 +698,8 @@ __device__ void fresh_velocities_f32(const DevParams &p, Work &w, const float4 *
 // thread that owns it, so no barrier separates the velocity from the advection.
 template <int KER>
 __device__ void finalize_advect_f32(const DevParams &p, Work &w, float4 *part, const float2 *vel,
-                                    int n, int n1, double *probe_vel)
+                                    const float2 *scr, int cap32, int rows_off, int n, int n1,
+                                    double *probe_vel)
 {
     const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
     const float inv2pi = (float)kInv2Pi;
@@ -585,7 +714,7 @@ __device__ void finalize_advect_f32(const DevParams &p, Work &w, float4 *part, c
         float xl, zl;
         if (i < n) {
             q = part[i];
-            const float2 raw = vel[i];
+            const float2 raw = old_sum(vel, scr, cap32, rows_off, i);
             unpack_lo(q.w, xl, zl);
             float bu = 0.f, bw = 0.f;
             bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
@@ -779,9 +908,18 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
             if (lane == 0) w.n = m;
             fresh_velocities_f32<KER>(p, w, part, n, m);
         }
-        const ChunkPlan cp = chunk_plan(n);
-        old_pairs_f32<KER>(p, w, part, vel, n, cp, claim_base);
-        claim_base += cp.nchunks + (int)(blockDim.x >> 5);
+        const PairPlan pp = pair_plan(n);
+        const int cap32 = (a.cap + 31) & ~31;
+        float2 *scr = a.rev ? a.rev + (size_t)blockIdx.x * a.rev_stride : nullptr;
+#if VPM_DEBUG_BOUNDS
+        if (pp.rows_off > 0 && (!scr || a.rev_stride < rev_slots(a.cap) || n > a.cap)) {
+            if (tid == 0) atomicOr(&w.flag, (int)kStCapacity);   // the host's scratch was short
+            __syncthreads();
+            return;
+        }
+#endif
+        old_pairs_f32<KER>(p, w, part, vel, scr, cap32, n, pp, claim_base);
+        claim_base += pp.nunits + (int)(blockDim.x >> 5);
         __syncthreads();
         n1 = w.n;
         if (probe) {
@@ -790,7 +928,8 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
             if (a.probe_gs) for (int t = tid; t < p.n_b + 2; t += (int)blockDim.x) a.probe_gs[t] = w.gs[t];
             if (a.probe_fm && tid < 3) a.probe_fm[tid] = w.fm[tid];
         }
-        finalize_advect_f32<KER>(p, w, part, vel, n, n1, probe ? a.probe_vel : nullptr);
+        finalize_advect_f32<KER>(p, w, part, vel, scr, cap32, pp.rows_off, n, n1,
+                                 probe ? a.probe_vel : nullptr);
     } else {
         if (warp == 0) plate_geometry(p, w);
         __syncthreads();
@@ -988,6 +1127,47 @@ static cudaError_t launch_f32(const RolloutArgs &a, int grid, size_t smem, cudaS
     return launch_t<float, KER, 128>(a, grid, smem, s);
 }
 
+long long rollout_rev_slots(int precision, int cap)
+{
+    return precision == VPM_FP64 ? 0 : rev_slots(cap);
+}
+
+// Stream-ordered allocations of the pair-sum scratch come from the device's default pool,
+// which keeps freed memory for the next launch instead of returning it at every synchronise.
+static void keep_pool_memory()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            unsigned long long keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
+}
+
+// Runs launch(args) with the binary32 pair-sum scratch in place: the caller's, or one
+// allocated on the stream for the launch's blocks and freed after it (stream-ordered, so
+// launches on other streams get their own).
+template <class F>
+static cudaError_t with_rev_scratch(const RolloutArgs &a, int grid, cudaStream_t s, F launch)
+{
+    const long long slots = rev_slots(a.cap);
+    if (slots == 0 || a.rev || a.H == 0) return launch(a);
+    keep_pool_memory();
+    RolloutArgs b = a;
+    void *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, sizeof(float2) * (size_t)slots * (size_t)grid, s);
+    if (e != cudaSuccess) return e;
+    b.rev = static_cast<float2 *>(buf);
+    b.rev_stride = slots;
+    e = launch(b);
+    const cudaError_t e2 = cudaFreeAsync(buf, s);
+    return e != cudaSuccess ? e : e2;
+}
+
 size_t rollout_smem_bytes(int precision, int cap)
 {
     return precision == VPM_FP64 ? (size_t)cap * (sizeof(Part64) + sizeof(double2))
@@ -1014,9 +1194,11 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
         if (ker == VPM_KERNEL_SINGULAR) return launch_t<double, VPM_KERNEL_SINGULAR, 128>(a, grid, smem, s);
         return launch_t<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
     }
-    if (ker == VPM_KERNEL_GAUSSIAN) return launch_f32<VPM_KERNEL_GAUSSIAN>(a, grid, smem, s);
-    if (ker == VPM_KERNEL_SINGULAR) return launch_f32<VPM_KERNEL_SINGULAR>(a, grid, smem, s);
-    return launch_f32<VPM_KERNEL_VATISTAS>(a, grid, smem, s);
+    return with_rev_scratch(a, grid, s, [&](const RolloutArgs &b) {
+        if (ker == VPM_KERNEL_GAUSSIAN) return launch_f32<VPM_KERNEL_GAUSSIAN>(b, grid, smem, s);
+        if (ker == VPM_KERNEL_SINGULAR) return launch_f32<VPM_KERNEL_SINGULAR>(b, grid, smem, s);
+        return launch_f32<VPM_KERNEL_VATISTAS>(b, grid, smem, s);
+    });
 }
 
 template <class R, int KER, int NT>
@@ -1053,9 +1235,11 @@ cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt,
         if (ker == VPM_KERNEL_SINGULAR) return launch_u<double, VPM_KERNEL_SINGULAR, 128>(a, grid, smem, s);
         return launch_u<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
     }
-    if (ker == VPM_KERNEL_GAUSSIAN) return launch_u_nt<float, VPM_KERNEL_GAUSSIAN>(a, grid, nt, smem, s);
-    if (ker == VPM_KERNEL_SINGULAR) return launch_u_nt<float, VPM_KERNEL_SINGULAR>(a, grid, nt, smem, s);
-    return launch_u_nt<float, VPM_KERNEL_VATISTAS>(a, grid, nt, smem, s);
+    return with_rev_scratch(a, grid, s, [&](const RolloutArgs &b) {
+        if (ker == VPM_KERNEL_GAUSSIAN) return launch_u_nt<float, VPM_KERNEL_GAUSSIAN>(b, grid, nt, smem, s);
+        if (ker == VPM_KERNEL_SINGULAR) return launch_u_nt<float, VPM_KERNEL_SINGULAR>(b, grid, nt, smem, s);
+        return launch_u_nt<float, VPM_KERNEL_VATISTAS>(b, grid, nt, smem, s);
+    });
 }
 
 // Sets the kernel's dynamic shared-memory limit to at least smem and returns the resident
@@ -1323,9 +1507,56 @@ __global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) pair_probe_kernel(co
     const int warp = threadIdx.x >> 5, nwarps = (int)blockDim.x >> 5;
     for (int r = 0; r < reps; ++r)
         for (int base = 32 * T * warp; base < n; base += 32 * T * nwarps)
-            old_pairs_chunk<VPM_KERNEL_VATISTAS, T>(p, part, vel, n, base, n);
+            old_pairs_chunk<VPM_KERNEL_VATISTAS, T>(p, part, vel, 0, n, base, n);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += (int)blockDim.x) out[(size_t)blockIdx.x * n + i] = vel[i];
+}
+
+// The rollout kernel's binary32 pair phase as it runs (rows with one evaluation per pair,
+// diagonal groups, claims from a shared counter, then every particle's partial sums combined),
+// `reps` times over the same n records.
+__global__ void __launch_bounds__(kThreads, VPM_MIN_BLOCKS) pair_probe_sym_kernel(const float4 *src,
+                                                                              float2 *out,
+                                                                              float2 *scratch,
+                                                                              long long stride,
+                                                                              int n, int reps,
+                                                                              float rc4)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *part = reinterpret_cast<float4 *>(smem);
+    float2 *vel = reinterpret_cast<float2 *>(smem + sizeof(float4) * (size_t)n);
+    __shared__ Work w;
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) part[i] = src[i];
+    if (threadIdx.x == 0) w.chunk_next = 0;
+    __syncthreads();
+    DevParams p = {};
+    p.rc4 = rc4;
+    float2 *scr = scratch + (size_t)blockIdx.x * stride;
+    const PairPlan pp = pair_plan(n);
+    const int cap32 = (n + 31) & ~31;
+    int claim_base = 0;
+    for (int r = 0; r < reps; ++r) {
+        old_pairs_f32<VPM_KERNEL_VATISTAS>(p, w, part, vel, scr, cap32, n, pp, claim_base);
+        claim_base += pp.nunits + (int)(blockDim.x >> 5);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += (int)blockDim.x) {
+            const float2 v = old_sum(vel, scr, cap32, pp.rows_off, i);
+            if (r == reps - 1) out[(size_t)blockIdx.x * n + i] = v;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_pair_probe_sym(int grid, int n, int reps, double r_core, const float4 *d_src,
+                                  float2 *d_out, float2 *d_scratch, cudaStream_t s)
+{
+    const size_t smem = (size_t)n * (sizeof(float4) + sizeof(float2));
+    const float rc4 = (float)(r_core * r_core * r_core * r_core);
+    cudaError_t e = cudaFuncSetAttribute(pair_probe_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    pair_probe_sym_kernel<<<grid, kThreads, smem, s>>>(d_src, d_out, d_scratch, rev_slots(n), n, reps, rc4);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pair_probe(int t, int grid, int n, int reps, double r_core, const float4 *d_src,

@@ -49,6 +49,10 @@ struct RolloutArgs {
     // the written-back states, indexed like root_n and out_n (null: none)
     const int *root_ndist;
     int *out_ndist;
+    // binary32 path: per-block scratch of the pair sums (rev_stride float2 slots per block,
+    // at least rollout_rev_slots(cap); null: the launcher allocates it around the launch)
+    float2 *rev;
+    long long rev_stride;
 };
 // Puts a disturbance pair in front of the n records of a state (one block): records move up by
 // two, the pair takes slots 0 and 1, the count and the pair count are updated on the device.
@@ -56,6 +60,9 @@ cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, int cap, c
                                cudaStream_t s);
 
 size_t rollout_smem_bytes(int precision, int cap);
+// float2 slots of pair-sum scratch one block of the binary32 path needs for capacity cap
+// (0: none; the binary64 path needs none).
+long long rollout_rev_slots(int precision, int cap);
 cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s);
 // Persistent launch over a.n_items rollouts with `nt` threads per block (128, 256 or 512; the
 // binary64 path uses 128); `grid` blocks claim rollouts in a.order through a.counter.
@@ -68,5 +75,9 @@ int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem);
 // writes its raw sums to d_out[b n ...].
 cudaError_t launch_pair_probe(int t, int grid, int n, int reps, double r_core, const float4 *d_src,
                               float2 *d_out, cudaStream_t s);
+// The pair phase of the binary32 rollout kernel itself (one evaluation per particle pair across
+// rows, d_scratch holding grid x rollout_rev_slots(VPM_FP32, n) float2), `reps` times.
+cudaError_t launch_pair_probe_sym(int grid, int n, int reps, double r_core, const float4 *d_src,
+                                  float2 *d_out, float2 *d_scratch, cudaStream_t s);
 
 }  // namespace vpm

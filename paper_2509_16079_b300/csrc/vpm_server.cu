@@ -29,6 +29,7 @@
 
 namespace vpm {
 vpm_status report_error(vpm_status st, const char *msg);
+size_t rollout_scratch_bytes(const vpm_state *s, int K, int H, int advance);
 }
 
 static vpm_status sfail(vpm_status st, const char *fmt, ...)
@@ -51,6 +52,7 @@ struct Request {
     float lambda = 1.f, advance_u = 0.f;
     std::vector<float> mu, eps;
     size_t bytes = 0;                 // device bytes the request holds while in flight
+    size_t buf_bytes = 0;             // of which its own buffers (the rest: rollout scratch)
     double t_submit = 0, t_start = 0, t_done = 0;
 };
 
@@ -111,7 +113,7 @@ static vpm_status start_request(vpm_server *s, Slot &sl, const Request &r)
     float *pin = sl.pinned;
     memcpy(pin, r.eps.data(), sizeof(float) * (size_t)K * H);
     memcpy(pin + (size_t)K * H, r.mu.data(), sizeof(float) * H);
-    cudaError_t e = cudaMallocAsync((void **)&sl.d_buf, r.bytes, sl.stream);
+    cudaError_t e = cudaMallocAsync((void **)&sl.d_buf, r.buf_bytes, sl.stream);
     if (e) { cudaGetLastError(); return sfail(VPM_ERR_OOM, "server: cudaMallocAsync: %s", cudaGetErrorString(e)); }
     float *d_eps = sl.d_buf, *d_ctrl = d_eps + (size_t)K * H, *d_costs = d_ctrl + (size_t)K * H;
     float *d_w = d_costs + K, *d_mu = d_w + K;
@@ -283,13 +285,14 @@ extern "C" vpm_status vpm_server_submit(vpm_server *s, int scenario, int K, int 
     r.lambda = lambda;
     r.advance_steps = advance_steps;
     r.advance_u = advance_u;
-    r.bytes = request_bytes(K, H);
+    r.buf_bytes = request_bytes(K, H);
     r.eps.assign(h_eps, h_eps + (size_t)K * H);
     r.mu.assign(H, 0.f);
     if (h_mu) r.mu.assign(h_mu, h_mu + H);
     std::lock_guard<std::mutex> lk(s->m);
     if (scenario < 0 || scenario >= (int)s->scenarios.size())
         return sfail(VPM_ERR_INVALID, "vpm_server_submit: unknown scenario %d", scenario);
+    r.bytes = r.buf_bytes + vpm::rollout_scratch_bytes(s->scenarios[scenario], K, H, advance_steps);
     if (r.bytes > s->budget)
         return sfail(VPM_ERR_CAPACITY, "vpm_server_submit: request needs %zu bytes, budget %zu", r.bytes, s->budget);
     r.ticket = s->next_ticket++;
@@ -331,6 +334,18 @@ extern "C" vpm_status vpm_server_poll(vpm_server *s, long long ticket, int timeo
     out->j_min = r.j_min;
     if (h_mu_out && !r.mu.empty()) memcpy(h_mu_out, r.mu.data(), sizeof(float) * r.mu.size());
     s->done.erase(ticket);
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_server_request_bytes(vpm_server *s, int scenario, int K, int H,
+                                               int advance_steps, size_t *bytes)
+{
+    if (!s || !bytes || K < 1 || H < 1 || advance_steps < 0)
+        return sfail(VPM_ERR_INVALID, "vpm_server_request_bytes: null, K or H < 1, or advance_steps < 0");
+    std::lock_guard<std::mutex> lk(s->m);
+    if (scenario < 0 || scenario >= (int)s->scenarios.size())
+        return sfail(VPM_ERR_INVALID, "vpm_server_request_bytes: unknown scenario %d", scenario);
+    *bytes = request_bytes(K, H) + vpm::rollout_scratch_bytes(s->scenarios[scenario], K, H, advance_steps);
     return VPM_OK;
 }
 

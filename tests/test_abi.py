@@ -64,6 +64,7 @@ def test_host_side_rejections(vlib):
     assert b"null" in vlib.vpm_last_error()
     r = C.c_double(0.0)
     assert vlib.vpm_probe_rate(99, 1, C.byref(r)) == V.VPM_ERR_INVALID
+    assert vlib.vpm_probe_rate(V.PROBE_PAIRS_SYM + 1, 1, C.byref(r)) == V.VPM_ERR_INVALID
     assert vlib.vpm_probe_rate(V.PROBE_FFMA, 0, C.byref(r)) == V.VPM_ERR_INVALID
     assert vlib.vpm_probe_rate(V.PROBE_FFMA, 8, C.byref(r)) == V.VPM_ERR_INVALID
 

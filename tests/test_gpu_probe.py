@@ -18,5 +18,8 @@ def test_probe_rates_within_unit_limits():
         assert 0 < r <= sms * 128 * ghz * 1e9
     pairs = V.probe_rate(V.PROBE_PAIRS_T4, 7)
     assert 0 < pairs <= ffma / 8 * 1.05         # at least 8 FP32 operations per pair
+    # one evaluation (11 FP32 operations) serves two pairs across rows
+    sym = V.probe_rate(V.PROBE_PAIRS_SYM, 7)
+    assert 0 < sym <= ffma / 5.5 * 1.05
     with pytest.raises(V.VpmError):
         V.probe_rate(V.PROBE_PAIRS_T4, 9)

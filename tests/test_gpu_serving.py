@@ -82,15 +82,22 @@ def test_admission_by_rollouts_in_flight():
 def test_admission_by_memory_budget():
     torch, V = cuda()
     K, H = 512, 20
-    need = 4 * (2 * K * H + 2 * K + H)
-    srv, p, fields = _server(V, 4, budget=need + need // 2)
-    tickets = [srv.submit(s, W.mppi_noise(20 + s, K, H, W.MPPI_SIGMA_U)) for s in range(3)]
+    scen = [0, 3, 1]                                   # fields of 300, 400 and 500 particles
+    probe, _, _ = _server(V, 1)
+    need = [probe.request_bytes(s, K, H) for s in scen]
+    probe.close()
+    buffers = 4 * (2 * K * H + 2 * K + H)            # noise, controls, costs, weights, controls out
+    assert all(b > buffers for b in need)              # plus the rollouts' pair-sum scratch
+    two = sum(sorted(need)[:2])                        # the smallest pair of requests together
+    assert max(need) < two
+    srv, p, fields = _server(V, 4, budget=(max(need) + two) // 2)   # any one fits, no two do
+    tickets = [srv.submit(s, W.mppi_noise(20 + s, K, H, W.MPPI_SIGMA_U)) for s in scen]
     res = [srv.poll(t)[0] for t in tickets]
     assert all(r["status"] == V.VPM_OK for r in res)
     spans = sorted((r["t_start_ms"], r["t_done_ms"]) for r in res)
     assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))   # one at a time
     with pytest.raises(V.VpmError) as e:
-        srv.submit(0, W.mppi_noise(30, 2048, H, W.MPPI_SIGMA_U))
+        srv.submit(1, W.mppi_noise(30, 2048, H, W.MPPI_SIGMA_U))
     assert e.value.status == V.VPM_ERR_CAPACITY
     srv.close()
 

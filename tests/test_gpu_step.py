@@ -98,6 +98,35 @@ def p_dt(params):
     return params["dt"]
 
 
+# Wake sizes at the edges of the binary32 pair phase: its rows of 128 particles (one pair
+# evaluation serves both particles across rows), diagonal groups of 64 targets and source
+# blocks of 32 (the last one ragged).
+ROW_EDGES = [1, 31, 63, 64, 65, 127, 128, 129, 191, 255, 256, 257, 383, 449]
+
+
+@pytest.mark.parametrize("n", ROW_EDGES)
+def test_pair_rows_edges(ora, n):
+    """One step from the oracle's state at sizes n and n + 2 (after one shedding) against the
+    oracle: convection velocities of every particle and the advanced positions."""
+    torch, V = cuda()
+    params = W.glider_params()
+    snaps, cap = _snapshots(ora, params, W.background_field(40 + n, n), np.array(W.GLIDER_X0), [0, 1])
+    for k, snap, u in snaps:
+        o = oracle_state(ora, params, snap, cap)
+        ref = o.step(u)
+        g = gpu_state(V, params, snap, cap, V.FP32)
+        out = g.step(u, probe=True)
+        torch.cuda.synchronize()
+        n1 = len(ref["vel"])
+        vel = out["vel"].cpu().numpy()[:2 * n1].reshape(-1, 2)
+        msg = "n=%d step %d" % (n, k)
+        assert normwise(vel, ref["vel"]) <= VEL_TOL, msg
+        vmax = np.linalg.norm(ref["vel"], axis=1).max()
+        parts_g = g.read()[0]
+        assert np.abs(parts_g[:, :2] - o.particles[:, :2]).max() <= params["dt"] * VEL_TOL * vmax + 1e-9, msg
+        g.close()
+
+
 def test_step_commits_and_rollout_agree(ora):
     """Ten vpm_step calls advance the resident state exactly as a 10-step rollout does."""
     torch, V = cuda()
