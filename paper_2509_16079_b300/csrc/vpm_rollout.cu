@@ -390,10 +390,10 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
 // evaluation of a pair serves both particles' sums. The n old particles form rows of kRow
 // (row a: particles kRow a .. kRow a + kRow - 1), and the work comes in two kinds of units:
 //   * off-diagonal row a: the row's particles (4 per lane) against every later particle, in
-//     blocks of 32 sources. A block takes 32 rounds; in round r lane l takes source
-//     (l + r) mod 32 for its 4 targets, adds the forward terms to its targets' sums and the
-//     reverse terms to the source's running sum, which then moves one lane down. After the 32
-//     rounds lane l holds source l's sum over the row's targets and stores it in the block's
+//     blocks of 32 sources (two at a time). A block takes 32 rounds; in round r lane l takes
+//     source (l + r) mod 32 for its 4 targets, adds the forward terms to its targets' sums and
+//     the reverse terms to the source's running sum, which then moves one lane down. After the
+//     32 rounds lane l holds source l's sum over the row's targets and stores it in the block's
 //     scratch slot of (row a, source); the targets' compensated sums over the later particles
 //     are kept in their own scratch slots;
 //   * diagonal group g: kDiagGroup targets against the kRow particles of their own row, every
@@ -408,9 +408,10 @@ constexpr int kTile = 64;
 #endif
 constexpr int kSrcUnroll = VPM_SRC_UNROLL;
 #ifndef VPM_ROT_UNROLL
-#define VPM_ROT_UNROLL 8      // rounds in flight per iteration of the rotation loop
+#define VPM_ROT_UNROLL 8      // rounds in flight per iteration of the rotation loop (one block;
+                              // half as many with two blocks per round)
 #endif
-constexpr int kRotUnroll = VPM_ROT_UNROLL;
+constexpr int kRotUnroll = VPM_ROT_UNROLL, kRotUnroll2 = VPM_ROT_UNROLL / 2;
 constexpr int kRow = 128;     // targets of an off-diagonal row (4 per lane)
 #ifndef VPM_DIAG_T
 #define VPM_DIAG_T 2          // targets per lane of a diagonal group (1, 2 or 4)
@@ -533,6 +534,52 @@ __device__ __forceinline__ void fold_row(float4 *kst, int a, float (&fu)[4], flo
     }
 }
 
+// Two full blocks b0 .. b0+31 and b0+32 .. b0+63 at once: each round takes one source of
+// each, so two independent running sums travel down the lanes (the chain through the shuffle
+// is half as long per pair as with one block). On return lane l holds the reverse sums of
+// sources b0 + l (r1) and b0 + 32 + l (r2).
+template <int KER>
+__device__ __forceinline__ void rotate_two(const DevParams &p, const float4 *part, int b0,
+                                           const float (&tx)[4], const float (&tz)[4],
+                                           const float (&tg)[4], float (&fu)[4], float (&fw)[4],
+                                           float2 &r1, float2 &r2)
+{
+    const int lane = threadIdx.x & 31;
+    const float rc4s = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    float ru1 = 0.f, rw1 = 0.f, ru2 = 0.f, rw2 = 0.f;
+#pragma unroll kRotUnroll2
+    for (int r = 0; r < 32; ++r) {
+        const int j = b0 + ((lane + r) & 31);
+        const float4 s1 = part[j], s2 = part[j + 32];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dx = tx[k] - s1.x, dz = tz[k] - s1.y;
+            const float q = PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4s, irc2);
+            const float gs = s1.z * q, gt = tg[k] * q;
+            fu[k] = fmaf(-dz, gs, fu[k]);
+            fw[k] = fmaf(dx, gs, fw[k]);
+            ru1 = fmaf(dz, gt, ru1);
+            rw1 = fmaf(-dx, gt, rw1);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dx = tx[k] - s2.x, dz = tz[k] - s2.y;
+            const float q = PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4s, irc2);
+            const float gs = s2.z * q, gt = tg[k] * q;
+            fu[k] = fmaf(-dz, gs, fu[k]);
+            fw[k] = fmaf(dx, gs, fw[k]);
+            ru2 = fmaf(dz, gt, ru2);
+            rw2 = fmaf(-dx, gt, rw2);
+        }
+        ru1 = __shfl_sync(0xffffffffu, ru1, (lane + 1) & 31);
+        rw1 = __shfl_sync(0xffffffffu, rw1, (lane + 1) & 31);
+        ru2 = __shfl_sync(0xffffffffu, ru2, (lane + 1) & 31);
+        rw2 = __shfl_sync(0xffffffffu, rw2, (lane + 1) & 31);
+    }
+    r1 = make_float2(ru1, rw1);
+    r2 = make_float2(ru2, rw2);
+}
+
 // Off-diagonal row a (kRow (a + 1) < n, so all of its targets exist).
 template <int KER>
 __device__ void offdiag_row(const DevParams &p, const float4 *part, float2 *scr, int cap32, int n,
@@ -550,16 +597,21 @@ __device__ void offdiag_row(const DevParams &p, const float4 *part, float2 *scr,
     }
     float4 *kst = reinterpret_cast<float4 *>(scr);
     float2 *rrow = scr + (rev_row_base(a, cap32) - (long long)kRow * (a + 1));   // by source index
-    int b0 = kRow * (a + 1);                   // a multiple of 64: fold after every odd block
+    int b0 = kRow * (a + 1);                   // a multiple of 64: fold after every two blocks
     bool first = true;
-    for (; b0 + 32 <= n; b0 += 32) {
+    for (; b0 + 64 <= n; b0 += 64) {
+        float2 r1, r2;
+        rotate_two<KER>(p, part, b0, tx, tz, tg, fu, fw, r1, r2);
+        rrow[b0 + lane] = r1;
+        rrow[b0 + 32 + lane] = r2;
+        fold_row(kst, a, fu, fw, first);
+        first = false;
+    }
+    if (b0 + 32 <= n) {
         float ru, rw;
         rotate_block<KER, true>(p, part, n, b0, tx, tz, tg, fu, fw, ru, rw);
         rrow[b0 + lane] = make_float2(ru, rw);
-        if (b0 & 32) {
-            fold_row(kst, a, fu, fw, first);
-            first = false;
-        }
+        b0 += 32;
     }
     if (b0 < n) {
         float ru, rw;
