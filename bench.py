@@ -88,7 +88,7 @@ def profiled_pipes(summary: str, source: str):
         return None
     return {"fma_pipe_pct": float(m.group(1)), "mufu_pipe_pct": float(m.group(2)),
             "fp64_pipe_pct": float(m.group(3)), "issue_active_pct": float(m.group(4)),
-            "capture": "ncu --set full, K=1024, H=10 (profiles/%s)" % summary}
+            "capture": "ncu --set full on the small case of profiles/%s" % summary}
 
 
 # ------------------------------------------------------------------ clocks during the run
@@ -395,8 +395,8 @@ def run_profile_case(args):
 # ------------------------------------------------------------------ extra workloads
 def run_freefield(args):
     """Large free field: N = 2^20 regularised vortices (64 Gaussian blobs, core 1e-3), 10 Heun
-    steps in binary32 with compensated tile sums; error of the final velocities against the FP64
-    oracle on 4096 sampled targets."""
+    steps in binary32 with compensated tile sums, one evaluation per particle pair; error of the
+    final velocities against the FP64 oracle on 4096 sampled targets."""
     import torch
     import paper_2509_16079_b300 as V
     from paper_2509_16079_b300 import build
@@ -444,8 +444,11 @@ def run_freefield(args):
                                "Vatistas core 1e-3, Heun dt=1e-3" % n, "pairs_per_step": 2 * n * n},
         "error_vs_fp64_oracle": {"normwise_velocity": err, "targets": int(len(idx))},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "kernel": "freefield_kernel<Vatistas, velocity>",
+                     "frac": achieved / peak,
+                     "kernel": "freefield_sym_kernel<Vatistas> + freefield_combine_kernel (one velocity "
+                               "evaluation; one evaluation per particle pair)",
                      "traffic": profiled_traffic("freefield_kernel_2pow20.md", "vpm_freefield.cu"),
+                     "pipes": profiled_pipes("freefield_kernel_2pow20.md", "vpm_freefield.cu"),
                      "launch_ms": kern_ms},
         "clocks": clk.summary()}), flush=True)
 

@@ -314,15 +314,25 @@ vpm_status mppi_perturb(const float *d_mu, const float *d_eps, int K, int H,
 /*
  * Free-field velocities (Eq. 3 with the chosen kernel, self term excluded) of n particles
  * d_particles[n*4] = (x, z, Gamma, unused) binary32; d_vel[n*2] receives (u, w). Binary32
- * pair sums, compensated across source tiles.
+ * pair sums, compensated across source tiles. One evaluation of each particle pair serves both
+ * particles; the partial sums go through vpm_freefield_scratch_bytes(n) bytes of device scratch
+ * (about n^2 / 256 bytes: 4.9 GB at n = 2^20) that the call allocates on `stream` from the
+ * device's default memory pool and frees after it (stream-ordered). Errors: VPM_ERR_INVALID,
+ * VPM_ERR_CUDA (including an allocation that does not fit).
  */
 vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel, double r_core,
                                   float *d_vel, cudaStream_t stream);
 
+/* Device bytes of pair-sum scratch one free-field velocity evaluation of n particles uses
+ * (rows of 1024 particles: one slot per row and later particle, per row segment and target,
+ * and two per particle). Errors: VPM_ERR_INVALID (n < 0, null). */
+vpm_status vpm_freefield_scratch_bytes(int n, size_t *bytes);
+
 /*
  * `steps` Heun (explicit trapezoidal RK2) steps of a free field in place:
  * v1 = V(r), r* = r + dt v1, v2 = V(r*), r <- r + dt (v1 + v2) / 2. d_particles as above.
- * Uses 24 n bytes of library-allocated scratch (stream-ordered allocation).
+ * Uses 24 n bytes plus vpm_freefield_scratch_bytes(n) bytes of library-allocated scratch
+ * (stream-ordered allocation); vpm_freefield_heun_noalloc allocates nothing.
  */
 vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, double r_core, double dt,
                               int steps, cudaStream_t stream);

@@ -100,6 +100,7 @@ _SIGNATURES = {
     "mppi_update": ([_VP, _VP, _I, _I, _VP, _VP], _I),
     "mppi_perturb": ([_VP, _VP, _I, _I, _VP, _VP], _I),
     "vpm_freefield_velocity": ([_VP, _I, _I, _D, _VP, _VP], _I),
+    "vpm_freefield_scratch_bytes": ([_I, C.POINTER(C.c_size_t)], _I),
     "vpm_freefield_heun": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
     "vpm_freefield_heun_noalloc": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
     "vpm_probe_rate": ([_I, _I, C.POINTER(_D)], _I),
@@ -643,6 +644,13 @@ def freefield_velocity(particles, kernel: int, r_core: float, out=None, stream=N
     check(lib().vpm_freefield_velocity(ptr(particles), n, int(kernel), float(r_core), ptr(v),
                                        stream_handle(stream)))
     return v
+
+
+def freefield_scratch_bytes(n: int) -> int:
+    """Device bytes of pair-sum scratch one free-field velocity evaluation of n particles uses."""
+    b = C.c_size_t()
+    check(lib().vpm_freefield_scratch_bytes(int(n), C.byref(b)))
+    return b.value
 
 
 def freefield_heun(particles, kernel: int, r_core: float, dt: float, steps: int, stream=None):

@@ -17,11 +17,15 @@ cudaError_t launch_mppi_update(const float *w, const float *xi, int K, int H, fl
                                cudaStream_t s);
 cudaError_t launch_mppi_perturb(const float *mu, const float *eps, int K, int H, float *out,
                                 cudaStream_t s);
-cudaError_t launch_freefield_velocity(const float *p, int n, int kernel, double r_core,
-                                      float *vel, cudaStream_t s);
 cudaError_t launch_freefield_heun(float *p, int n, int kernel, double r_core, double dt,
                                   int steps, float *scratch_mid, float *scratch_v1,
                                   cudaStream_t s);
+size_t freefield_sym_scratch_bytes(int n);
+cudaError_t launch_freefield_sym_velocity(const float *p, int n, int kernel, double r_core,
+                                          float *vel, void *scratch, cudaStream_t s);
+cudaError_t launch_freefield_sym_heun(float *p, int n, int kernel, double r_core, double dt,
+                                      int steps, float *scratch_mid, float *scratch_v1,
+                                      void *scratch, cudaStream_t s);
 }  // namespace vpm
 
 using namespace vpm;
@@ -812,13 +816,27 @@ extern "C" vpm_status mppi_perturb(const float *d_mu, const float *d_eps, int K,
 
 // ------------------------------------------------------------------ free field
 
+extern "C" vpm_status vpm_freefield_scratch_bytes(int n, size_t *bytes)
+{
+    if (n < 0 || !bytes) return fail(VPM_ERR_INVALID, "vpm_freefield_scratch_bytes: n < 0 or null");
+    *bytes = freefield_sym_scratch_bytes(n);
+    return VPM_OK;
+}
+
 extern "C" vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel,
                                              double r_core, float *d_vel, cudaStream_t stream)
 {
     if (n < 0 || (n > 0 && (!d_particles || !d_vel))) return fail(VPM_ERR_INVALID, "bad arguments");
     if (kernel < 0 || kernel > 2 || (kernel != VPM_KERNEL_SINGULAR && !(r_core > 0)))
         return fail(VPM_ERR_INVALID, "bad kernel or core radius");
-    CUDA_TRY(launch_freefield_velocity(d_particles, n, kernel, r_core, d_vel, stream), "freefield velocity");
+    if (n == 0) return VPM_OK;
+    keep_pool_memory();
+    void *scratch = nullptr;
+    CUDA_TRY(cudaMallocAsync(&scratch, freefield_sym_scratch_bytes(n), stream), "freefield scratch");
+    cudaError_t e = launch_freefield_sym_velocity(d_particles, n, kernel, r_core, d_vel, scratch, stream);
+    cudaError_t e2 = cudaFreeAsync(scratch, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "freefield velocity");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "freefield scratch free");
     return VPM_OK;
 }
 
@@ -830,10 +848,15 @@ extern "C" vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, 
     if (kernel < 0 || kernel > 2 || (kernel != VPM_KERNEL_SINGULAR && !(r_core > 0)))
         return fail(VPM_ERR_INVALID, "bad kernel or core radius");
     if (n == 0 || steps == 0) return VPM_OK;
-    float *scratch = nullptr;
-    CUDA_TRY(cudaMallocAsync((void **)&scratch, (size_t)n * 24, stream), "heun scratch");
-    cudaError_t e = launch_freefield_heun(d_particles, n, kernel, r_core, dt, steps, scratch,
-                                          scratch + (size_t)4 * n, stream);
+    keep_pool_memory();
+    // stage positions (16 n bytes), first-stage velocities (8 n bytes), then the pair sums
+    char *scratch = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&scratch, (size_t)n * 24 + freefield_sym_scratch_bytes(n), stream),
+             "heun scratch");
+    cudaError_t e = launch_freefield_sym_heun(d_particles, n, kernel, r_core, dt, steps,
+                                              reinterpret_cast<float *>(scratch),
+                                              reinterpret_cast<float *>(scratch + (size_t)n * 16),
+                                              scratch + (size_t)n * 24, stream);
     cudaError_t e2 = cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_fail(e, "freefield heun");
     if (e2 != cudaSuccess) return cuda_fail(e2, "heun scratch free");

@@ -1,11 +1,13 @@
 // Free-field Heun stepping that allocates nothing.
 //
-// vpm_freefield_heun asks the stream-ordered allocator for its 24 n bytes of scratch on every
-// call. Some callers cannot let a library allocate: a real-time control loop whose memory is
-// fixed up front (an allocation can stall or fail in the middle of a control period), or a
-// host process that hands the GPU over to code that owns all device memory. For them this
-// file keeps the scratch in one statically sized device array, reserved when the library is
-// loaded, and vpm_freefield_heun_noalloc uses it instead of allocating.
+// vpm_freefield_heun asks the stream-ordered allocator for its scratch on every call (24 n bytes
+// plus the pair-sum slots of its one-evaluation-per-pair kernel). Some callers cannot let a
+// library allocate: a real-time control loop whose memory is fixed up front (an allocation can
+// stall or fail in the middle of a control period), or a host process that hands the GPU over
+// to code that owns all device memory. For them this file keeps the scratch in one statically
+// sized device array, reserved when the library is loaded, and vpm_freefield_heun_noalloc uses
+// it instead of allocating; it evaluates every pair once per target, which needs only the
+// 24 n bytes.
 #include <mutex>
 #include <stdio.h>
 

@@ -1186,7 +1186,7 @@ long long rollout_rev_slots(int precision, int cap)
 
 // Stream-ordered allocations of the pair-sum scratch come from the device's default pool,
 // which keeps freed memory for the next launch instead of returning it at every synchronise.
-static void keep_pool_memory()
+void keep_pool_memory()
 {
     static std::once_flag once;
     std::call_once(once, [] {

@@ -16,7 +16,7 @@ def _dev_particles(torch, P):
 
 
 @pytest.mark.parametrize("kernel", [0, 1, 2])
-@pytest.mark.parametrize("n", [0, 1, 2, 511, 512, 513, 1500, 4097])
+@pytest.mark.parametrize("n", [0, 1, 2, 511, 512, 513, 1023, 1024, 1025, 1500, 2049, 4097])
 def test_freefield_velocity(ora, kernel, n):
     torch, V = cuda()
     P = W.background_field(n, n)
