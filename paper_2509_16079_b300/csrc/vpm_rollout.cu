@@ -12,6 +12,7 @@
 // decay of Eq. 17; merging of the two oldest particles while N > N_w,max.
 #include <cooperative_groups.h>
 
+#include <climits>
 #include <mutex>
 
 #include "vpm_rollout.cuh"
@@ -60,7 +61,7 @@ struct Work {
 #endif
 };
 
-// ------------------------------------------------------------------ geometry (warp 0)
+// ------------------------------------------------------------------ geometry (the plate warp)
 
 // Plate frame from the glider state. All lanes of the calling warp take part: lane 1 forms sin
 // and cos of pitch + elevator angle (needed by the elevator force of Eqs. 18-20 later in the
@@ -185,9 +186,9 @@ __device__ void plate_sums_f64(const DevParams &p, Work &w, const Part64 *part, 
     if (lane == 0) w.red[warp] = gsum;
 }
 
-// Phase A, binary32 path, by warp 0 alone while the other warps start on the pair sums. The
-// plate points are formed in binary64 (one lane each) and rounded once; targets then go
-// kPlateG at a time so that their dependency chains overlap. Lanes split the sources; the 32
+// Phase A, binary32 path, by the plate warp alone while the other warps start on the pair
+// sums. The plate points are formed in binary64 (one lane each) and rounded once; targets then
+// go kPlateG at a time so that their dependency chains overlap. Lanes split the sources; the 32
 // partial sums of a target are combined by a butterfly in binary32. The Kelvin sum (Eq. 7) is
 // Kahan-compensated per lane and combined in binary64; w.red[0] receives it.
 constexpr int kPlateG = 4;
@@ -382,8 +383,9 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
 // Phase C: convection velocity of every wake particle (Eq. 16) plus the free stream.
 //
 // Binary32 path. The sum over pairs of particles that existed before this step's shedding
-// does not depend on the surface solve, so it runs while warp 0 does the plate work; only the
-// bound vortices and the freshly shed vortices need Gamma_S, and their terms are added after.
+// does not depend on the surface solve, so it runs while the plate warp does the plate work;
+// only the bound vortices and the freshly shed vortices need Gamma_S, and their terms are
+// added after.
 //
 // The pair factor of every kernel (Eqs. 4-5, and the Gaussian core) depends on the distance
 // alone, and the displacement changes sign when the two particles swap roles, so one
@@ -693,8 +695,8 @@ __device__ __forceinline__ void bound_terms_f32(const DevParams &p, const Work &
     }
 }
 
-// Full sums of the freshly shed particles n .. n1-1 (at most two; warp 0, right after the
-// solve, while the other warps are still on the old-old pairs), both targets in one pass:
+// Full sums of the freshly shed particles n .. n1-1 (at most two; the plate warp, right after
+// the solve, while the other warps are still on the old-old pairs), both targets in one pass:
 // lanes split the sources, partial sums are combined in binary64, lane f adds the bound terms
 // and the free stream for shed particle f.
 template <int KER>
@@ -936,6 +938,14 @@ __device__ __noinline__ int terminate_pair(const DevParams &p, Work &w, typename
     return n - 2;
 }
 
+// The warp that does the binary32 path's plate work: it changes with the block, so that the
+// serial binary64 work of the blocks resident on an SM is spread over its warp schedulers
+// (a block's warp w runs on scheduler w mod 4) rather than all landing on one.
+__device__ __forceinline__ int plate_warp()
+{
+    return (int)(blockIdx.x & ((blockDim.x >> 5) - 1));
+}
+
 // One full step of one rollout. All threads call it with the same particle count n (updated
 // here) and chunk-claim base; returns with the block synchronised.
 template <class R, int KER>
@@ -946,10 +956,10 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
     const int tid = threadIdx.x, warp = tid >> 5;
     int n1;
     if constexpr (sizeof(R) == 4) {
-        // warp 0: plate geometry, plate sums, surface solve, loads, glider, shedding and the
-        // shed particles' velocities; meanwhile (and afterwards for warp 0) every warp works
-        // on the old-old pair sums
-        if (warp == 0) {
+        // the plate warp: plate geometry, plate sums, surface solve, loads, glider, shedding
+        // and the shed particles' velocities; meanwhile (and afterwards for the plate warp)
+        // every warp works on the old-old pair sums
+        if (warp == plate_warp()) {
             const int lane = tid & 31;
             plate_geometry(p, w);
             prefetch_solve_rows(p, w.geo);
@@ -1075,6 +1085,52 @@ __device__ void finish(const RolloutArgs &a, Work &w, const typename Store<R>::P
     }
 }
 
+// Pacing of the blocks that share an SM. All blocks of a one-wave launch start together, but
+// the warp schedulers favour the oldest warps, so left alone the first of seven co-resident
+// blocks finishes after about 56 % of the launch and the last runs alone at its end, where one
+// block's warps cannot hide the latency of the pair loop's shuffles (measured: 66 % of the
+// SM's rate with one block). A block that is more than kPaceAhead steps ahead of the slowest
+// block on its SM therefore sleeps until that block catches up, for at most kPaceWaits short
+// sleeps per step; giving up only costs time, never changes a result.
+constexpr int kPaceSlots = 8, kPaceAhead = 1, kPaceWaits = 4000;
+constexpr int kPaceSms = 1024;    // SM ids paced (blocks on an SM with a larger id are not)
+
+__device__ __forceinline__ unsigned sm_id()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// Thread 0: takes a slot on this SM (-1: pacing off for this block).
+__device__ int pace_join(const RolloutArgs &a, unsigned sm)
+{
+    if (!a.pace_mask || sm >= (unsigned)a.pace_sms) return -1;
+    for (int b = 0; b < kPaceSlots; ++b) {
+        const unsigned old = atomicOr(&a.pace_mask[sm], 1u << b);
+        if (!(old & (1u << b))) {
+            atomicExch(&a.pace_prog[sm * kPaceSlots + b], 0);
+            return b;
+        }
+    }
+    return -1;
+}
+
+// Thread 0, before step k: publishes k and waits while the block is ahead.
+__device__ void pace_step(const RolloutArgs &a, unsigned sm, int slot, int k)
+{
+    int *prog = a.pace_prog + sm * kPaceSlots;
+    atomicExch(&prog[slot], k);
+    for (int it = 0; it < kPaceWaits; ++it) {
+        const unsigned m = atomicOr(&a.pace_mask[sm], 0u);
+        int lo = INT_MAX;
+        for (int b = 0; b < kPaceSlots; ++b)
+            if (b != slot && (m & (1u << b))) lo = min(lo, atomicOr(&prog[b], 0));
+        if (lo == INT_MAX || k <= lo + kPaceAhead) return;
+        __nanosleep(1000);
+    }
+}
+
 // One rollout of a.H steps by the whole block, field resident in shared memory.
 template <class R, int KER>
 __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P *part,
@@ -1082,12 +1138,21 @@ __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P 
 {
     load_state<R>(a, w, part, rid);
     int n = w.n, claim_base = 0;
+    __shared__ int s_slot;
+    const unsigned sm = sm_id();
+    if (threadIdx.x == 0) s_slot = pace_join(a, sm);
+    __syncthreads();
+    const int slot = s_slot;
     for (int k = 0; k < a.H; ++k) {
+        if (slot >= 0 && k > 0) {
+            if (threadIdx.x == 0) pace_step(a, sm, slot, k);
+            __syncthreads();
+        }
         double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k]
                               : a.u_const;
-        if (a.pol_gains && threadIdx.x < 32) {
-            // the feedback control from the glider state in shared memory, formed by warp 0,
-            // the only warp that uses the control (the other warps never read it)
+        if (a.pol_gains && (int)(threadIdx.x >> 5) == (sizeof(R) == 4 ? plate_warp() : 0)) {
+            // the feedback control from the glider state in shared memory, formed by the warp
+            // that does the plate work, the only warp that uses the control
             const size_t j = (size_t)a.pol_offset + k;
             double fb = (double)a.pol_ubar[j];
             for (int c = 0; c < 7; ++c)
@@ -1098,7 +1163,10 @@ __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P 
         if (a.traj && threadIdx.x < 7)
             a.traj[((size_t)rid * a.H + k) * 7 + threadIdx.x] = w.xg[threadIdx.x];
     }
-    if (threadIdx.x == 0) w.n = n;
+    if (threadIdx.x == 0) {
+        w.n = n;
+        if (slot >= 0) atomicAnd(&a.pace_mask[sm], ~(1u << slot));   // leaves the SM's pacing
+    }
     __syncthreads();
     if (a.out_part) store_state<R>(a, w, part, rid);
     finish<R>(a, w, part, rid);
@@ -1165,8 +1233,39 @@ static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStr
         if (e != cudaSuccess) return e;
         granted = smem;
     }
-    k<<<grid, NT, smem, s>>>(a);
-    return cudaGetLastError();
+    // binary32 multi-step launches that fit in one wave with several blocks per SM are paced
+    RolloutArgs b = a;
+    void *pace = nullptr;
+    if (sizeof(R) == 4 && a.H > 1 && !a.pace_mask) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) == cudaSuccess &&
+            per_sm > 1 && grid > sms && grid <= per_sm * sms) {
+            const int ids = kPaceSms;
+            const size_t bytes = sizeof(unsigned) * ids + sizeof(int) * ids * kPaceSlots;
+            if (cudaMallocAsync(&pace, bytes, s) == cudaSuccess) {
+                cudaError_t e = cudaMemsetAsync(pace, 0, bytes, s);
+                if (e != cudaSuccess) {
+                    cudaFreeAsync(pace, s);
+                    return e;
+                }
+                b.pace_mask = static_cast<unsigned *>(pace);
+                b.pace_prog = reinterpret_cast<int *>(b.pace_mask + ids);
+                b.pace_sms = ids;
+            } else {
+                pace = nullptr;          // no pacing: a speed hint only
+            }
+        }
+        cudaGetLastError();
+    }
+    k<<<grid, NT, smem, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (pace) {
+        const cudaError_t e2 = cudaFreeAsync(pace, s);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e;
 }
 
 // Binary32 block size by field capacity: more warps where shared memory admits fewer blocks

@@ -53,6 +53,11 @@ struct RolloutArgs {
     // at least rollout_rev_slots(cap); null: the launcher allocates it around the launch)
     float2 *rev;
     long long rev_stride;
+    // pacing of the co-resident blocks of a one-wave launch (null: off): per SM id below
+    // pace_sms, a mask of the occupied slots and the step each slot's block has reached
+    unsigned *pace_mask;
+    int *pace_prog;             // pace_sms x kPaceSlots
+    int pace_sms;
 };
 // Puts a disturbance pair in front of the n records of a state (one block): records move up by
 // two, the pair takes slots 0 and 1, the count and the pair count are updated on the device.

@@ -160,6 +160,21 @@ def test_batch_invariance_and_per_launch_form():
     assert torch.equal(pl["final_glider"], full["final_glider"][:8])
 
 
+def test_paced_launch_matches_unpaced_launches():
+    """A one-wave launch of 1024 rollouts paces its co-resident blocks (a block ahead of the
+    slowest on its SM sleeps); launches of 128 (one block per SM at most) are not paced. The
+    pacing changes timing only: the results are the same bits."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(2, K=1024, H=6, n=300)
+    st = V.State(p, field, xg0, 320)
+    c = torch.tensor(eps, device="cuda")
+    full = st.rollout_batch(c)
+    for b in range(0, 1024, 128):
+        part = st.rollout_batch(c[b:b + 128].contiguous())
+        assert torch.equal(part["costs"], full["costs"][b:b + 128])
+        assert torch.equal(part["final_glider"], full["final_glider"][b:b + 128])
+
+
 def test_full_size_batch_properties(ora):
     """K = 1024 rollouts x 100 steps from 1000 particles, binary32, the benchmark's launch:
     every rollout ends with 1200 particles and finite costs; sampled rollouts are rerun alone
