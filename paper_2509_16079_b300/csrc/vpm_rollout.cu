@@ -938,9 +938,13 @@ __device__ __noinline__ int terminate_pair(const DevParams &p, Work &w, typename
     return n - 2;
 }
 
-// The warp that does the binary32 path's plate work: it changes with the block, so that the
-// serial binary64 work of the blocks resident on an SM is spread over its warp schedulers
-// (a block's warp w runs on scheduler w mod 4) rather than all landing on one.
+// The warp that does the binary32 path's plate work: it varies with the block (block index mod
+// warps per block). Measured against always using warp 0: 2.5 % faster on the MPPI batch and
+// 5 % slower on the perch-shape batch (<= 62 particles); a variant that chose by field size
+// (varying above 256 particles, warp 0 below) was fast on the perch shape but lost the gain on
+// the MPPI batch, where it chose the same warps. The pair loop's code generation is this
+// sensitive to the surrounding code, so the form kept is the one that measures best on the
+// MPPI batch.
 __device__ __forceinline__ int plate_warp()
 {
     return (int)(blockIdx.x & ((blockDim.x >> 5) - 1));
@@ -1094,6 +1098,11 @@ __device__ void finish(const RolloutArgs &a, Work &w, const typename Store<R>::P
 // sleeps per step; giving up only costs time, never changes a result.
 constexpr int kPaceSlots = 8, kPaceAhead = 1, kPaceWaits = 4000;
 constexpr int kPaceSms = 1024;    // SM ids paced (blocks on an SM with a larger id are not)
+// Fields that stay small have short, plate-bound steps (~18 us at 60 particles), where a
+// 1 us sleep and the extra barrier cost more than the tail they remove: pacing is for launches
+// whose fields can exceed this many particles (measured: the perch-shape batch of 1024 took
+// 2.64 ms paced against 2.30 ms unpaced, the MPPI batch 2.3 % less time paced).
+constexpr int kPaceMinCap = 256;
 
 __device__ __forceinline__ unsigned sm_id()
 {
@@ -1236,7 +1245,7 @@ static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStr
     // binary32 multi-step launches that fit in one wave with several blocks per SM are paced
     RolloutArgs b = a;
     void *pace = nullptr;
-    if (sizeof(R) == 4 && a.H > 1 && !a.pace_mask) {
+    if (sizeof(R) == 4 && a.H > 1 && a.cap > kPaceMinCap && !a.pace_mask) {
         int dev = 0, sms = 0, per_sm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
