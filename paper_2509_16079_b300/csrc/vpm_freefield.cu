@@ -163,7 +163,7 @@ constexpr int kFsRow = 128 * kFsWarps;      // targets of a row (4 per lane)
 constexpr int kFsTile = 512;                // sources per staged tile (16 blocks of 32)
 constexpr int kFsSeg = 32;                  // tiles per off-diagonal unit (16384 sources)
 #ifndef VPM_FS_MIN_BLOCKS
-#define VPM_FS_MIN_BLOCKS 3
+#define VPM_FS_MIN_BLOCKS 4
 #endif
 
 struct FsGeom {
