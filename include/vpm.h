@@ -213,7 +213,9 @@ vpm_status vpm_rollout_scratch_bytes(const vpm_state *state, int K, int H, size_
  *   d_count[K]               final particle count per rollout, or null
  * Binary32 roots whose field can grow past 128 particles need device scratch for the pair
  * sums (vpm_rollout_scratch_bytes); it is allocated on `stream` from the device's default
- * memory pool for the launch and freed after it (stream-ordered).
+ * memory pool for the launch and freed after it (stream-ordered). The first such allocation
+ * sets that pool's release threshold to its maximum, so freed memory stays cached in the pool
+ * for later calls (this affects every user of the default pool in the process).
  * Errors: VPM_ERR_INVALID (K, H < 1, null controls/costs), VPM_ERR_CAPACITY (the count could
  * exceed the capacity within H steps), VPM_ERR_CUDA.
  */
