@@ -801,32 +801,54 @@ __device__ void finalize_advect_f32(const DevParams &p, Work &w, float4 *part, c
     if (bad) atomicOr(&w.flag, (int)kStNonFinite);
 }
 
+// Convection velocity (Eq. 16) of one target at (x, z) on the binary64 path, by one warp: lane l
+// sums sources l, l + 32, ... in order, lanes below n_b add bound vortex l, and a butterfly
+// combines the 32 partial sums (every lane ends with the same bits). Binary64 warp instructions
+// take the same time however many lanes are active, so a warp per target keeps every lane busy
+// even when a block has few targets; the one-block and the cluster paths both use this order.
+template <int KER>
+__device__ __forceinline__ double2 convect_target_f64(const DevParams &p, const Work &w,
+                                                      const Part64 *part, int n1, double x,
+                                                      double z)
+{
+    const int lane = threadIdx.x & 31;
+    const Geo &G = w.geo;
+    double su = 0.0, sw = 0.0;
+    for (int j = lane; j < n1; j += 32) {
+        const Part64 s = part[j];
+        const double dx = x - s.x, dz = z - s.z;
+        const double g = s.g * PairF64<KER>::q(fma(dx, dx, dz * dz), p.rc4, p.inv_rc2);
+        su = fma(-dz, g, su);
+        sw = fma(dx, g, sw);
+    }
+    if (lane < p.n_b) {
+        const double sj = -0.5 * p.chord + (lane + 0.5) * p.lb;
+        const double dx = x - (G.xw + sj * G.tx), dz = z - (G.zw + sj * G.tz);
+        const double r2 = fma(dx, dx, dz * dz);
+        const double q = r2 > 0.0 ? w.gs[lane] / r2 : 0.0;
+        su = fma(-dz, q, su);
+        sw = fma(dx, q, sw);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    return make_double2(su * kInv2Pi + p.u_inf_x, sw * kInv2Pi + p.u_inf_z);
+}
+
+// Phase C on the binary64 path: one warp per target.
 template <int KER>
 __device__ void convect_f64(const DevParams &p, const Work &w, const Part64 *part, double2 *vel,
                             int n, double *probe_vel)
 {
-    const Geo &G = w.geo;
-    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int i = warp; i < n; i += nwarps) {
         const Part64 pi = part[i];
-        double su = 0.0, sw = 0.0;
-        for (int j = 0; j < n; ++j) {
-            const Part64 s = part[j];
-            double dx = pi.x - s.x, dz = pi.z - s.z;
-            double g = s.g * PairF64<KER>::q(fma(dx, dx, dz * dz), p.rc4, p.inv_rc2);
-            su = fma(-dz, g, su);
-            sw = fma(dx, g, sw);
+        const double2 v = convect_target_f64<KER>(p, w, part, n, pi.x, pi.z);
+        if (lane == 0) {
+            vel[i] = v;
+            if (probe_vel) { probe_vel[2 * i] = v.x; probe_vel[2 * i + 1] = v.y; }
         }
-        for (int j = 0; j < p.n_b; ++j) {
-            double sj = -0.5 * p.chord + (j + 0.5) * p.lb;
-            double dx = pi.x - (G.xw + sj * G.tx), dz = pi.z - (G.zw + sj * G.tz);
-            double r2 = fma(dx, dx, dz * dz);
-            double q = r2 > 0.0 ? w.gs[j] / r2 : 0.0;
-            su = fma(-dz, q, su);
-            sw = fma(dx, q, sw);
-        }
-        double u = su * kInv2Pi + p.u_inf_x, v = sw * kInv2Pi + p.u_inf_z;
-        vel[i] = make_double2(u, v);
-        if (probe_vel) { probe_vel[2 * i] = u; probe_vel[2 * i + 1] = v; }
     }
 }
 
@@ -1512,32 +1534,16 @@ __global__ void __launch_bounds__(kThreads) cluster_rollout_kernel(const Rollout
         }
         __syncthreads();
         const int n1 = w.n;
-        // convection of this CTA's slice of targets (Eq. 16), sources in the one-block order.
-        // Slots go round-robin over the warps first: binary64 throughput is per SM partition,
-        // so a small slice still keeps all four partitions busy.
+        // convection of this CTA's slice of targets (Eq. 16), one warp per target in the
+        // one-block order (convect_target_f64)
         const int per = (n1 + C - 1) / C, lo = min(n1, rank * per), hi = min(n1, lo + per);
         const int slot0 = warp + nwarps * lane, slot_step = nwarps * 32;
-        const Geo &G = w.geo;
-        for (int i = lo + slot0; i < hi; i += slot_step) {
+        for (int i = lo + warp; i < hi; i += nwarps) {
             const Part64 pi = part[i];
-            double su = 0.0, sw = 0.0;
-            for (int j = 0; j < n1; ++j) {
-                const Part64 sj = part[j];
-                const double dx = pi.x - sj.x, dz = pi.z - sj.z;
-                const double g = sj.g * PairF64<KER>::q(fma(dx, dx, dz * dz), p.rc4, p.inv_rc2);
-                su = fma(-dz, g, su);
-                sw = fma(dx, g, sw);
-            }
-            for (int j = 0; j < p.n_b; ++j) {
-                const double sj = -0.5 * p.chord + (j + 0.5) * p.lb;
-                const double dx = pi.x - (G.xw + sj * G.tx), dz = pi.z - (G.zw + sj * G.tz);
-                const double r2 = fma(dx, dx, dz * dz);
-                const double q = r2 > 0.0 ? w.gs[j] / r2 : 0.0;
-                su = fma(-dz, q, su);
-                sw = fma(dx, q, sw);
-            }
-            vel[i] = make_double2(su * kInv2Pi + p.u_inf_x, sw * kInv2Pi + p.u_inf_z);
+            const double2 v = convect_target_f64<KER>(p, w, part, n1, pi.x, pi.z);
+            if (lane == 0) vel[i] = v;
         }
+        __syncthreads();                             // vel of the slice is complete in this CTA
         cl.sync();                                   // every CTA is done reading the positions
         bool bad = false;
         for (int i = lo + slot0; i < hi; i += slot_step) {
