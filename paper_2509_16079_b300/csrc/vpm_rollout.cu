@@ -1117,8 +1117,10 @@ __device__ void finish(const RolloutArgs &a, Work &w, const typename Store<R>::P
 // block's warps cannot hide the latency of the pair loop's shuffles (measured: 66 % of the
 // SM's rate with one block). A block that is more than kPaceAhead steps ahead of the slowest
 // block on its SM therefore sleeps until that block catches up, for at most kPaceWaits short
-// sleeps per step; giving up only costs time, never changes a result.
-constexpr int kPaceSlots = 8, kPaceAhead = 1, kPaceWaits = 4000;
+// sleeps per step; giving up only costs time, never changes a result. Blocks more than
+// kPaceWindow steps behind are not waited for: such a block started late (other work held its
+// SM when the launch began) and cannot catch up.
+constexpr int kPaceSlots = 8, kPaceAhead = 1, kPaceWaits = 1000, kPaceWindow = 4;
 constexpr int kPaceSms = 1024;    // SM ids paced (blocks on an SM with a larger id are not)
 // Fields that stay small have short, plate-bound steps (~18 us at 60 particles), where a
 // 1 us sleep and the extra barrier cost more than the tail they remove: pacing is for launches
@@ -1155,8 +1157,11 @@ __device__ void pace_step(const RolloutArgs &a, unsigned sm, int slot, int k)
     for (int it = 0; it < kPaceWaits; ++it) {
         const unsigned m = atomicOr(&a.pace_mask[sm], 0u);
         int lo = INT_MAX;
-        for (int b = 0; b < kPaceSlots; ++b)
-            if (b != slot && (m & (1u << b))) lo = min(lo, atomicOr(&prog[b], 0));
+        for (int b = 0; b < kPaceSlots; ++b) {
+            if (b == slot || !(m & (1u << b))) continue;
+            const int pb = atomicOr(&prog[b], 0);
+            if (pb >= k - kPaceWindow) lo = min(lo, pb);
+        }
         if (lo == INT_MAX || k <= lo + kPaceAhead) return;
         __nanosleep(1000);
     }
