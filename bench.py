@@ -922,6 +922,46 @@ def run_serving(args):
                       "p50_ms": float(np.percentile(lat, 50)) if lat else None,
                       "p99_ms": float(np.percentile(lat, 99)) if lat else None,
                       "rollouts_per_s": done_k / wall, "wall_s": wall}
+    # sustainable-rate sweep: the same scenarios and request mix at total rates around one GPU's
+    # capacity (a request averages ~1.7e12 pair interactions, ~0.5 s of the device); a rate is
+    # sustained when no request is superseded and the p99 latency stays within twice the p99
+    # at the lowest rate
+    sweep, base_p99, sustained = [], None, None
+    for rate in args.serve_rates:
+        arr, strm = W.poisson_arrivals(11, rate / len(fields), args.serve_sweep_seconds, len(fields))
+        ks = W.request_sizes(12, len(arr))
+        srv = V.Server(max_inflight=16, max_rollouts=4096, max_horizon=Hh)
+        for f in fields:
+            p = W.glider_params(n_wake_max=len(f) + 300)
+            srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 300 + 2 * Hh + 8)
+        tickets, t0 = [], time.perf_counter()
+        for j, (ta, sc) in enumerate(zip(arr, strm)):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            k = int(ks[j])
+            tickets.append(srv.submit(int(sc), noise[k][j % 3], advance_steps=2, advance_u=0.0))
+        lat, done_k, sup = [], 0, 0
+        for t in tickets:
+            r = srv.poll(t)
+            if r[0]["status"] == V.VPM_OK:
+                lat.append(r[0]["t_done_ms"] - r[0]["t_submit_ms"])
+                done_k += r[0]["K"]
+            else:
+                sup += 1
+        wall = time.perf_counter() - t0
+        srv.close()
+        p99 = float(np.percentile(lat, 99)) if lat else None
+        if base_p99 is None:
+            base_p99 = p99
+        ok = sup == 0 and p99 is not None and base_p99 is not None and p99 <= 2.0 * base_p99
+        if ok:
+            sustained = rate
+        sweep.append({"offered_hz": rate, "offered": int(len(arr)), "completed": len(lat), "superseded": sup,
+                      "p50_ms": float(np.percentile(lat, 50)) if lat else None, "p99_ms": p99,
+                      "rollouts_per_s": done_k / wall, "sustained": ok})
+    out["rate_sweep"] = sweep
+    out["sustainable_rate_hz"] = sustained
     print(json.dumps(out), flush=True)
 
 # ------------------------------------------------------------------ reference arm (oracle)
@@ -977,6 +1017,9 @@ def main():
     ap.add_argument("--horizon", type=int, default=H)
     ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1", "policy", "nmpc", "plate"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0, 1.5, 2.0, 3.0],
+                    help="total request rates (Hz) of the serving workload's sustainable-rate sweep")
+    ap.add_argument("--serve-sweep-seconds", type=float, default=12.0)
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
     ap.add_argument("--n", type=int, default=1 << 20, help="free-field particle count")
