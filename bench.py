@@ -91,6 +91,47 @@ def profiled_pipes(summary: str, source: str):
             "capture": "ncu --set full on the small case of profiles/%s" % summary}
 
 
+def graph_replans(V, L, stream, flush, replans, body, state):
+    """Replan latency of the graph-captured form: body(stream_handle) enqueues one replan; it is
+    captured once into a CUDA graph and replayed `replans` times (L2 flushed in between, outside
+    the events). The replayed replan must give the same bits as the eager one from the same
+    state. Returns p50/p99 ms, or the reason capture failed."""
+    import torch
+    try:
+        cs = torch.cuda.Stream()
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            body(V.stream_handle(cs))                       # warm-up on the capture stream
+        stream.wait_stream(cs)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cs, capture_error_mode="thread_local"):
+            body(V.stream_handle(cs))
+        torch.cuda.synchronize()
+        s0 = state.clone()
+        body(V.stream_handle(stream))                       # eager replan from s0
+        torch.cuda.synchronize()
+        eager = state.clone()
+        state.copy_(s0)
+        g.replay()
+        torch.cuda.synchronize()
+        same = bool(torch.equal(state, eager))
+        lat = []
+        for r in range(replans):
+            flush.fill_(float(r))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+        return {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                "replans": len(lat), "same_bits_as_eager": same}
+    except Exception as e:                                   # report, keep the eager numbers
+        torch.cuda.synchronize()
+        return {"unavailable": str(e)[:200]}
+
+
 # ------------------------------------------------------------------ clocks during the run
 class ClockSampler:
     def __init__(self, index: int):
@@ -249,12 +290,15 @@ def run_gpu(args):
     sh = V.stream_handle(stream)
     L = V.lib()
 
-    def iteration(j):
-        V.check(L.mppi_perturb(V.ptr(mu), V.ptr(eps_all[j % n_iter_noise]), K_ROLL, H, V.ptr(controls), sh))
+    def iteration_on(j, hs):
+        V.check(L.mppi_perturb(V.ptr(mu), V.ptr(eps_all[j % n_iter_noise]), K_ROLL, H, V.ptr(controls), hs))
         V.check(L.vpm_rollout_batch(root.handle, K_ROLL, H, V.ptr(controls), V.ptr(costs), None, None,
-                                    None, None, sh))
-        V.check(L.mppi_weights(V.ptr(costs), K_ROLL, LAMBDA, V.ptr(weights), sh))
-        V.check(L.mppi_update(V.ptr(weights), V.ptr(controls), K_ROLL, H, V.ptr(mu), sh))
+                                    None, None, hs))
+        V.check(L.mppi_weights(V.ptr(costs), K_ROLL, LAMBDA, V.ptr(weights), hs))
+        V.check(L.mppi_update(V.ptr(weights), V.ptr(controls), K_ROLL, H, V.ptr(mu), hs))
+
+    def iteration(j):
+        iteration_on(j, sh)
 
     for j in range(args.warmup):
         iteration(j)
@@ -303,6 +347,8 @@ def run_gpu(args):
     rep.sort()
     p50 = float(np.percentile(rep, 50)) if rep else None
     p99 = float(np.percentile(rep, 99)) if rep else None
+    replan_graph = graph_replans(V, L, stream, flush, args.replans,
+                                 lambda hs: [iteration_on(j, hs) for j in range(3)], mu)
 
     # end-to-end: host noise -> device each iteration, nominal controls back to the host
     eps_host = [torch.tensor(W.mppi_noise(2000 + j, K_ROLL, H, W.MPPI_SIGMA_U)).pin_memory()
@@ -353,7 +399,8 @@ def run_gpu(args):
             "l2": "flushed between timed iterations (256 MB write outside the events)",
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
-        "replan_ms": {"p50": p50, "p99": p99, "replans": len(rep), "iterations_per_replan": 3},
+        "replan_ms": {"p50": p50, "p99": p99, "replans": len(rep), "iterations_per_replan": 3,
+                      "form": "eager launches", "graph": replan_graph},
         "e2e": {"value": e2e_value, "unit": "pair-interactions/s",
                 "h2d_bytes_per_step": K_ROLL * H * 4, "d2h_bytes_per_step": H * 4,
                 "steps": e2e_steps},
@@ -788,6 +835,20 @@ def run_northstar(args):
         b.record()
         b.synchronize()
         lat.append(a.elapsed_time(b))
+    # the same replans captured once into a CUDA graph and replayed
+    mu_s = mu.clone()
+
+    def body(hs):
+        m = mu_s
+        for j in range(3):
+            c = V.mppi_perturb(m, eps[j])
+            out = root.rollout_batch(c, want_final=False)
+            m = V.mppi_update(V.mppi_weights(out["costs"], LAMBDA), c)
+        mu_s.copy_(m)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    graph = graph_replans(V, V.lib(), torch.cuda.current_stream(), flush, args.replans, body, mu_s)
+    del flush
     # one-rollout-per-launch form on a subset
     ks = args.per_launch_subset
     c = V.mppi_perturb(mu, eps[0])[:ks].contiguous()
@@ -806,7 +867,9 @@ def run_northstar(args):
         "metric": "MPPI replan latency (3 iterations)", "unit": "ms", "higher_is_better": False,
         "config": {"workload": "K=1024 x H=100, fields %d -> %d particles" % (n0, n0 + 2 * Hh)},
         "persistent": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "replans": len(lat), "pairs_per_s": 3 * pairs_iter / (np.median(lat) / 1e3)},
+                       "replans": len(lat), "pairs_per_s": 3 * pairs_iter / (np.median(lat) / 1e3),
+                       "form": "eager launches"},
+        "persistent_graph": graph,
         "one_rollout_per_launch": {"replan_ms_scaled": 3 * per_launch_iter_ms,
                                    "timed_rollouts": ks, "launches_per_iteration": K * Hh,
                                    "bitwise_equal_costs": same},
