@@ -175,6 +175,32 @@ def test_paced_launch_matches_unpaced_launches():
         assert torch.equal(part["final_glider"], full["final_glider"][b:b + 128])
 
 
+def test_rollout_batch_replays_from_a_cuda_graph():
+    """A rollout batch captured into a CUDA graph (its pair-sum scratch and pacing table are
+    allocated stream-ordered inside the capture) gives the eager launch's bits on replay."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(4, K=1024, H=5, n=400)
+    st = V.State(p, field, xg0, 420)
+    c = torch.tensor(eps, device="cuda")
+    eager = st.rollout_batch(c)
+    costs = torch.empty(1024, dtype=torch.float32, device="cuda")
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cs):
+        st.rollout_batch(c, want_final=False, costs=costs)        # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(cs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cs, capture_error_mode="thread_local"):
+        st.rollout_batch(c, want_final=False, costs=costs)
+    costs.zero_()
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(costs, eager["costs"])
+        costs.zero_()
+
+
 def test_full_size_batch_properties(ora):
     """K = 1024 rollouts x 100 steps from 1000 particles, binary32, the benchmark's launch:
     every rollout ends with 1200 particles and finite costs; sampled rollouts are rerun alone
