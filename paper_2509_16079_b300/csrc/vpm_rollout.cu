@@ -12,6 +12,7 @@
 // decay of Eq. 17; merging of the two oldest particles while N > N_w,max.
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <climits>
 #include <mutex>
 
@@ -1256,18 +1257,34 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const Ro
 
 // ------------------------------------------------------------------ host-side launch helpers
 
+// Raises a kernel's dynamic shared-memory limit to at least smem, once per size increase (the
+// 48 KB default covers static + dynamic, so launchers always opt in; the library runs on one
+// device per process). Host threads may launch at the same time (the NMPC planner and control
+// paths, the serving worker), so the raise happens under a lock and the limit only grows.
+static std::mutex g_grant_mutex;
+
+template <class F>
+static cudaError_t grant_smem(F k, std::atomic<size_t> &granted, size_t smem)
+{
+    if (smem <= granted.load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_grant_mutex);
+    if (smem <= granted.load(std::memory_order_relaxed)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    granted.store(smem, std::memory_order_release);
+    return cudaSuccess;
+}
+
 template <class R, int KER, int NT>
 static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
     auto k = rollout_kernel<R, KER, NT>;
     // raise the kernel's dynamic shared-memory limit once per size increase (per process;
     // the library runs on one device per process)
-    static size_t granted = 0;          // the 48 KB default covers static + dynamic: always opt in
-    if (smem > granted) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    static std::atomic<size_t> granted{0};
+    {
+        const cudaError_t e = grant_smem(k, granted, smem);
         if (e != cudaSuccess) return e;
-        granted = smem;
     }
     // binary32 multi-step launches that fit in one wave with several blocks per SM are paced
     RolloutArgs b = a;
@@ -1392,14 +1409,12 @@ template <class R, int KER, int NT>
 static cudaError_t launch_u(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
     auto k = uneven_kernel<R, KER, NT>;
-    static size_t granted = 0;          // the 48 KB default covers static + dynamic: always opt in
+    static std::atomic<size_t> granted{0};
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
-    if (smem > granted && cs == cudaStreamCaptureStatusNone) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    if (cs == cudaStreamCaptureStatusNone) {         // under capture the batch raised it before
+        const cudaError_t e = grant_smem(k, granted, smem);
         if (e != cudaSuccess) return e;
-        granted = smem;
     }
     k<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
@@ -1582,14 +1597,15 @@ template <int KER>
 static cudaError_t launch_cluster_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
     auto k = cluster_rollout_kernel<KER>;
-    static size_t granted = 0;
-    static int csize = 0;
-    if (smem > granted) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<size_t> granted{0};
+    static std::atomic<int> csize_cached{0};
+    {
+        const cudaError_t e = grant_smem(k, granted, smem);
         if (e != cudaSuccess) return e;
-        granted = smem;
     }
+    int csize = csize_cached.load(std::memory_order_acquire);
     if (!csize) {                                    // 16 CTAs where the part allows, else 8
+        std::lock_guard<std::mutex> lock(g_grant_mutex);
         csize = 8;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
             cudaLaunchConfig_t q = {};
@@ -1605,6 +1621,7 @@ static cudaError_t launch_cluster_t(const RolloutArgs &a, int grid, size_t smem,
             if (cudaOccupancyMaxActiveClusters(&clusters, k, &q) == cudaSuccess && clusters > 0) csize = 16;
         }
         cudaGetLastError();
+        csize_cached.store(csize, std::memory_order_release);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid * csize);
