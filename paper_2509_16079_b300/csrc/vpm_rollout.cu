@@ -1,6 +1,6 @@
-// Persistent rollout kernel: one 128-thread block advances one rollout of the coupled
-// glider + VPM model (§III-A, §III-B) for the whole horizon with the field resident in shared
-// memory, then writes the terminal cost (Eq. 24). The same step code serves vpm_step (one
+// Persistent rollout kernel: one block (128 threads on the MPPI batch; 256 or 512 for larger
+// fields) advances one rollout of the coupled glider + VPM model (§III-A, §III-B) for the whole
+// horizon with the field resident in shared memory, then writes the terminal cost (Eq. 24). The same step code serves vpm_step (one
 // block, one step, state written back) and the one-rollout-per-launch comparison form.
 //
 // One step, in the order of §III-A: plate geometry from the glider state; relative velocity of
@@ -55,7 +55,7 @@ struct Work {
     Geo geo;
     int n;
     int flag;
-    int chunk_next;                  // next unclaimed target chunk of the pair sums
+    int chunk_next;                  // next unclaimed unit of the pair sums (rows, then diagonals)
     int ndist;                       // 2 while the first two records are the disturbance pair
 #if VPM_DEBUG_BOUNDS
     int cap;                         // records the shared arrays hold
@@ -974,7 +974,7 @@ __device__ __forceinline__ int plate_warp()
 }
 
 // One full step of one rollout. All threads call it with the same particle count n (updated
-// here) and chunk-claim base; returns with the block synchronised.
+// here) and unit-claim base; returns with the block synchronised.
 template <class R, int KER>
 __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *part,
                           typename Store<R>::V *vel, double u_ctrl, const RolloutArgs &a,
