@@ -464,7 +464,9 @@ vpm_status vpm_server_destroy(vpm_server *server);
 /*
  * The same Heun steps as vpm_freefield_heun for callers that must not let the library
  * allocate device memory, such as a control loop whose memory is fixed before it starts or a
- * host that gives all device memory to another owner. The paper has no counterpart; it is a
+ * host that gives all device memory to another owner. It evaluates every pair once per target
+ * (vpm_freefield_heun evaluates each pair once for both particles, which needs n^2-sized
+ * scratch), so the two agree to binary32 rounding, not bit for bit. The paper has no counterpart; it is a
  * deployment variant. Its scratch is one device array of fixed size built into the library
  * (6 MiB, reserved on every device that loads the library until the process exits), so n is
  * limited to 262144 particles; larger n returns VPM_ERR_CAPACITY without launching anything.
