@@ -231,6 +231,34 @@ def test_full_size_batch_properties(ora):
     assert normwise(vel, ref["vel"]) <= VEL_TOL
 
 
+def test_north_star_size_batch_properties(ora):
+    """K = 1024 rollouts x 100 steps from 1900 particles (fields up to 2100), the replan
+    benchmark's launch (256-thread blocks, more than one wave, one evaluation per pair across
+    16 rows): counts and costs, sampled rollouts rerun alone bitwise, and a step from a sampled
+    final state against the oracle's step from that state."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(0, K=1024, H=100, n=1900)
+    st = V.State(p, field, xg0, 2100)
+    c = torch.tensor(eps, device="cuda")
+    out = st.rollout_batch(c, want_field=True)
+    torch.cuda.synchronize()
+    st.status()
+    assert (out["count"] == 2100).all()
+    assert torch.isfinite(out["costs"]).all()
+    for i in (0, 700, 1023):
+        one = st.rollout_batch(c[i:i + 1].contiguous(), want_field=True)
+        assert torch.equal(one["costs"][0], out["costs"][i])
+        assert torch.equal(one["field"][0], out["field"][i])
+    fin = out["field"][700, :2100].cpu().numpy()
+    xg = out["final_glider"][700].cpu().numpy()
+    g = V.State(p, fin, xg, 2102)
+    probe = g.step(-0.2, probe=True)
+    o = ora.State(p, fin, xg, 2102)
+    ref = o.step(-0.2)
+    vel = probe["vel"].cpu().numpy()[:2 * 2102].reshape(-1, 2)
+    assert normwise(vel, ref["vel"]) <= VEL_TOL
+
+
 def test_launch_sizes_across_the_48k_default():
     """Every field size launches in a fresh process, including those whose dynamic shared memory
     is under 48 KB but whose dynamic + static memory is over it (the default limit covers both)."""
