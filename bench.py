@@ -476,9 +476,12 @@ def run_freefield(args):
     Pf = d[:, :3].double().cpu().numpy()
     idx = W.sample_indices(1, n, 4096)
     chunks = np.array_split(idx, os.cpu_count() or 1)
+    t_ora = time.perf_counter()
     with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
         parts = list(ex.map(lambda c: oracle.velocity_at(Pf, Pf[c, :2], 1, rc, skip=c), chunks))
+    t_ora = time.perf_counter() - t_ora
     ref = np.concatenate(parts)
+    ora_pairs = float(len(idx)) * n
     got = vel.cpu().numpy()[idx].astype(np.float64)
     err = np.linalg.norm(got - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max()
     achieved = n * float(n) * FLOPS_PER_PAIR / (kern_ms / 1e3) / 1e12
@@ -490,6 +493,11 @@ def run_freefield(args):
         "config": {"workload": "free field N=%d, 64 Gaussian blobs sigma 0.1 in a 10x10 box, "
                                "Vatistas core 1e-3, Heun dt=1e-3" % n, "pairs_per_step": 2 * n * n},
         "error_vs_fp64_oracle": {"normwise_velocity": err, "targets": int(len(idx))},
+        "cpu_baseline": {"value": ora_pairs / t_ora, "unit": "pair-interactions/s",
+                         "cores": len(chunks), "kind": "oracle",
+                         "per_core": ora_pairs / t_ora / len(chunks), "cpu_model": cpu_model(),
+                         "sample": "%d sampled targets against all %d sources (FP64 C oracle), %.1f s wall"
+                                   % (len(idx), n, t_ora)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "kernel": "freefield_sym_kernel<Vatistas> + freefield_combine_kernel (one velocity "
