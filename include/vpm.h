@@ -201,6 +201,11 @@ vpm_status vpm_step(vpm_state *state, double u, double *d_fm, double *d_gamma_s,
  */
 vpm_status vpm_rollout_scratch_bytes(const vpm_state *state, int K, int H, size_t *bytes);
 
+/* The same for K rollout blocks whose fields can reach `capacity` particles, without a state
+ * (precision VPM_FP32 or VPM_FP64; host only). Errors: VPM_ERR_INVALID (null, K < 1,
+ * capacity < 0, unknown precision). */
+vpm_status vpm_rollout_scratch_bytes_cap(int precision, int capacity, int K, size_t *bytes);
+
 /*
  * K independent rollouts of H steps from the root model, which is not modified. Rollout i
  * applies elevator rates d_controls[i*H + k] (binary32, K x H row-major). One thread block

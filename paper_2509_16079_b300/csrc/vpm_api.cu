@@ -594,6 +594,14 @@ size_t rollout_scratch_bytes(const vpm_state *s, int K, int H, int advance)
 }
 }  // namespace vpm
 
+extern "C" vpm_status vpm_rollout_scratch_bytes_cap(int precision, int capacity, int K, size_t *bytes)
+{
+    if (!bytes || K < 1 || capacity < 0 || (precision != VPM_FP32 && precision != VPM_FP64))
+        return fail(VPM_ERR_INVALID, "vpm_rollout_scratch_bytes_cap: null, K < 1, capacity < 0 or bad precision");
+    *bytes = sizeof(float2) * (size_t)K * (size_t)rollout_rev_slots(precision, capacity);
+    return VPM_OK;
+}
+
 extern "C" vpm_status vpm_rollout_scratch_bytes(const vpm_state *s, int K, int H, size_t *bytes)
 {
     if (!s || !bytes || K < 1 || H < 1) return fail(VPM_ERR_INVALID, "vpm_rollout_scratch_bytes: null or K, H < 1");
