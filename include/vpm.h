@@ -114,7 +114,9 @@ vpm_status vpm_state_destroy(vpm_state *state);
 /*
  * Sets the previous-step bound circulations h_gb_prev[n_b], the previous LEV circulation and
  * whether they are valid (has_prev = 0 makes the next step's derivatives zero). Synchronises
- * `stream`.
+ * `stream`. The previous LEV circulation is kept with the state for the caller's records;
+ * the pressure of Eq. 13 does not use it: each step sheds a new LEV, and the derivative of
+ * the leading-edge circulation in Eq. 13 is that new LEV's circulation over dt.
  */
 vpm_status vpm_state_set_history(vpm_state *state, const double *h_gb_prev, double glev_prev,
                                  int has_prev, cudaStream_t stream);

@@ -26,7 +26,11 @@
  *  - M_w is the counter-clockwise moment about x_w of the pressure forces of Eq. 14,
  *    sum (r_b - x_w) x (l_b s dp e_n);
  *  - the time derivatives in Eq. 13 are backward differences over one step, zero on the
- *    first step;
+ *    first step. Every step sheds a new LEV (§III-A), and the potential jump across the
+ *    plate at panel i holds the bound circulation from the leading edge to panel i plus all
+ *    circulation shed at the leading edge so far. Its derivative therefore takes the new
+ *    LEV's whole circulation over the step: dGamma_LEV/dt = Gamma_LEV^n / dt, the rate at
+ *    which the leading edge sheds circulation;
  *  - the moment arms of §III-B's pitch equation are the world-frame offsets of x_w and x_e
  *    (Eq. 18) from the centre of gravity;
  *  - step order: geometry, relative velocity at the plate from the wake before shedding,
@@ -339,7 +343,8 @@ double ora_terminal_cost(const ora_params *p, const double *xg) { return termina
  *   n, x, z, g     : wake particles (in/out; capacity entries allocated)
  *   xg             : glider state (7, in/out)
  *   gb_prev        : bound circulations of the previous step (n_b, in/out)
- *   glev_prev      : LEV circulation of the previous step (in/out)
+ *   glev_prev      : LEV circulation of the previous step (in/out; kept with the state, not
+ *                    needed by Eq. 13 under the reading above)
  *   has_prev       : 0 on the first step (time derivatives are zero), set to 1
  * Optional outputs (NULL to skip):
  *   out_gs         : Gamma_S = [Gamma_b(n_b), Gamma_LEV, Gamma_TEV]
@@ -487,7 +492,7 @@ static int step_impl(const ora_params *p, int capacity, int *n_io, double *x, do
         cum_prev += gb_prev[i];
         double tang = (gs[i] / G.lb) * (vbx[i] * G.tx + vbz[i] * G.tz);
         double dsum = *has_prev ? (cum - cum_prev) / dt : 0.0;
-        double dlev = *has_prev ? (gs[nb] - *glev_prev) / dt : 0.0;
+        double dlev = *has_prev ? gs[nb] / dt : 0.0;     /* the new LEV's circulation over dt */
         double dp = p->rho * (tang + dsum + dlev);
         double fx = G.lb * p->span * dp * G.nx, fz = G.lb * p->span * dp * G.nz;
         fwx += fx;

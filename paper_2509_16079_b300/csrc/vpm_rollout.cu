@@ -311,9 +311,11 @@ __device__ int plate_solve(const DevParams &p, Work &w, typename Store<R>::P *pa
     }
     __syncwarp();
     // unsteady Bernoulli pressure (Eq. 13) and panel loads (Eqs. 14-15), one panel per lane;
-    // the running sums of Gamma_b up to the panel are formed as in a serial pass
+    // the running sums of Gamma_b up to the panel are formed as in a serial pass. Each step
+    // sheds a new LEV, and all circulation shed at the leading edge counts in the potential
+    // jump across the plate, so its time derivative is the new LEV's circulation over dt.
     const bool hp = w.hist[nb + 1] != 0.0;
-    const double dlev = hp ? (w.gs[nb] - w.hist[nb]) * p.inv_dt : 0.0;
+    const double dlev = hp ? w.gs[nb] * p.inv_dt : 0.0;
     for (int i = lane; i < nb; i += 32) {
         double cum = 0.0, cum_prev = 0.0;
         for (int k = 0; k <= i; ++k) {
