@@ -47,3 +47,42 @@ def wagner_jones(s):
     """R. T. Jones' two-exponential approximation of Wagner's indicial lift function,
     s = distance travelled in semichords."""
     return 1.0 - 0.165 * np.exp(-0.0455 * s) - 0.335 * np.exp(-0.3 * s)
+
+
+def vortex_impulse(points, gammas):
+    """Hydrodynamic impulse per unit density and span of a system of point vortices in the
+    plane: P = sum_k Gamma_k r_k x e_out, with e_out the out-of-plane axis about which
+    circulation is positive (counter-clockwise in the (x, z) plane, z up). In (x, z)
+    components, r x e_out = (z, -x). The fluid's momentum changes only by the force the
+    body exerts on it, so the force of the fluid on the body is -rho s dP/dt."""
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, 2)
+    g = np.asarray(gammas, dtype=np.float64).reshape(-1)
+    return np.array([(g * pts[:, 1]).sum(), -(g * pts[:, 0]).sum()])
+
+
+def elevator_point(xg, l, l_e):
+    """Elevator point of the planar glider: the tail hinge lies l behind the centre of gravity
+    along the body axis (cos theta, sin theta), the elevator point l_e behind the hinge along
+    the elevator chord (cos(theta + phi), sin(theta + phi))."""
+    x, z, th, ph = xg[0], xg[1], xg[2], xg[3]
+    return np.array([x - l * math.cos(th) - l_e * math.cos(th + ph),
+                     z - l * math.sin(th) - l_e * math.sin(th + ph)])
+
+
+def wing_point(xg, l_w):
+    """Wing centre: l_w behind the centre of gravity along the body axis."""
+    x, z, th = xg[0], xg[1], xg[2]
+    return np.array([x - l_w * math.cos(th), z - l_w * math.sin(th)])
+
+
+def point_velocity(point_of, xg, u, h=1e-6):
+    """Velocity of a body point by a central difference along the state's own motion
+    (constant rates xdot, zdot, thetadot and elevator rate u over +-h)."""
+    xg = np.asarray(xg, dtype=np.float64)
+    rate = np.array([xg[4], xg[5], xg[6], u, 0.0, 0.0, 0.0])
+    return (point_of(xg + h * rate) - point_of(xg - h * rate)) / (2 * h)
+
+
+def cross2(a, b):
+    """Planar cross product a x b = a_x b_z - a_z b_x (counter-clockwise positive)."""
+    return a[0] * b[1] - a[1] * b[0]

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from tests.independent import cross2, elevator_point, point_velocity, wing_point
 
 
 def test_ballistic_euler_recurrence(ora):
@@ -66,6 +67,96 @@ def test_tail_is_pitch_stabilising(ora):
     xg = np.array([0, 0, 0.0, 0.1, 7.0, 0.0, 0.0])
     f = ora.glider_rhs(p, xg, (0.0, 0.0), 0.0, 0.0)
     assert f[6] < 0 and f[5] > -p["g"]
+
+
+# Hand-chosen glider states (x, z, theta, phi, xdot, zdot, thetadot) and elevator rates u with
+# the elevator at incidence: level flight with a deflected elevator, a climb with pitch rate,
+# a dive pitching down, and a slow, steep state with the elevator moving (u != 0).
+_ELEVATOR_CASES = [
+    ((0.0, 0.0, 0.0, 0.1, 7.0, 0.0, 0.0), 0.0),
+    ((1.0, -0.5, 0.25, -0.15, 6.0, 1.5, 0.8), 0.0),
+    ((-2.0, 3.0, -0.4, 0.3, 8.0, -3.0, -1.1), 0.0),
+    ((0.5, 0.2, 0.9, -0.6, 2.5, -1.0, 0.4), 2.3),
+]
+
+
+def _elevator_force_flat_plate(p, xg, u):
+    """Elevator load from flat-plate theory (§III-B, Eqs. 19-20), from the geometry alone: the
+    elevator point's velocity by differencing its position, the incidence from the cross
+    product of the unit velocity with the elevator chord, and the normal force
+    (1/2) rho |v|^2 S_e C_n with C_n = 2 sin(alpha_e) along the body-up elevator normal."""
+    v = point_velocity(lambda s: elevator_point(s, p["l"], p["l_e"]), xg, u)
+    a = xg[2] + xg[3]
+    chord = np.array([math.cos(a), math.sin(a)])
+    normal = np.array([-math.sin(a), math.cos(a)])
+    sin_alpha = cross2(v / np.linalg.norm(v), chord)
+    return 0.5 * p["rho"] * (v @ v) * p["s_e"] * (2.0 * sin_alpha) * normal, v
+
+
+def test_elevator_force_is_flat_plate_normal_force(ora):
+    """With no wing load the translational equations (Eq. 21) carry the elevator force alone:
+    m (xddot, zddot + g) must equal the flat-plate normal force at each state. A missing 1/2,
+    C_n = sin(alpha_e), a wrong S_e or a wrong incidence sign fails here."""
+    p = W.glider_params()
+    for xg, u in _ELEVATOR_CASES:
+        xg = np.array(xg)
+        f = ora.glider_rhs(p, xg, (0.0, 0.0), 0.0, u)
+        fe = p["mass"] * np.array([f[4], f[5] + p["g"]])
+        ref, _ = _elevator_force_flat_plate(p, xg, u)
+        assert np.linalg.norm(ref) > 0.05
+        assert np.allclose(fe, ref, rtol=1e-7, atol=1e-9 * np.linalg.norm(ref))
+    # level flight at 7 m/s with the elevator 0.1 rad nose-up: |F_e| = rho V^2 S_e sin(0.1)
+    xg = np.array(_ELEVATOR_CASES[0][0])
+    f = ora.glider_rhs(p, xg, (0.0, 0.0), 0.0, 0.0)
+    mag = p["mass"] * math.hypot(f[4], f[5] + p["g"])
+    assert mag == pytest.approx(1.2 * 49.0 * 0.1 * math.sin(0.1), rel=1e-12)
+
+
+def test_elevator_force_dissipates(ora):
+    """A flat plate's normal force never drives it: with the elevator fixed to the body
+    (u = 0) the force's power on the elevator point is -rho S_e |v|^3 sin^2(alpha_e) <= 0."""
+    p = W.glider_params()
+    for xg, u in _ELEVATOR_CASES[:3]:
+        xg = np.array(xg)
+        f = ora.glider_rhs(p, xg, (0.0, 0.0), 0.0, u)
+        fe = p["mass"] * np.array([f[4], f[5] + p["g"]])
+        _, v = _elevator_force_flat_plate(p, xg, u)
+        a = xg[2] + xg[3]
+        sin_alpha = cross2(v / np.linalg.norm(v), np.array([math.cos(a), math.sin(a)]))
+        power = fe @ v
+        assert power < 0
+        assert power == pytest.approx(-p["rho"] * p["s_e"] * np.linalg.norm(v) ** 3 * sin_alpha ** 2,
+                                      rel=1e-6)
+
+
+def test_pitch_moment_arms_rigid_body_power(ora):
+    """Pitch equation (Eq. 22) with the elevator fixed to the body (u = 0): the power of the wing
+    force at x_w, the elevator force at x_e and the couple M_w equals the power of the net force
+    at the centre of gravity plus torque times pitch rate, (F_w + F_e) . v_cg + tau thetadot,
+    for any loads, if and only if tau is the moment of the forces about the centre of gravity
+    with their true points of application. The point velocities come from differencing the
+    positions (Eq. 18), not from the oracle's formulas. The torque is also checked directly
+    as (x_w - x_cg) x F_w + (x_e - x_cg) x F_e + M_w."""
+    p = W.glider_params()
+    rng = np.random.default_rng(5)
+    for xg, _ in _ELEVATOR_CASES[:3]:
+        xg = np.array(xg)
+        for _ in range(4):
+            fw = rng.normal(scale=20.0, size=2)
+            mw = float(rng.normal(scale=3.0))
+            f = ora.glider_rhs(p, xg, fw, mw, 0.0)
+            f0 = ora.glider_rhs(p, xg, (0.0, 0.0), 0.0, 0.0)
+            fe = p["mass"] * np.array([f0[4], f0[5] + p["g"]])        # elevator load alone
+            tau = p["inertia"] * f[6]
+            vw = point_velocity(lambda s: wing_point(s, p["l_w"]), xg, 0.0)
+            ve = point_velocity(lambda s: elevator_point(s, p["l"], p["l_e"]), xg, 0.0)
+            vcg = xg[4:6]
+            lhs = fw @ vw + fe @ ve + mw * xg[6]
+            rhs = (fw + fe) @ vcg + tau * xg[6]
+            assert lhs == pytest.approx(rhs, rel=1e-7, abs=1e-7)
+            xe = elevator_point(xg, p["l"], p["l_e"]) - xg[:2]
+            xw = wing_point(xg, p["l_w"]) - xg[:2]
+            assert tau == pytest.approx(cross2(xw, fw) + cross2(xe, fe) + mw, rel=1e-10, abs=1e-12)
 
 
 def test_terminal_cost(ora):
