@@ -475,14 +475,19 @@ vpm_status vpm_server_destroy(vpm_server *server);
  * (vpm_freefield_heun evaluates each pair once for both particles, which needs n^2-sized
  * scratch), so the two agree to binary32 rounding, not bit for bit. The paper has no counterpart; it is a
  * deployment variant. Its scratch is one device array of fixed size built into the library
- * (6 MiB, reserved on every device that loads the library until the process exits), so n is
+ * (6 MiB, held on every device where it has been taken until the process exits), so n is
  * limited to 262144 particles; larger n returns VPM_ERR_CAPACITY without launching anything.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current; make that first call before capturing the stream into a graph.
- * Every call on a device uses the same array: calls whose work overlaps on the GPU (other
- * streams, other host threads) race on it and must be serialised by the caller. Nothing in
- * the array needs clearing between calls: each step writes it fully before reading it.
- * No cudaMalloc, cudaFree or other allocating routine is called.
+ * Every call looks up that array's device address (cudaGetSymbolAddress) with the caller's
+ * device current. CUDA loads a library's device code lazily by default, so the array's 6 MiB
+ * are taken from the device on the first call on that device (n >= 1 and steps >= 1; calls
+ * with n = 0 or steps = 0 return before the lookup), and that first call can fail with
+ * VPM_ERR_CUDA if other owners already hold all device memory. Make one such warm-up call
+ * (n = 1, steps = 1 is enough) before fixing the process's memory, handing device memory to
+ * another owner, or capturing the stream into a graph. Every call on a device uses the same
+ * array: calls whose work overlaps on the GPU (other streams, other host threads) race on it
+ * and must be serialised by the caller. Nothing in the array needs clearing between calls:
+ * each step writes it fully before reading it. No cudaMalloc, cudaFree or other allocating
+ * routine is called.
  */
 vpm_status vpm_freefield_heun_noalloc(float *d_particles, int n, int kernel, double r_core,
                                       double dt, int steps, cudaStream_t stream);

@@ -5,10 +5,10 @@
 // library allocate: a real-time control loop whose memory is fixed up front (an allocation can
 // stall or fail in the middle of a control period), or a host process that hands the GPU over
 // to code that owns all device memory. For them this file keeps the scratch in one statically
-// sized device array, reserved when the library is loaded, and vpm_freefield_heun_noalloc uses
+// sized device array, which the device gives to the library when its device code is loaded
+// (lazily by default: on the first call on that device), and vpm_freefield_heun_noalloc uses
 // it instead of allocating; it evaluates every pair once per target, which needs only the
 // 24 n bytes.
-#include <mutex>
 #include <stdio.h>
 
 #include "vpm_device.cuh"
@@ -26,34 +26,28 @@ vpm_status report_error(vpm_status st, const char *msg);
 static constexpr int kNoAllocMaxN = 262144;
 static __device__ __align__(256) float g_heun_scratch[(size_t)kNoAllocMaxN * 6];
 
-// Device address of g_heun_scratch, looked up once per device. In host code the array's name
-// only stands in for the symbol; it is not a device pointer.
-static constexpr int kMaxDevices = 64;
-static float *g_scratch_addr[kMaxDevices];
-static std::mutex g_scratch_mutex;
-
+// Device address of g_heun_scratch on the current device. In host code the array's name only
+// stands in for the symbol; it is not a device pointer. The address is looked up on every call
+// (cheap once the module is loaded) rather than cached, so that a device reset, after which
+// the module is loaded again at a possibly different address, cannot leave a stale pointer.
 static vpm_status scratch_for_current_device(float **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess || dev < 0) {
         cudaGetLastError();
         return vpm::report_error(VPM_ERR_CUDA, "vpm_freefield_heun_noalloc: no usable current CUDA device");
     }
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_heun_scratch);
-        if (e != cudaSuccess || !ptr) {
-            cudaGetLastError();
-            char msg[256];
-            snprintf(msg, sizeof msg, "vpm_freefield_heun_noalloc: cudaGetSymbolAddress failed: %s",
-                     cudaGetErrorString(e));
-            return vpm::report_error(VPM_ERR_CUDA, msg);
-        }
-        g_scratch_addr[dev] = static_cast<float *>(ptr);
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_heun_scratch);
+    if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        char msg[256];
+        snprintf(msg, sizeof msg, "vpm_freefield_heun_noalloc: cudaGetSymbolAddress failed: %s",
+                 cudaGetErrorString(e));
+        return vpm::report_error(VPM_ERR_CUDA, msg);
     }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<float *>(ptr);
     return VPM_OK;
 }
 

@@ -76,15 +76,17 @@ def _conditioned_check(ora, p, field, xg0, eps, res, bump, glider_tol, cost_rel)
     return conditioned
 
 
-def test_fp64_ungated_100_steps(ora):
-    """Binary64 path, ungated 1000-particle workload, 100 steps, K = 16, every rollout. The
-    oracle's own 100-step field moves by 4e-7 .. 0.7 c when the initial positions move by
-    1e-13, so the check is conditioning-aware (_conditioned_check)."""
+@pytest.mark.parametrize("H,min_conditioned", [(50, 16), (100, 2)])
+def test_fp64_ungated(ora, H, min_conditioned):
+    """Binary64 path, ungated 1000-particle workload, K = 16, every rollout, after 50 and 100
+    steps. The oracle's own 100-step field moves by 1e-7 .. 0.75 c when the initial positions
+    move by 1e-13, so the check is conditioning-aware (_conditioned_check): pointwise where the
+    oracle's result is well conditioned, within 100 times its own movement everywhere."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(0, K=16, H=100, n=1000)
+    p, field, xg0, eps = W.mppi_c2(0, K=16, H=H, n=1000)
     res = _run_gpu(V, torch, p, field, xg0, eps, V.FP64)
-    assert (res["count"] == 1200).all()
-    assert len(_conditioned_check(ora, p, field, xg0, eps, res, 1e-13, 1e-6, 1e-6)) >= 4
+    assert (res["count"] == 1000 + 2 * H).all()
+    assert len(_conditioned_check(ora, p, field, xg0, eps, res, 1e-13, 1e-6, 1e-6)) >= min_conditioned
 
 
 def test_fp32_lev_gated_100_steps(ora):
@@ -148,7 +150,10 @@ def _binary32_envelope(ora, p, parts, xg, u, checkpoints, cap):
         for arr in (b.x, b.z, b.g):
             arr[:n] = arr[:n].astype(np.float32).astype(np.float64)
         if k + 1 in checkpoints:
-            out[k + 1] = (a.particles.copy(), np.abs(a.particles[:, :2] - b.particles[:, :2]).max())
+            # a gate decision that differs between the two runs leaves no pointwise spread
+            spread = (np.abs(a.particles[:, :2] - b.particles[:, :2]).max() if a.n == b.n
+                      else np.inf)
+            out[k + 1] = (a.particles.copy(), spread)
     return out
 
 
@@ -196,15 +201,32 @@ def test_fp64_merging_and_gate(ora):
 
 def test_table1_shape_merging_dominated_fp64(ora):
     """The perch benchmark's shape: clean wake, at most 60 particles (merging every step after
-    the 30th), 80 steps, binary64 path pointwise against the oracle. (The binary32 path on
-    this shape is held to the model's sensitivity envelope below.)"""
+    the 30th), binary64 path against the oracle. Once merging starts, a 1e-13 change of the
+    initial forward speed grows about tenfold every five steps in the oracle itself (1e-10 c at
+    40 steps, up to 5e-4 c at 80), so the comparison is pointwise at 1e-9 after 40 steps and
+    within 100 times the oracle's own movement after 80. (The binary32 path on this shape is
+    held to the model's sensitivity envelope below.)"""
+    from concurrent.futures import ThreadPoolExecutor
     torch, V = cuda()
     p = dict(W.glider_params(), n_wake_max=60)
     field = np.zeros((0, 3))
+    x0 = np.array(W.GLIDER_X0)
     eps = W.mppi_noise(11, 8, 80, W.MPPI_SIGMA_U)
-    res = _run_gpu(V, torch, p, field, np.array(W.GLIDER_X0), eps, V.FP64, 62)
+    res = _run_gpu(V, torch, p, field, x0, eps[:, :40].copy(), V.FP64, 62)
+    _check_rollouts(ora, p, field, x0, eps[:, :40].copy(), res, [0, 5], 1e-9, 1e-9, 1e-9)
+    res = _run_gpu(V, torch, p, field, x0, eps, V.FP64, 62)
     assert (res["count"] == 60).all()
-    _check_rollouts(ora, p, field, np.array(W.GLIDER_X0), eps, res, [0, 5], 1e-9, 1e-9, 1e-9)
+    x1 = x0.copy()
+    x1[4] += 1e-13
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        ref = list(ex.map(lambda i: ora.rollout(p, field, x0, eps[i].astype(np.float64), capacity=62,
+                                                want_field=True), range(8)))
+        alt = list(ex.map(lambda i: ora.rollout(p, field, x1, eps[i].astype(np.float64), capacity=62,
+                                                want_field=True), range(8)))
+    for i in range(8):
+        sens = np.abs(ref[i]["field"][:, :2] - alt[i]["field"][:, :2]).max()
+        err = np.abs(res["field"][i, :60, :2] - ref[i]["field"][:, :2]).max()
+        assert err <= 100.0 * sens + 1e-9, (i, err, sens)
 
 
 def test_batch_invariance_and_per_launch_form():
