@@ -17,6 +17,7 @@ constexpr int kThreads = 128;             // threads of a rollout block on the d
 constexpr int kMaxWarps = 16;             // largest rollout block: 512 threads
 constexpr double kInv2Pi = 0.15915494309189533577;
 
+// Device status bits of a rollout launch (latched in the state's status word).
 enum Status : int { kStOk = 0, kStNonFinite = 1, kStCapacity = 2 };
 
 // Everything a rollout kernel needs to know about the model, prepared on the host.

@@ -748,59 +748,69 @@ __device__ void fresh_velocities_f32(const DevParams &p, Work &w, const float4 *
     }
 }
 
-// Phase C completion and phase D for one particle at a time: the old targets add the bound
-// terms and the freshly shed vortices (from their pre-advection copies) to their old-old sums;
-// every particle is then advected by explicit Euler (double-length positions) and decayed
-// exactly, Gamma <- Gamma exp(-gamma dt) (Eq. 17). Each record is read and written by the
-// thread that owns it, so no barrier separates the velocity from the advection.
+// Phase C completion and phase D for one particle: an old target adds the bound terms and the
+// freshly shed vortices (from their pre-advection copies) to its old-old sum; every particle is
+// then advected by explicit Euler (double-length positions) and decayed exactly,
+// Gamma <- Gamma exp(-gamma dt) (Eq. 17). The record is read and written by the thread that
+// owns it, so no barrier separates the velocity from the advection. `bad` collects non-finite
+// velocities.
 template <int KER>
-__device__ void finalize_advect_f32(const DevParams &p, Work &w, float4 *part, const float2 *vel,
-                                    const float2 *scr, int cap32, int rows_off, int n, int n1,
-                                    double *probe_vel)
+__device__ __forceinline__ void finalize_one(const DevParams &p, const Work &w, float4 *part,
+                                             const float2 *vel, const float2 *scr, int cap32,
+                                             int rows_off, int n, int nf, int i, double *probe_vel,
+                                             bool &bad)
 {
     const float rc4 = (float)p.rc4, irc2 = (float)p.inv_rc2;
     const float inv2pi = (float)kInv2Pi;
     const float uix = (float)p.u_inf_x, uiz = (float)p.u_inf_z;
     const float dth = (float)p.dt, dtl = (float)(p.dt - (double)dth);
     const float dch = (float)p.decay, dcl = (float)(p.decay - (double)dch);
+    float4 q;
+    float2 v;
+    float xl, zl;
+    if (i < n) {
+        q = part[i];
+        const float2 raw = old_sum(vel, scr, cap32, rows_off, i);
+        unpack_lo(q.w, xl, zl);
+        float bu = 0.f, bw = 0.f;
+        bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
+        for (int f = 0; f < nf; ++f) {
+            const float4 s = w.fresh[f];
+            const float dx = q.x - s.x, dz = q.y - s.y;
+            const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
+            bu = fmaf(-dz, g, bu);
+            bw = fmaf(dx, g, bw);
+        }
+        v = make_float2(fmaf(raw.x + bu, inv2pi, uix), fmaf(raw.y + bw, inv2pi, uiz));
+    } else {
+        q = w.fresh[i - n];
+        v = w.fresh_vel[i - n];
+        unpack_lo(q.w, xl, zl);
+    }
+    if (probe_vel) { probe_vel[2 * i] = v.x; probe_vel[2 * i + 1] = v.y; }
+    bad |= !(isfinite(v.x) && isfinite(v.y));
+    const float ddx = fmaf(v.x, dth, fmaf(v.x, dtl, xl));
+    const float ddz = fmaf(v.y, dth, fmaf(v.y, dtl, zl));
+    float sx, ex, sz, ez;
+    two_sum(q.x, ddx, sx, ex);
+    two_sum(q.y, ddz, sz, ez);
+    q.x = sx;
+    q.y = sz;
+    q.z = fmaf(q.z, dcl, q.z * dch);
+    q.w = pack_lo(ex, ez);
+    part[i] = q;
+}
+
+// Phase C completion and phase D for every particle of the step, by the whole block.
+template <int KER>
+__device__ void finalize_advect_f32(const DevParams &p, Work &w, float4 *part, const float2 *vel,
+                                    const float2 *scr, int cap32, int rows_off, int n, int n1,
+                                    double *probe_vel)
+{
     const int nf = n1 - n;
     bool bad = false;
-    for (int i = threadIdx.x; i < n1; i += (int)blockDim.x) {
-        float4 q;
-        float2 v;
-        float xl, zl;
-        if (i < n) {
-            q = part[i];
-            const float2 raw = old_sum(vel, scr, cap32, rows_off, i);
-            unpack_lo(q.w, xl, zl);
-            float bu = 0.f, bw = 0.f;
-            bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
-            for (int f = 0; f < nf; ++f) {
-                const float4 s = w.fresh[f];
-                const float dx = q.x - s.x, dz = q.y - s.y;
-                const float g = s.z * PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4, irc2);
-                bu = fmaf(-dz, g, bu);
-                bw = fmaf(dx, g, bw);
-            }
-            v = make_float2(fmaf(raw.x + bu, inv2pi, uix), fmaf(raw.y + bw, inv2pi, uiz));
-        } else {
-            q = w.fresh[i - n];
-            v = w.fresh_vel[i - n];
-            unpack_lo(q.w, xl, zl);
-        }
-        if (probe_vel) { probe_vel[2 * i] = v.x; probe_vel[2 * i + 1] = v.y; }
-        bad |= !(isfinite(v.x) && isfinite(v.y));
-        const float ddx = fmaf(v.x, dth, fmaf(v.x, dtl, xl));
-        const float ddz = fmaf(v.y, dth, fmaf(v.y, dtl, zl));
-        float sx, ex, sz, ez;
-        two_sum(q.x, ddx, sx, ex);
-        two_sum(q.y, ddz, sz, ez);
-        q.x = sx;
-        q.y = sz;
-        q.z = fmaf(q.z, dcl, q.z * dch);
-        q.w = pack_lo(ex, ez);
-        part[i] = q;
-    }
+    for (int i = threadIdx.x; i < n1; i += (int)blockDim.x)
+        finalize_one<KER>(p, w, part, vel, scr, cap32, rows_off, n, nf, i, probe_vel, bad);
     if (bad) atomicOr(&w.flag, (int)kStNonFinite);
 }
 

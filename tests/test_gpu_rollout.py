@@ -261,6 +261,26 @@ def test_paced_launch_matches_unpaced_launches():
         assert torch.equal(part["final_glider"], full["final_glider"][b:b + 128])
 
 
+def test_two_wave_batch_matches_single_launches():
+    """A batch of 2048 rollouts runs in two waves of blocks (more than the 148 SMs x 7 blocks
+    resident at once). Each rollout's costs, final glider state, trajectory and field are the
+    same bits as in a launch of its own."""
+    torch, V = cuda()
+    p, field, xg0, eps = W.mppi_c2(5, K=2048, H=4, n=300)
+    st = V.State(p, field, xg0, 310)
+    c = torch.tensor(eps, device="cuda")
+    full = st.rollout_batch(c, want_traj=True, want_field=True)
+    for i in (0, 1, 700, 1035, 1036, 2047):
+        one = st.rollout_batch(c[i:i + 1].contiguous(), want_traj=True, want_field=True)
+        assert torch.equal(one["costs"][0], full["costs"][i]), i
+        assert torch.equal(one["final_glider"][0], full["final_glider"][i]), i
+        assert torch.equal(one["traj"][0], full["traj"][i]), i
+        n = int(one["count"][0])
+        assert n == int(full["count"][i]) == 308
+        assert torch.equal(one["field"][0, :n], full["field"][i, :n]), i
+    st.status()
+
+
 def test_rollout_batch_replays_from_a_cuda_graph():
     """A rollout batch captured into a CUDA graph (its pair-sum scratch and pacing table are
     allocated stream-ordered inside the capture) gives the eager launch's bits on replay."""
