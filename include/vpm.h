@@ -324,17 +324,19 @@ vpm_status mppi_perturb(const float *d_mu, const float *d_eps, int K, int H,
  * Free-field velocities (Eq. 3 with the chosen kernel, self term excluded) of n particles
  * d_particles[n*4] = (x, z, Gamma, unused) binary32; d_vel[n*2] receives (u, w). Binary32
  * pair sums, compensated across source tiles. One evaluation of each particle pair serves both
- * particles; the partial sums go through vpm_freefield_scratch_bytes(n) bytes of device scratch
- * (about n^2 / 256 bytes: 4.9 GB at n = 2^20) that the call allocates on `stream` from the
- * device's default memory pool and frees after it (stream-ordered). Errors: VPM_ERR_INVALID,
+ * particles; every particle's partial sums are added exactly into a 128-bit fixed-point
+ * accumulator per velocity component, so the result does not depend on the order in which the
+ * partial sums arrive. The call allocates vpm_freefield_scratch_bytes(n) bytes (32 n + 64) of
+ * device scratch on `stream` from the device's default memory pool and frees it after it
+ * (stream-ordered). Non-finite input gives NaN velocities. Errors: VPM_ERR_INVALID,
  * VPM_ERR_CUDA (including an allocation that does not fit).
  */
 vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel, double r_core,
                                   float *d_vel, cudaStream_t stream);
 
-/* Device bytes of pair-sum scratch one free-field velocity evaluation of n particles uses
- * (rows of 1024 particles: one slot per row and later particle, per row segment and target,
- * and two per particle). Errors: VPM_ERR_INVALID (n < 0, null). */
+/* Device bytes of scratch one free-field velocity evaluation of n particles uses: two 128-bit
+ * accumulators per particle and the call's scale (32 n + 64; 0 for n = 0). Errors:
+ * VPM_ERR_INVALID (n < 0, null). */
 vpm_status vpm_freefield_scratch_bytes(int n, size_t *bytes);
 
 /*
@@ -345,6 +347,17 @@ vpm_status vpm_freefield_scratch_bytes(int n, size_t *bytes);
  */
 vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, double r_core, double dt,
                               int steps, cudaStream_t stream);
+
+/*
+ * Host-only checks of the free-field accumulators (no device needed; the paper has no
+ * counterpart). vpm_fixed_sum converts h_v[count] to fixed point with unit 2^-e, adds them as
+ * 128-bit integers in the given order and returns the total as a double in *h_sum (*h_bad = 1 if a
+ * value was NaN or infinite). vpm_fixed_exponent gives the e the kernels use for n particles whose
+ * largest |Gamma| is gmax: with B = n gmax kappa (kappa = 1 / r_core for the regularised kernels,
+ * 2^40 for the singular one) and B < 2^eb, e = 125 - eb. Errors: VPM_ERR_INVALID.
+ */
+vpm_status vpm_fixed_sum(const float *h_v, int count, int e, double *h_sum, int *h_bad);
+vpm_status vpm_fixed_exponent(float gmax, int n, int kernel, double r_core, int *h_e);
 
 /* ------------------------------------------------------------------ uneven batches
  * Rollouts from many different roots at once: the MPPI step of §IV-A applied to R scenarios
@@ -472,8 +485,8 @@ vpm_status vpm_server_destroy(vpm_server *server);
  * The same Heun steps as vpm_freefield_heun for callers that must not let the library
  * allocate device memory, such as a control loop whose memory is fixed before it starts or a
  * host that gives all device memory to another owner. It evaluates every pair once per target
- * (vpm_freefield_heun evaluates each pair once for both particles, which needs n^2-sized
- * scratch), so the two agree to binary32 rounding, not bit for bit. The paper has no counterpart; it is a
+ * (vpm_freefield_heun evaluates each pair once for both particles and adds the partial sums into
+ * exact accumulators), so the two agree to binary32 rounding, not bit for bit. The paper has no counterpart; it is a
  * deployment variant. Its scratch is one device array of fixed size built into the library
  * (6 MiB, held on every device where it has been taken until the process exits), so n is
  * limited to 262144 particles; larger n returns VPM_ERR_CAPACITY without launching anything.

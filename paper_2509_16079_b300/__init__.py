@@ -104,6 +104,8 @@ _SIGNATURES = {
     "vpm_freefield_scratch_bytes": ([_I, C.POINTER(C.c_size_t)], _I),
     "vpm_freefield_heun": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
     "vpm_freefield_heun_noalloc": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
+    "vpm_fixed_sum": ([_VP, _I, _I, C.POINTER(_D), C.POINTER(_I)], _I),
+    "vpm_fixed_exponent": ([C.c_float, _I, _I, _D, C.POINTER(_I)], _I),
     "vpm_probe_rate": ([_I, _I, C.POINTER(_D)], _I),
     "vpm_batch_create": ([C.POINTER(Params), _I, _VP, _VP, _VP, _I, C.POINTER(_VP), _VP], _I),
     "vpm_batch_destroy": ([_VP], _I),

@@ -857,7 +857,7 @@ extern "C" vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, 
         return fail(VPM_ERR_INVALID, "bad kernel or core radius");
     if (n == 0 || steps == 0) return VPM_OK;
     keep_pool_memory();
-    // stage positions (16 n bytes), first-stage velocities (8 n bytes), then the pair sums
+    // stage positions (16 n bytes), first-stage velocities (8 n bytes), then the accumulators
     char *scratch = nullptr;
     CUDA_TRY(cudaMallocAsync((void **)&scratch, (size_t)n * 24 + freefield_sym_scratch_bytes(n), stream),
              "heun scratch");

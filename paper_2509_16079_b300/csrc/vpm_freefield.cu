@@ -8,6 +8,8 @@
 //
 // Once per pair (freefield_sym_kernel + freefield_combine_kernel, below): the form of
 // vpm_freefield_velocity and vpm_freefield_heun.
+#include <string.h>
+
 #include "vpm_device.cuh"
 
 namespace vpm {
@@ -26,6 +28,8 @@ struct FfArgs {
     const float4 *src;   // sources and targets (x, z, Gamma, unused)
     int n;
     float rc4, inv_rc2;
+    int kernel;          // vpm_kernel (the one-evaluation-per-pair form's scale)
+    float r_core;
     float dt;
     float2 *vel;         // velocity mode and stage 1: output; stage 2: v1 input
     float4 *mid;         // stage 1 output
@@ -150,14 +154,16 @@ cudaError_t launch_freefield_heun(float *p, int n, int kernel, double r_core, do
 // reverse terms to the sources' running sums, which then move one lane down. After a tile the
 // 8 warps' reverse sums of each source are added in warp order in shared memory.
 //   * off-diagonal units (row I, segment s): the row against kFsSeg tiles of later particles;
-//     the reverse sums go to the slot of (row I, source), the targets' compensated sums over
-//     the segment to the slot of (row I, segment, target);
+//     the targets' sums over the segment are Kahan-compensated across the tiles;
 //   * diagonal unit (row I): the row against itself. Warp w takes the 32-blocks of warps
 //     w' > w by rotation and its own 4 blocks once per target (both orders), and leaves the
-//     blocks of warps w' < w to them; the reverse sums go to the slot of the source.
-// A second kernel adds, per particle, its diagonal sums, its row's segment sums and the
-// reverse sums of every earlier row, in that order (Kahan), and applies the step's epilogue.
-// Every partial sum is formed in a fixed order, so results do not depend on scheduling.
+//     blocks of warps w' < w to them.
+// Every partial sum (a tile's reverse sums of a source, a unit's forward sums of a target) is
+// added into its particle's exact accumulator: two 128-bit two's-complement fixed-point
+// integers (u, w) per particle, 32 bytes. Integer addition is exact and associative, so each
+// particle's total is the exact sum of its binary32 partial sums whatever order the CTAs run
+// in, and the scratch grows like n, not like n^2. A second kernel turns each accumulator into
+// the velocity, applies the step's epilogue and clears the accumulator for the next evaluation.
 constexpr int kFsWarps = 8, kFsThreads = 32 * kFsWarps;
 constexpr int kFsRow = 128 * kFsWarps;      // targets of a row (4 per lane)
 constexpr int kFsTile = 512;                // sources per staged tile (16 blocks of 32)
@@ -168,7 +174,6 @@ constexpr int kFsSeg = 32;                  // tiles per off-diagonal unit (1638
 
 struct FsGeom {
     int n, rows, ntiles, max_seg;           // rows = ceil(n / kFsRow), ntiles = ceil(n / kFsTile)
-    long long f_seg, r_slot, total;         // float2 offsets: [diag fwd n][diag rev n][seg][rev]
 };
 
 __host__ __device__ inline FsGeom fs_geom(int n)
@@ -180,19 +185,92 @@ __host__ __device__ inline FsGeom fs_geom(int n)
     // row 0 has the most off-diagonal tiles: ntiles - 2 (the row spans two tiles)
     const int t0 = g.ntiles - kFsRow / kFsTile;
     g.max_seg = t0 > 0 ? (t0 + kFsSeg - 1) / kFsSeg : 0;
-    g.f_seg = 2LL * n;
-    g.r_slot = g.f_seg + (long long)g.rows * g.max_seg * kFsRow;
-    // reverse slots of row I: sources kFsRow (I + 1) .. ntiles kFsTile - 1
-    const long long span = (long long)g.ntiles * kFsTile;
-    const long long R = g.rows > 1 ? g.rows - 1 : 0;       // rows with later particles
-    g.total = g.r_slot + R * span - (long long)kFsRow * R * (R + 1) / 2;
     return g;
 }
 
-__host__ __device__ inline long long fs_rev_base(const FsGeom &g, int I)
+// ------------------------------------------------------------------ exact accumulation
+//
+// A particle's accumulator holds its velocity sums (u, w) in units of 2^-e as 128-bit
+// two's-complement integers: acc[4 j + 0, 1] are the low and high words of u, [2, 3] of w. The
+// exponent e is fixed for a call by a bound B on every partial sum and on every total: no term
+// of the sums exceeds max|Gamma| kappa, with kappa = 1 / r_core for the regularised kernels
+// (|r q(r)| peaks at 1 / (sqrt(2) r_core) for Eq. 5 and at 0.64 / r_core for the Gaussian core)
+// and 2^40 for the singular kernel (distances down to 2^-40), so |sum| <= B = n max|Gamma| kappa.
+// With B < 2^eb, e = 125 - eb keeps every value below 2^126 and the resolution at B 2^-125.
+struct FsScale {
+    int gmax_bits;                          // max |Gamma| of the call (binary32 bits, >= 0)
+    int nonfinite;                          // set when a partial sum is NaN or infinite
+    int pad[14];
+};
+
+__host__ __device__ inline int fs_exponent(float gmax, int n, int kernel, float r_core)
 {
-    const long long span = (long long)g.ntiles * kFsTile;
-    return g.r_slot + (long long)I * span - (long long)kFsRow * I * (I + 1) / 2 - (long long)kFsRow * (I + 1);
+    if (!(gmax > 0.f) || n <= 0) return 0;
+    const double kappa = kernel == VPM_KERNEL_SINGULAR ? 1099511627776.0 : 1.0 / (double)r_core;
+    const double B = (double)n * (double)gmax * kappa;
+    if (!(B < 1e300)) return 0;
+    int eb = 0;
+    frexp(B, &eb);                          // B < 2^eb
+    return 125 - eb;
+}
+
+// v 2^e as a 128-bit two's-complement integer (lo, hi), rounded to nearest (half away from
+// zero) below the unit; bad is set for NaN and infinities. Zero and subnormal v give 0.
+__host__ __device__ inline void fs_to_fixed(float v, int e, unsigned long long &lo,
+                                            unsigned long long &hi, bool &bad)
+{
+    unsigned b;
+    memcpy(&b, &v, sizeof b);
+    const int ex = (int)((b >> 23) & 0xffu);
+    lo = hi = 0ull;
+    if (ex == 0xff) { bad = true; return; }
+    if (ex == 0) return;
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);   // v = m 2^(ex-150)
+    const int sh = ex - 150 + e;
+    if (sh >= 64) {
+        hi = m << (sh - 64);
+    } else if (sh > 40) {
+        lo = m << sh;
+        hi = m >> (64 - sh);
+    } else if (sh >= 0) {
+        lo = m << sh;
+    } else if (sh > -25) {
+        lo = (m + (1ull << (-sh - 1))) >> (-sh);
+    }
+    if (b >> 31) {                          // negate: two's complement over 128 bits
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+}
+
+// The accumulator (lo, hi) as a double (one rounding), in units of 1.
+__host__ __device__ inline double fs_from_fixed(unsigned long long lo, unsigned long long hi, int e)
+{
+    const bool neg = (long long)hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const double d = ldexp((double)hi, 64) + (double)lo;
+    return ldexp(neg ? -d : d, -e);
+}
+
+// Adds v (units of 1) to the 128-bit accumulator at a: the low words' carry goes to the high
+// word, so concurrent additions in any order leave the exact sum.
+__device__ __forceinline__ void fs_acc_add(unsigned long long *a, float v, int e, int *nonfinite)
+{
+    unsigned long long lo, hi;
+    bool bad = false;
+    fs_to_fixed(v, e, lo, hi, bad);
+    if (bad) {
+        atomicOr(nonfinite, 1);
+        return;
+    }
+    if (lo) {
+        const unsigned long long old = atomicAdd(a, lo);
+        if (old + lo < old) hi += 1ull;
+    }
+    if (hi) atomicAdd(a + 1, hi);
 }
 
 // Stages sources t0 .. t0 + kFsTile - 1 (past n: the last particle's position, zero strength).
@@ -309,11 +387,14 @@ __device__ __forceinline__ void fs_fold(float (&su)[4], float (&cu)[4], float (&
 // grid (1 + max_seg, rows): x = 0 the diagonal unit of row y, x = s + 1 its segment s.
 template <int KER>
 __global__ void __launch_bounds__(kFsThreads, VPM_FS_MIN_BLOCKS)
-freefield_sym_kernel(const float4 *src, int n, float rc4, float irc2, float2 *scr)
+freefield_sym_kernel(const float4 *src, int n, float rc4, float irc2, unsigned long long *acc,
+                     FsScale *scale, int kernel, float r_core)
 {
     __shared__ float4 tile[kFsTile];
     __shared__ float2 stage[kFsWarps][kFsTile];
+    __shared__ int s_e;
     const FsGeom g = fs_geom(n);
+    if (threadIdx.x == 0) s_e = fs_exponent(__int_as_float(scale->gmax_bits), n, kernel, r_core);
     const int I = blockIdx.y, unit = blockIdx.x;
     const int tr0 = I * (kFsRow / kFsTile);                 // the row's first tile
     int t_begin, t_end;
@@ -373,62 +454,34 @@ freefield_sym_kernel(const float4 *src, int n, float rc4, float irc2, float2 *sc
                 ru += stage[w][q].x;
                 rw += stage[w][q].y;
             }
-            if (unit == 0) scr[(long long)n + j] = make_float2(ru, rw);
-            else scr[fs_rev_base(g, I) + j] = make_float2(ru, rw);
+            fs_acc_add(acc + 4 * (size_t)j, ru, s_e, &scale->nonfinite);
+            fs_acc_add(acc + 4 * (size_t)j + 2, rw, s_e, &scale->nonfinite);
         }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int li = 128 * warp + 32 * k + lane, i = I * kFsRow + li;
+        const int i = I * kFsRow + 128 * warp + 32 * k + lane;
         if (i >= n) continue;
-        const float2 f = make_float2(su[k] - cu[k], sw[k] - cw[k]);
-        if (unit == 0) scr[i] = f;
-        else scr[g.f_seg + ((long long)I * g.max_seg + (unit - 1)) * kFsRow + li] = f;
+        fs_acc_add(acc + 4 * (size_t)i, su[k] - cu[k], s_e, &scale->nonfinite);
+        fs_acc_add(acc + 4 * (size_t)i + 2, sw[k] - cw[k], s_e, &scale->nonfinite);
     }
 }
 
-// Per particle: every partial sum in a fixed order, then the evaluation's epilogue.
+// Per particle: the exact sums as velocities, the evaluation's epilogue, and the accumulator
+// cleared for the next evaluation of the call.
 template <int MODE>
-__global__ void __launch_bounds__(256) freefield_combine_kernel(const FfArgs a, const float2 *scr)
+__global__ void __launch_bounds__(256) freefield_combine_kernel(const FfArgs a, unsigned long long *acc,
+                                                                 const FsScale *scale)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = a.n;
     if (j >= n) return;
-    const FsGeom g = fs_geom(n);
-    const int T = j / kFsRow, li = j - T * kFsRow;
-    float2 v = scr[j];
-    float cu = 0.f, cw = 0.f;
-    {
-        const float2 d = scr[(long long)n + j];
-        kahan_add(v.x, cu, d.x);
-        kahan_add(v.y, cw, d.y);
-    }
-    // the row's segments: those that exist (tiles after the row's own two)
-    const int t_after = g.ntiles - (T + 1) * (kFsRow / kFsTile);
-    const int segs = t_after > 0 ? (t_after + kFsSeg - 1) / kFsSeg : 0;
-    for (int s = 0; s < segs; ++s) {
-        const float2 f = scr[g.f_seg + ((long long)T * g.max_seg + s) * kFsRow + li];
-        kahan_add(v.x, cu, f.x);
-        kahan_add(v.y, cw, f.y);
-    }
-    int I = 0;
-    for (; I + 4 <= T; I += 4) {                           // four loads in flight
-        float2 r[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) r[q] = scr[fs_rev_base(g, I + q) + j];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            kahan_add(v.x, cu, r[q].x);
-            kahan_add(v.y, cw, r[q].y);
-        }
-    }
-    for (; I < T; ++I) {
-        const float2 r = scr[fs_rev_base(g, I) + j];
-        kahan_add(v.x, cu, r.x);
-        kahan_add(v.y, cw, r.y);
-    }
-    const float inv2pi = (float)kInv2Pi;
-    const float vu = (v.x - cu) * inv2pi, vw = (v.y - cw) * inv2pi;
+    const int e = fs_exponent(__int_as_float(scale->gmax_bits), n, a.kernel, a.r_core);
+    unsigned long long *q = acc + 4 * (size_t)j;
+    const double su = fs_from_fixed(q[0], q[1], e), sw = fs_from_fixed(q[2], q[3], e);
+    q[0] = q[1] = q[2] = q[3] = 0ull;
+    float vu = (float)(su * kInv2Pi), vw = (float)(sw * kInv2Pi);
+    if (scale->nonfinite) vu = vw = __int_as_float(0x7fc00000);
     if (MODE == kFfVelocity) {
         a.vel[j] = make_float2(vu, vw);
     } else if (MODE == kFfHeunStage1) {
@@ -438,33 +491,57 @@ __global__ void __launch_bounds__(256) freefield_combine_kernel(const FfArgs a, 
     } else {
         const float h = 0.5f * a.dt;
         const float2 v1 = a.vel[j];
-        float4 q = a.out[j];
-        q.x = fmaf(h, v1.x + vu, q.x);
-        q.y = fmaf(h, v1.y + vw, q.y);
-        a.out[j] = q;
+        float4 p = a.out[j];
+        p.x = fmaf(h, v1.x + vu, p.x);
+        p.y = fmaf(h, v1.y + vw, p.y);
+        a.out[j] = p;
     }
 }
 
+// max |Gamma| of the field (binary32 bits of non-negative floats order like the integers).
+__global__ void __launch_bounds__(256) freefield_gmax_kernel(const float4 *src, int n, FsScale *scale)
+{
+    int m = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        m = max(m, __float_as_int(fabsf(src[j].z)));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&scale->gmax_bits, m);
+}
+
+// Scratch of one call: the accumulators (32 bytes per particle), then the call's scale.
 size_t freefield_sym_scratch_bytes(int n)
 {
-    return n > 0 ? sizeof(float2) * (size_t)fs_geom(n).total : 0;
+    return n > 0 ? 32 * (size_t)n + sizeof(FsScale) : 0;
+}
+
+// Zeroes the call's scratch and finds max |Gamma| (the strengths do not change during a call).
+static cudaError_t sym_begin(const float4 *src, int n, void *scratch, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(scratch, 0, freefield_sym_scratch_bytes(n), s);
+    if (e != cudaSuccess) return e;
+    FsScale *scale = reinterpret_cast<FsScale *>(static_cast<unsigned char *>(scratch) + 32 * (size_t)n);
+    const int grid = min((n + 255) / 256, 1184);
+    freefield_gmax_kernel<<<grid, 256, 0, s>>>(src, n, scale);
+    return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t sym_eval(int kernel, const FfArgs &a, float2 *scr, cudaStream_t s)
+static cudaError_t sym_eval(int kernel, const FfArgs &a, void *scratch, cudaStream_t s)
 {
     const FsGeom g = fs_geom(a.n);
     if (a.n == 0) return cudaSuccess;
+    unsigned long long *acc = static_cast<unsigned long long *>(scratch);
+    FsScale *scale = reinterpret_cast<FsScale *>(static_cast<unsigned char *>(scratch) + 32 * (size_t)a.n);
     const dim3 grid(1 + g.max_seg, g.rows);
     if (kernel == VPM_KERNEL_GAUSSIAN)
-        freefield_sym_kernel<VPM_KERNEL_GAUSSIAN><<<grid, kFsThreads, 0, s>>>(a.src, a.n, a.rc4, a.inv_rc2, scr);
+        freefield_sym_kernel<VPM_KERNEL_GAUSSIAN><<<grid, kFsThreads, 0, s>>>(a.src, a.n, a.rc4, a.inv_rc2, acc, scale, kernel, a.r_core);
     else if (kernel == VPM_KERNEL_SINGULAR)
-        freefield_sym_kernel<VPM_KERNEL_SINGULAR><<<grid, kFsThreads, 0, s>>>(a.src, a.n, a.rc4, a.inv_rc2, scr);
+        freefield_sym_kernel<VPM_KERNEL_SINGULAR><<<grid, kFsThreads, 0, s>>>(a.src, a.n, a.rc4, a.inv_rc2, acc, scale, kernel, a.r_core);
     else
-        freefield_sym_kernel<VPM_KERNEL_VATISTAS><<<grid, kFsThreads, 0, s>>>(a.src, a.n, a.rc4, a.inv_rc2, scr);
+        freefield_sym_kernel<VPM_KERNEL_VATISTAS><<<grid, kFsThreads, 0, s>>>(a.src, a.n, a.rc4, a.inv_rc2, acc, scale, kernel, a.r_core);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    freefield_combine_kernel<MODE><<<(a.n + 255) / 256, 256, 0, s>>>(a, scr);
+    freefield_combine_kernel<MODE><<<(a.n + 255) / 256, 256, 0, s>>>(a, acc, scale);
     return cudaGetLastError();
 }
 
@@ -477,12 +554,17 @@ cudaError_t launch_freefield_sym_velocity(const float *p, int n, int kernel, dou
     a.n = n;
     a.rc4 = (float)(r_core * r_core * r_core * r_core);
     a.inv_rc2 = r_core > 0 ? (float)(1.0 / (r_core * r_core)) : 0.f;
+    a.kernel = kernel;
+    a.r_core = (float)r_core;
     a.vel = reinterpret_cast<float2 *>(vel);
-    return sym_eval<kFfVelocity>(kernel, a, static_cast<float2 *>(scratch), s);
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = sym_begin(a.src, n, scratch, s);
+    if (e != cudaSuccess) return e;
+    return sym_eval<kFfVelocity>(kernel, a, scratch, s);
 }
 
 // Heun steps with one evaluation per pair; scratch_mid[n] float4, scratch_v1[n] float2 and
-// the pair-sum scratch of freefield_sym_scratch_bytes(n).
+// the accumulators of freefield_sym_scratch_bytes(n).
 cudaError_t launch_freefield_sym_heun(float *p, int n, int kernel, double r_core, double dt,
                                       int steps, float *scratch_mid, float *scratch_v1,
                                       void *scratch, cudaStream_t s)
@@ -491,20 +573,53 @@ cudaError_t launch_freefield_sym_heun(float *p, int n, int kernel, double r_core
     a.n = n;
     a.rc4 = (float)(r_core * r_core * r_core * r_core);
     a.inv_rc2 = r_core > 0 ? (float)(1.0 / (r_core * r_core)) : 0.f;
+    a.kernel = kernel;
+    a.r_core = (float)r_core;
     a.dt = (float)dt;
     a.vel = reinterpret_cast<float2 *>(scratch_v1);
     a.mid = reinterpret_cast<float4 *>(scratch_mid);
     a.out = reinterpret_cast<float4 *>(p);
-    float2 *scr = static_cast<float2 *>(scratch);
+    if (n == 0 || steps == 0) return cudaSuccess;
+    cudaError_t e = sym_begin(reinterpret_cast<const float4 *>(p), n, scratch, s);
+    if (e != cudaSuccess) return e;
     for (int k = 0; k < steps; ++k) {
         a.src = reinterpret_cast<const float4 *>(p);
-        cudaError_t e = sym_eval<kFfHeunStage1>(kernel, a, scr, s);
+        e = sym_eval<kFfHeunStage1>(kernel, a, scratch, s);
         if (e != cudaSuccess) return e;
         a.src = a.mid;
-        e = sym_eval<kFfHeunStage2>(kernel, a, scr, s);
+        e = sym_eval<kFfHeunStage2>(kernel, a, scratch, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 }  // namespace vpm
+
+// Host-side check of the exact accumulation (no device needed): the values h_v[count] converted
+// with exponent e and added as 128-bit integers in the given order, returned as a double.
+extern "C" vpm_status vpm_fixed_sum(const float *h_v, int count, int e, double *h_sum, int *h_bad)
+{
+    if ((!h_v && count > 0) || count < 0 || !h_sum || !h_bad) return VPM_ERR_INVALID;
+    unsigned long long lo = 0ull, hi = 0ull;
+    int bad = 0;
+    for (int i = 0; i < count; ++i) {
+        unsigned long long l, h;
+        bool b = false;
+        vpm::fs_to_fixed(h_v[i], e, l, h, b);
+        if (b) { bad = 1; continue; }
+        const unsigned long long old = lo;
+        lo += l;
+        hi += h + (lo < old ? 1ull : 0ull);
+    }
+    *h_sum = vpm::fs_from_fixed(lo, hi, e);
+    *h_bad = bad;
+    return VPM_OK;
+}
+
+// The exponent the free-field kernels use for n particles of largest |Gamma| gmax.
+extern "C" vpm_status vpm_fixed_exponent(float gmax, int n, int kernel, double r_core, int *h_e)
+{
+    if (!h_e || n < 0) return VPM_ERR_INVALID;
+    *h_e = vpm::fs_exponent(gmax, n, kernel, (float)r_core);
+    return VPM_OK;
+}

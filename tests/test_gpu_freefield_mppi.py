@@ -31,10 +31,11 @@ def test_freefield_velocity(ora, kernel, n):
         assert normwise(v, ref) <= VEL_TOL
 
 
-def test_freefield_large_sampled(ora):
-    """2^20 blob-field particles (core 1e-3): 256 sampled targets against all sources."""
+@pytest.mark.parametrize("n", [1 << 20, 1 << 22])
+def test_freefield_large_sampled(ora, n):
+    """2^20 and 2^22 blob-field particles (core 1e-3): 256 sampled targets against all sources.
+    The scratch is 32 bytes per particle (134 MB at 2^22)."""
     torch, V = cuda()
-    n = 1 << 20
     P = W.blob_field(0, n, gamma_std=1e-3)
     d = _dev_particles(torch, P)
     v = V.freefield_velocity(d, 1, 1e-3).cpu().numpy()
@@ -42,6 +43,16 @@ def test_freefield_large_sampled(ora):
     idx = W.sample_indices(1, n, 256)
     ref = ora.velocity_at(Pf, Pf[idx, :2], 1, 1e-3, skip=idx)
     assert normwise(v[idx], ref) <= VEL_TOL
+
+
+def test_freefield_velocity_is_deterministic():
+    """The CTAs add their partial sums into the exact accumulators in whatever order they run;
+    integer addition makes the result the same bits every time."""
+    torch, V = cuda()
+    d = _dev_particles(torch, W.blob_field(2, 300000, gamma_std=1e-3))
+    a = V.freefield_velocity(d, 1, 1e-3)
+    for _ in range(3):
+        assert torch.equal(V.freefield_velocity(d, 1, 1e-3), a)
 
 
 def test_freefield_heun(ora):
