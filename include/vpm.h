@@ -219,10 +219,9 @@ vpm_status vpm_rollout_scratch_bytes_cap(int precision, int capacity, int K, siz
  *   d_field[K*capacity*3]    final wake (x, z, Gamma) per rollout (binary64), or null
  *   d_count[K]               final particle count per rollout, or null
  * Binary32 roots whose field can grow past 128 particles need device scratch for the pair
- * sums (vpm_rollout_scratch_bytes); it is allocated on `stream` from the device's default
- * memory pool for the launch and freed after it (stream-ordered). The first such allocation
- * sets that pool's release threshold to its maximum, so freed memory stays cached in the pool
- * for later calls (this affects every user of the default pool in the process).
+ * sums (vpm_rollout_scratch_bytes); it is allocated on `stream` from the library's own memory
+ * pool for the launch and freed after it (stream-ordered; see vpm_pool_trim). The device's
+ * default pool is not touched.
  * Errors: VPM_ERR_INVALID (K, H < 1, null controls/costs), VPM_ERR_CAPACITY (the count could
  * exceed the capacity within H steps), VPM_ERR_CUDA.
  */
@@ -327,7 +326,7 @@ vpm_status mppi_perturb(const float *d_mu, const float *d_eps, int K, int H,
  * particles; every particle's partial sums are added exactly into a 128-bit fixed-point
  * accumulator per velocity component, so the result does not depend on the order in which the
  * partial sums arrive. The call allocates vpm_freefield_scratch_bytes(n) bytes (32 n + 64) of
- * device scratch on `stream` from the device's default memory pool and frees it after it
+ * device scratch on `stream` from the library's memory pool and frees it after it
  * (stream-ordered). Non-finite input gives NaN velocities. Errors: VPM_ERR_INVALID,
  * VPM_ERR_CUDA (including an allocation that does not fit).
  */
@@ -347,6 +346,16 @@ vpm_status vpm_freefield_scratch_bytes(int n, size_t *bytes);
  */
 vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, double r_core, double dt,
                               int steps, cudaStream_t stream);
+
+/*
+ * The library's stream-ordered scratch (rollout pair sums, pacing tables, free-field
+ * accumulators, serving buffers) comes from a memory pool of its own on each device, separate
+ * from the device's default pool, which it leaves untouched. Freed scratch stays reserved in
+ * that pool for the library's next launches. vpm_pool_trim gives the current device's reserved,
+ * unused pool memory back to the device (memory still in use is not affected) and writes the
+ * bytes the pool still holds to *bytes_held if non-null. Errors: VPM_ERR_CUDA.
+ */
+vpm_status vpm_pool_trim(size_t *bytes_held);
 
 /*
  * Host-only checks of the free-field accumulators (no device needed; the paper has no
@@ -422,7 +431,11 @@ typedef struct vpm_server vpm_server;
 
 typedef struct {
     int max_inflight;     /* requests on the device at once; 1 gives the plain per-request form */
-    size_t hbm_budget;    /* device bytes of request buffers in flight; 0: 80 % of free memory   */
+    size_t hbm_budget;    /* cap on the device bytes of requests in flight; 0: no cap. Either
+                             way a request is admitted only while the device has its bytes free
+                             at that moment (cudaMemGetInfo plus the library pool's idle memory,
+                             less a reserve of max(1 GiB, 2 % of device memory)), so memory other
+                             code takes after the server was made delays admission              */
     int max_rollouts;     /* largest K accepted                                                 */
     int max_horizon;      /* largest H accepted                                                 */
     int max_inflight_rollouts;  /* rollouts on the device at once; a request is admitted while the

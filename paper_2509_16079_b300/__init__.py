@@ -105,6 +105,7 @@ _SIGNATURES = {
     "vpm_freefield_heun": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
     "vpm_freefield_heun_noalloc": ([_VP, _I, _I, _D, _D, _I, _VP], _I),
     "vpm_fixed_sum": ([_VP, _I, _I, C.POINTER(_D), C.POINTER(_I)], _I),
+    "vpm_pool_trim": ([C.POINTER(C.c_size_t)], _I),
     "vpm_fixed_exponent": ([C.c_float, _I, _I, _D, C.POINTER(_I)], _I),
     "vpm_probe_rate": ([_I, _I, C.POINTER(_D)], _I),
     "vpm_batch_create": ([C.POINTER(Params), _I, _VP, _VP, _VP, _I, C.POINTER(_VP), _VP], _I),
@@ -341,6 +342,14 @@ class State:
         check(lib().vpm_rollout_batch_per_launch(self._h, K, H, ptr(controls), ptr(costs),
                                                  ptr(fin), stream_handle(stream)))
         return dict(costs=costs, final_glider=fin)
+
+
+def pool_trim() -> int:
+    """Gives the library pool's reserved, unused device memory back to the device
+    (vpm_pool_trim); returns the bytes the pool still holds."""
+    b = C.c_size_t()
+    check(lib().vpm_pool_trim(C.byref(b)))
+    return b.value
 
 
 class ServerConfig(C.Structure):

@@ -747,15 +747,15 @@ extern "C" vpm_status vpm_rollout_batch_per_launch(const vpm_state *s, int K, in
     void *parts = nullptr;
     int *ns = nullptr;
     double *gl = nullptr, *hi = nullptr;
-    CUDA_TRY(cudaMallocAsync(&parts, rec * (size_t)cap * K, stream), "per-launch scratch");
-    CUDA_TRY(cudaMallocAsync((void **)&ns, sizeof(int) * 2 * K, stream), "per-launch scratch");
-    CUDA_TRY(cudaMallocAsync((void **)&gl, sizeof(double) * stride * K, stream), "per-launch scratch");
-    CUDA_TRY(cudaMallocAsync((void **)&hi, sizeof(double) * stride * K, stream), "per-launch scratch");
+    CUDA_TRY(lib_malloc_async(&parts, rec * (size_t)cap * K, stream), "per-launch scratch");
+    CUDA_TRY(lib_malloc_async((void **)&ns, sizeof(int) * 2 * K, stream), "per-launch scratch");
+    CUDA_TRY(lib_malloc_async((void **)&gl, sizeof(double) * stride * K, stream), "per-launch scratch");
+    CUDA_TRY(lib_malloc_async((void **)&hi, sizeof(double) * stride * K, stream), "per-launch scratch");
     // pair-sum scratch of the one block every launch runs, allocated once for all launches
     const long long rev_slots = rollout_rev_slots(s->params.precision, cap);
     float2 *rev = nullptr;
     if (rev_slots > 0)
-        CUDA_TRY(cudaMallocAsync((void **)&rev, sizeof(float2) * (size_t)rev_slots, stream), "per-launch scratch");
+        CUDA_TRY(lib_malloc_async((void **)&rev, sizeof(float2) * (size_t)rev_slots, stream), "per-launch scratch");
     // replicate the root into every rollout's slot (a zero-step launch of the rollout kernel)
     RolloutArgs a;
     base_args(s, a);
@@ -831,6 +831,19 @@ extern "C" vpm_status vpm_freefield_scratch_bytes(int n, size_t *bytes)
     return VPM_OK;
 }
 
+extern "C" vpm_status vpm_pool_trim(size_t *bytes_held)
+{
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return fail(VPM_ERR_CUDA, "vpm_pool_trim: no library pool on the current device");
+    CUDA_TRY(cudaMemPoolTrimTo(pool, 0), "vpm_pool_trim");
+    if (bytes_held) {
+        unsigned long long held = 0;
+        CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &held), "vpm_pool_trim");
+        *bytes_held = (size_t)held;
+    }
+    return VPM_OK;
+}
+
 extern "C" vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel,
                                              double r_core, float *d_vel, cudaStream_t stream)
 {
@@ -838,9 +851,8 @@ extern "C" vpm_status vpm_freefield_velocity(const float *d_particles, int n, in
     if (kernel < 0 || kernel > 2 || (kernel != VPM_KERNEL_SINGULAR && !(r_core > 0)))
         return fail(VPM_ERR_INVALID, "bad kernel or core radius");
     if (n == 0) return VPM_OK;
-    keep_pool_memory();
     void *scratch = nullptr;
-    CUDA_TRY(cudaMallocAsync(&scratch, freefield_sym_scratch_bytes(n), stream), "freefield scratch");
+    CUDA_TRY(lib_malloc_async(&scratch, freefield_sym_scratch_bytes(n), stream), "freefield scratch");
     cudaError_t e = launch_freefield_sym_velocity(d_particles, n, kernel, r_core, d_vel, scratch, stream);
     cudaError_t e2 = cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_fail(e, "freefield velocity");
@@ -856,10 +868,9 @@ extern "C" vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, 
     if (kernel < 0 || kernel > 2 || (kernel != VPM_KERNEL_SINGULAR && !(r_core > 0)))
         return fail(VPM_ERR_INVALID, "bad kernel or core radius");
     if (n == 0 || steps == 0) return VPM_OK;
-    keep_pool_memory();
     // stage positions (16 n bytes), first-stage velocities (8 n bytes), then the accumulators
     char *scratch = nullptr;
-    CUDA_TRY(cudaMallocAsync((void **)&scratch, (size_t)n * 24 + freefield_sym_scratch_bytes(n), stream),
+    CUDA_TRY(lib_malloc_async((void **)&scratch, (size_t)n * 24 + freefield_sym_scratch_bytes(n), stream),
              "heun scratch");
     cudaError_t e = launch_freefield_sym_heun(d_particles, n, kernel, r_core, dt, steps,
                                               reinterpret_cast<float *>(scratch),

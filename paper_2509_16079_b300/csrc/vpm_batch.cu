@@ -335,7 +335,7 @@ extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_control
     if (b->params.precision == VPM_FP64) return VPM_OK;
     const int Ht = std::min(H, 3);
     float *costs = nullptr;
-    BTRY(cudaMallocAsync((void **)&costs, sizeof(float) * b->R, stream), "tune scratch");
+    BTRY(lib_malloc_async((void **)&costs, sizeof(float) * b->R, stream), "tune scratch");
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);

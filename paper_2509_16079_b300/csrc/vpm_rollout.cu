@@ -1309,7 +1309,7 @@ static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStr
             per_sm > 1 && grid > sms && grid <= per_sm * sms) {
             const int ids = kPaceSms;
             const size_t bytes = sizeof(unsigned) * ids + sizeof(int) * ids * kPaceSlots;
-            if (cudaMallocAsync(&pace, bytes, s) == cudaSuccess) {
+            if (lib_malloc_async(&pace, bytes, s) == cudaSuccess) {
                 cudaError_t e = cudaMemsetAsync(pace, 0, bytes, s);
                 if (e != cudaSuccess) {
                     cudaFreeAsync(pace, s);
@@ -1348,20 +1348,59 @@ long long rollout_rev_slots(int precision, int cap)
     return precision == VPM_FP64 ? 0 : rev_slots(cap);
 }
 
-// Stream-ordered allocations of the pair-sum scratch come from the device's default pool,
-// which keeps freed memory for the next launch instead of returning it at every synchronise.
-void keep_pool_memory()
+// The library's own memory pool, one per device, for the stream-ordered scratch of its launches.
+// Its release threshold is at its maximum, so scratch freed by one launch stays reserved for
+// the next instead of going back to the device at every synchronisation; the device's default
+// pool, which other code in the process uses, keeps its own settings.
+static constexpr int kPoolDevices = 64;
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pools[kPoolDevices];
+
+cudaMemPool_t lib_pool()
 {
-    static std::once_flag once;
-    std::call_once(once, [] {
-        int dev = 0;
-        cudaMemPool_t pool;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            unsigned long long keep = ~0ull;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kPoolDevices) {
         cudaGetLastError();
-    });
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaGetLastError();
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s)
+{
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+size_t lib_pool_idle_bytes()
+{
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return 0;
+    unsigned long long reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return reserved > used ? (size_t)(reserved - used) : 0;
 }
 
 // Runs launch(args) with the binary32 pair-sum scratch in place: the caller's, or one
@@ -1372,10 +1411,9 @@ static cudaError_t with_rev_scratch(const RolloutArgs &a, int grid, cudaStream_t
 {
     const long long slots = rev_slots(a.cap);
     if (slots == 0 || a.rev || a.H == 0) return launch(a);
-    keep_pool_memory();
     RolloutArgs b = a;
     void *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, sizeof(float2) * (size_t)slots * (size_t)grid, s);
+    cudaError_t e = lib_malloc_async(&buf, sizeof(float2) * (size_t)slots * (size_t)grid, s);
     if (e != cudaSuccess) return e;
     b.rev = static_cast<float2 *>(buf);
     b.rev_stride = slots;

@@ -65,9 +65,12 @@ cudaError_t launch_inject_pair(int precision, void *d_part, int *d_n, int cap, c
                                cudaStream_t s);
 
 size_t rollout_smem_bytes(int precision, int cap);
-// Makes the device's default memory pool keep freed memory for later stream-ordered
-// allocations (the library's scratch) instead of releasing it at every synchronisation.
-void keep_pool_memory();
+// The library's memory pool on the current device (null if it cannot be made) and a
+// stream-ordered allocation from it; freed with cudaFreeAsync. Freed memory stays reserved in the
+// pool for the library's next allocations; lib_pool_idle_bytes() is that reserved, unused part.
+cudaMemPool_t lib_pool();
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+size_t lib_pool_idle_bytes();
 // float2 slots of pair-sum scratch one block of the binary32 path needs for capacity cap
 // (0: none; the binary64 path needs none).
 long long rollout_rev_slots(int precision, int cap);

@@ -5,7 +5,9 @@
 // scenario's resident field, optionally after advancing that field by a few committed steps
 // (the tracking instance of §IV-C). A worker thread owns all device work: it completes finished
 // requests, then admits queued ones in arrival order while a slot is free, the scenario has no
-// request on the device, the request's device buffers fit the memory budget, and its rollouts
+// request on the device, the request's device memory (its buffers and its rollouts' pair-sum
+// scratch) fits both the configured budget and the memory the device has free at that moment
+// (read at each admission, less a reserve of max(1 GiB, 2 % of the device)), and its rollouts
 // fit the rollout budget (beyond the rollout blocks the device holds at once, more concurrency
 // adds latency without throughput). Each admitted
 // request runs on its own stream, so requests that arrive while others are on the GPU overlap
@@ -30,6 +32,8 @@
 namespace vpm {
 vpm_status report_error(vpm_status st, const char *msg);
 size_t rollout_scratch_bytes(const vpm_state *s, int K, int H, int advance);
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+size_t lib_pool_idle_bytes();
 }
 
 static vpm_status sfail(vpm_status st, const char *fmt, ...)
@@ -78,7 +82,8 @@ struct Slot {
 struct vpm_server {
     vpm_server_config cfg;
     int device = 0;
-    size_t budget = 0, in_flight_bytes = 0;
+    size_t budget = 0, in_flight_bytes = 0;   // budget: the configured cap (SIZE_MAX: none)
+    size_t reserve = 0, total_mem = 0;       // device memory admission leaves free, and the total
     long long rollout_budget = 0, in_flight_rollouts = 0;
     Clock::time_point t0;
     std::vector<vpm_state *> scenarios;
@@ -113,8 +118,8 @@ static vpm_status start_request(vpm_server *s, Slot &sl, const Request &r)
     float *pin = sl.pinned;
     memcpy(pin, r.eps.data(), sizeof(float) * (size_t)K * H);
     memcpy(pin + (size_t)K * H, r.mu.data(), sizeof(float) * H);
-    cudaError_t e = cudaMallocAsync((void **)&sl.d_buf, r.buf_bytes, sl.stream);
-    if (e) { cudaGetLastError(); return sfail(VPM_ERR_OOM, "server: cudaMallocAsync: %s", cudaGetErrorString(e)); }
+    cudaError_t e = vpm::lib_malloc_async((void **)&sl.d_buf, r.buf_bytes, sl.stream);
+    if (e) { cudaGetLastError(); return sfail(VPM_ERR_OOM, "server: allocation: %s", cudaGetErrorString(e)); }
     float *d_eps = sl.d_buf, *d_ctrl = d_eps + (size_t)K * H, *d_costs = d_ctrl + (size_t)K * H;
     float *d_w = d_costs + K, *d_mu = d_w + K;
     e = cudaMemcpyAsync(d_eps, pin, sizeof(float) * (size_t)K * H, cudaMemcpyHostToDevice, sl.stream);
@@ -149,6 +154,20 @@ static void finish(vpm_server *s, const Request &r, int status, const float *mu,
     if (mu) res.mu.assign(mu, mu + r.H);
     s->done[r.ticket] = std::move(res);
     s->cv_done.notify_all();
+}
+
+// Device memory a request can take now: what the device has free plus what the library's pool
+// holds reserved and unused, less the reserve. Read at every admission, so memory that other
+// code in the process allocates or frees after the server was made counts.
+static size_t live_available(const vpm_server *s)
+{
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const size_t avail = free_b + vpm::lib_pool_idle_bytes();
+    return avail > s->reserve ? avail - s->reserve : 0;
 }
 
 static void worker_loop(vpm_server *s)
@@ -189,7 +208,11 @@ static void worker_loop(vpm_server *s)
             const bool fits_rollouts = s->in_flight_rollouts == 0 ||
                                        s->in_flight_rollouts + it->K <= s->rollout_budget;
             if (!fits_rollouts) break;        // keep arrival order for work that fills the device
-            if (s->scenario_busy[it->scenario] || s->in_flight_bytes + it->bytes > s->budget) { ++it; continue; }
+            if (s->scenario_busy[it->scenario] || s->in_flight_bytes + it->bytes > s->budget ||
+                it->bytes > live_available(s)) {
+                ++it;
+                continue;
+            }
             Request r = std::move(*it);
             it = s->queue.erase(it);
             r.t_start = s->now_ms();
@@ -209,9 +232,12 @@ static void worker_loop(vpm_server *s)
         bool any_busy = false;
         for (auto &sl : s->slots) any_busy |= sl.busy;
         if (!progressed) {
-            // idle: sleep until a submission; busy: poll the device again shortly
+            // busy: poll the device again shortly; requests waiting for device memory that other
+            // code holds: look again every half millisecond; idle: sleep until a submission
             if (any_busy)
                 s->cv_work.wait_for(lk, std::chrono::microseconds(50));
+            else if (!s->queue.empty())
+                s->cv_work.wait_for(lk, std::chrono::microseconds(500));
             else
                 s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
         }
@@ -233,7 +259,9 @@ extern "C" vpm_status vpm_server_create(const vpm_server_config *cfg, vpm_server
     cudaGetDevice(&s->device);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    s->budget = cfg->hbm_budget ? cfg->hbm_budget : (size_t)(0.8 * (double)free_b);
+    s->total_mem = total_b;
+    s->reserve = total_b / 50 > ((size_t)1 << 30) ? total_b / 50 : ((size_t)1 << 30);
+    s->budget = cfg->hbm_budget ? cfg->hbm_budget : ~(size_t)0;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     s->rollout_budget = cfg->max_inflight_rollouts > 0 ? cfg->max_inflight_rollouts : (long long)sms * 7;
@@ -293,8 +321,9 @@ extern "C" vpm_status vpm_server_submit(vpm_server *s, int scenario, int K, int 
     if (scenario < 0 || scenario >= (int)s->scenarios.size())
         return sfail(VPM_ERR_INVALID, "vpm_server_submit: unknown scenario %d", scenario);
     r.bytes = r.buf_bytes + vpm::rollout_scratch_bytes(s->scenarios[scenario], K, H, advance_steps);
-    if (r.bytes > s->budget)
-        return sfail(VPM_ERR_CAPACITY, "vpm_server_submit: request needs %zu bytes, budget %zu", r.bytes, s->budget);
+    if (r.bytes > s->budget || r.bytes + s->reserve > s->total_mem)
+        return sfail(VPM_ERR_CAPACITY, "vpm_server_submit: request needs %zu bytes; budget %zu, device %zu less %zu "
+                     "kept free", r.bytes, s->budget, s->total_mem, s->reserve);
     r.ticket = s->next_ticket++;
     r.t_submit = s->now_ms();
     // the newest request for a scenario supersedes the one still waiting in the queue

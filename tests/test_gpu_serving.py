@@ -1,5 +1,6 @@
 """Replanning server: results alone and in a mix, the plain per-request form, supersession of
-queued requests, admission by the memory budget, resident fields advanced between replans."""
+queued requests, admission by the memory budget and by the device memory free at admission,
+resident fields advanced between replans."""
 import numpy as np
 import pytest
 
@@ -113,4 +114,30 @@ def test_resident_field_advances_like_vpm_step():
         st.step(0.75)
     ref_parts, ref_xg, _ = st.read()
     assert np.array_equal(parts, ref_parts) and np.array_equal(xg, ref_xg)
+    srv.close()
+
+
+def test_admission_waits_for_memory_taken_after_creation():
+    """Device memory that other code takes after the server was made holds a request in the queue
+    (no out-of-memory failure) until it is freed; then the request runs. The library's scratch
+    comes from its own pool, so the device's default pool (torch's allocations here) is untouched."""
+    torch, V = cuda()
+    srv, p, fields = _server(V, 2)
+    K, H = 512, 20
+    need = srv.request_bytes(4, K, H)
+    V.pool_trim()
+    torch.cuda.empty_cache()
+    free, total = torch.cuda.mem_get_info()
+    reserve = max(1 << 30, total // 50)                # the server keeps this much free
+    hog_bytes = free - reserve - need // 2               # leaves half the request's bytes
+    assert hog_bytes > 0
+    hog = torch.empty(hog_bytes, dtype=torch.uint8, device="cuda")
+    t = srv.submit(4, W.mppi_noise(70, K, H, W.MPPI_SIGMA_U))
+    assert srv.poll(t, timeout_ms=1500) is None          # waiting, not failed
+    st = srv.stats()
+    assert st["queued"] == 1 and st["in_flight"] == 0
+    del hog
+    torch.cuda.empty_cache()
+    res = srv.poll(t, timeout_ms=60000)
+    assert res is not None and res[0]["status"] == V.VPM_OK
     srv.close()
