@@ -916,7 +916,8 @@ def run_northstar(args):
 
 def run_uneven(args):
     """Uneven batching: 4096 rollouts with particle counts log-uniform in [64, 8192], H = 50,
-    binary32, persistent class launches with autotuned block sizes, the horizon replayed from a
+    binary32, persistent launches (class launches side by side or one merged launch) with
+    autotuned block and diagonal-unit sizes, the horizon replayed from a
     CUDA graph; against one launch per rollout (timed on a systematic sample of the rollouts
     sorted by size and scaled to all of them: the launches are serial on one stream)."""
     import torch
@@ -968,7 +969,7 @@ def run_uneven(args):
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "uneven batch: %d rollouts, counts log-uniform in [64, 8192], H=50" % R,
                    "pairs_per_step": pairs, "max_count": int(counts.max()),
-                   "schedule": b.schedule(), "graph": True},
+                   "schedule": b.schedule(), "tuner_whole_batch_3_steps": b.tuned_modes(), "graph": True},
         "one_launch_per_rollout": {"ms_scaled": per_launch_ms, "sampled_rollouts": int(len(sample)),
                                    "pairs_per_s": pairs / (per_launch_ms / 1e3)},
         "speedup": per_launch_ms / ms, "clocks": clk.summary()}), flush=True)

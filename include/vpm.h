@@ -373,8 +373,9 @@ vpm_status vpm_fixed_exponent(float gmax, int n, int kernel, double r_core, int 
  * whose fields have different particle counts (one rollout per root). Roots are grouped by
  * the shared memory their fields can need into classes; each class runs as one persistent
  * launch (blocks claim rollouts largest-first) on its own stream, forked from and joined back
- * into the caller's stream. A rollout's result does not depend on the class, the block size or
- * the order of execution.
+ * into the caller's stream, or, if the autotuner finds it faster, all rollouts run in one
+ * persistent launch sized for the largest field. A rollout's result does not depend on the
+ * class, the block size, the diagonal-unit size or the order of execution.
  */
 typedef struct vpm_batch vpm_batch;
 
@@ -404,16 +405,33 @@ vpm_status vpm_batch_rollout(vpm_batch *batch, int H, const float *d_controls, f
                              cudaStream_t stream);
 
 /*
- * Autotuner: times each class alone over min(H, 3) steps with 128, 256 and 512 threads per
- * block (where they fit) and keeps the fastest per class. It changes speed only, never
- * results. Synchronises `stream`.
+ * Autotuner over the launch shape. Each class, and the merged class that runs every rollout in
+ * one persistent launch sized for the largest field, is timed alone over min(H, 3) steps for
+ * each block size that fits (128, 256, 512 threads) and each diagonal pair-unit size (32, 64 or
+ * 128 targets, i.e. 1, 2 or 4 per lane; Vatistas kernel only, others keep 2), keeping its
+ * fastest. Then the whole batch is timed as the class launches side by side and as the one
+ * merged launch, and the faster is kept. Rollouts use one block (CTA) each. It changes speed
+ * only, never results. Synchronises `stream`.
  */
 vpm_status vpm_batch_tune(vpm_batch *batch, int H, const float *d_controls, cudaStream_t stream);
 
-/* The schedule: number of non-empty classes and, per class, its capacity, threads per block,
- * number of rollouts and tuned time (ms, 0 before tuning). Arrays hold up to 5 entries. */
+/* The schedule: the number of launches it runs and, per launch, the capacity, threads per
+ * block, number of rollouts, tuned time (ms, 0 before tuning), targets per lane of the
+ * diagonal pair units and CTAs per rollout (any output array may be null; arrays hold up to 5
+ * entries); *h_merged (if non-null) is 1 when all rollouts run in one launch. */
 vpm_status vpm_batch_schedule(const vpm_batch *batch, int *h_nclasses, int *h_cap, int *h_nt,
-                              int *h_items, float *h_tuned_ms);
+                              int *h_items, float *h_tuned_ms, int *h_diag_t, int *h_ctas,
+                              int *h_merged);
+
+/* The tuner's times (ms, min(H, 3) steps of the whole batch) of the class launches side by side
+ * and of the one merged launch (0 before tuning or with a single class). */
+vpm_status vpm_batch_tuned_modes(const vpm_batch *batch, float *h_split_ms, float *h_merged_ms);
+
+/* Sets the schedule by hand: merged = 1 selects the one-launch schedule, then launch `cls` of
+ * that schedule (as vpm_batch_schedule lists them) gets nt threads (128, 256, 512) and diag_t
+ * targets per lane (1, 2, 4; 2 unless the wake kernel is Vatistas; binary64 batches: 128 and
+ * 2). Results do not depend on it. Errors: VPM_ERR_INVALID (a size that does not fit). */
+vpm_status vpm_batch_set_schedule(vpm_batch *batch, int merged, int cls, int nt, int diag_t);
 
 /* Reads and clears the batch's device error word (synchronises `stream`). */
 vpm_status vpm_batch_status(vpm_batch *batch, cudaStream_t stream);

@@ -112,7 +112,9 @@ _SIGNATURES = {
     "vpm_batch_destroy": ([_VP], _I),
     "vpm_batch_rollout": ([_VP, _I, _VP, _VP, _VP, _VP, _I, _VP], _I),
     "vpm_batch_tune": ([_VP, _I, _VP, _VP], _I),
-    "vpm_batch_schedule": ([_VP, C.POINTER(_I), _VP, _VP, _VP, _VP], _I),
+    "vpm_batch_set_schedule": ([_VP, _I, _I, _I, _I], _I),
+    "vpm_batch_tuned_modes": ([_VP, C.POINTER(_F), C.POINTER(_F)], _I),
+    "vpm_batch_schedule": ([_VP, C.POINTER(_I), _VP, _VP, _VP, _VP, _VP, _VP, C.POINTER(_I)], _I),
     "vpm_batch_status": ([_VP, _VP], _I),
     "vpm_server_create": ([_VP, C.POINTER(_VP)], _I),
     "vpm_server_add_scenario": ([_VP, C.POINTER(Params), _VP, _I, _I, _VP, C.POINTER(_I)], _I),
@@ -489,14 +491,27 @@ class Batch:
         check(lib().vpm_batch_tune(self._h, controls.shape[1], ptr(controls), stream_handle(stream)))
 
     def schedule(self):
+        """Per launch of the current schedule: capacity, threads, rollouts, tuned ms, diagonal
+        targets per lane, CTAs per rollout, and whether all rollouts run in one launch."""
         n = C.c_int()
-        cap, nt, items = (np.zeros(5, np.int32) for _ in range(3))
-        ms = np.zeros(5, np.float32)
+        cap, nt, items, dt, ctas = (np.zeros(6, np.int32) for _ in range(5))
+        ms = np.zeros(6, np.float32)
+        merged = C.c_int()
         check(lib().vpm_batch_schedule(self._h, C.byref(n), cap.ctypes.data_as(_VP), nt.ctypes.data_as(_VP),
-                                       items.ctypes.data_as(_VP), ms.ctypes.data_as(_VP)))
-        k = n.value
-        return [dict(cap=int(cap[i]), threads=int(nt[i]), rollouts=int(items[i]), tuned_ms=float(ms[i]))
-                for i in range(k)]
+                                       items.ctypes.data_as(_VP), ms.ctypes.data_as(_VP),
+                                       dt.ctypes.data_as(_VP), ctas.ctypes.data_as(_VP), C.byref(merged)))
+        return [dict(cap=int(cap[i]), threads=int(nt[i]), rollouts=int(items[i]), tuned_ms=float(ms[i]),
+                     diag_t=int(dt[i]), ctas=int(ctas[i]), merged=bool(merged.value))
+                for i in range(n.value)]
+
+    def tuned_modes(self):
+        """The tuner's whole-batch times (ms): class launches side by side, one merged launch."""
+        a, m = C.c_float(), C.c_float()
+        check(lib().vpm_batch_tuned_modes(self._h, C.byref(a), C.byref(m)))
+        return dict(class_launches_ms=a.value, one_launch_ms=m.value)
+
+    def set_schedule(self, merged: bool, cls: int, threads: int, diag_t: int):
+        check(lib().vpm_batch_set_schedule(self._h, int(bool(merged)), int(cls), int(threads), int(diag_t)))
 
     def status(self, stream=None):
         check(lib().vpm_batch_status(self._h, stream_handle(stream)))

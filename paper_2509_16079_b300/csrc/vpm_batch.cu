@@ -1,6 +1,7 @@
 // Batches of rollouts from many different roots (uneven particle counts) in persistent
 // launches: host-side grouping into shared-memory classes, longest-first ordering, the
-// block-size autotuner, and capture of a whole horizon into a CUDA graph.
+// autotuner (block size, diagonal-unit size, class launches or one launch for all), and
+// capture of a whole horizon into a CUDA graph.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -52,6 +53,7 @@ static const int kStateStride = kMaxB + 2;
 struct BatchClass {
     int cap = 0;                 // largest capacity in the class (shared-memory size)
     int nt = 128;                // threads per block (autotuned)
+    int dt = 2;                  // targets per lane of the diagonal pair units (autotuned)
     int grid = 0;                // persistent blocks for nt (resident blocks per SM x SMs)
     float tuned_ms = 0.f;
     std::vector<int> items;      // rollout indices, largest first
@@ -73,7 +75,9 @@ struct vpm_batch {
     int *d_n = nullptr;
     double *d_glider = nullptr, *d_hist = nullptr, *d_kinv = nullptr;
     int *d_counters = nullptr, *d_status = nullptr;
-    BatchClass cls[kNumClasses];
+    BatchClass cls[kNumClasses + 1];   // the classes, then all rollouts as one class
+    bool merged = false;               // run the last one (one launch) instead of the classes
+    float split_ms = 0.f, merged_ms = 0.f;   // the tuner's whole-batch times of both schedules
     cudaEvent_t fork = nullptr;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -141,7 +145,8 @@ extern "C" vpm_status vpm_batch_create(const vpm_params *params, int R, const in
     BTRY(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     b->rec_bytes = params->precision == VPM_FP64 ? sizeof(Part64) : sizeof(float4);
     fill_dev_params_ext(params, b->dp);
-    // classes by capacity, longest first within a class
+    // classes by capacity, longest first within a class; the merged class holds every rollout
+    BatchClass &all = b->cls[kNumClasses];
     for (int i = 0; i < R; ++i) {
         long long cap = (long long)h_counts[i] + 2LL * max_horizon;
         if (params->n_wake_max > 0)
@@ -154,6 +159,8 @@ extern "C" vpm_status vpm_batch_create(const vpm_params *params, int R, const in
         }
         b->cls[c].items.push_back(i);
         b->cls[c].cap = std::max(b->cls[c].cap, (int)std::max<long long>(cap, 1));
+        all.items.push_back(i);
+        all.cap = std::max(all.cap, (int)std::max<long long>(cap, 1));
     }
     for (auto &c : b->cls)
         std::stable_sort(c.items.begin(), c.items.end(),
@@ -176,7 +183,7 @@ extern "C" vpm_status vpm_batch_create(const vpm_params *params, int R, const in
         (e = cudaMalloc((void **)&b->d_glider, sizeof(double) * gl.size())) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_hist, sizeof(double) * hist.size())) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_kinv, sizeof(double) * kinv.size())) != cudaSuccess ||
-        (e = cudaMalloc((void **)&b->d_counters, sizeof(int) * kNumClasses)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&b->d_counters, sizeof(int) * (kNumClasses + 1))) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_status, sizeof(int))) != cudaSuccess) {
         batch_free(b);
         cudaGetLastError();
@@ -237,11 +244,11 @@ static void batch_args(const vpm_batch *b, int H, const float *ctrl, float *cost
 
 // Persistent grid of class c for nt threads per block; also sets the kernel's shared-memory
 // limit, so it runs before any capture.
-static cudaError_t prepare_class(vpm_batch *b, int c, int nt)
+static cudaError_t prepare_class(vpm_batch *b, int c, int nt, int dt)
 {
     BatchClass &k = b->cls[c];
     const size_t smem = rollout_smem_bytes(b->params.precision, k.cap);
-    const int per_sm = uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, smem);
+    const int per_sm = uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, dt, smem);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     k.grid = std::min<int>((int)k.items.size(), per_sm * b->sms);
     // scratch for the grid's blocks; a captured graph that holds the old buffer is dropped
@@ -260,18 +267,27 @@ static cudaError_t prepare_class(vpm_batch *b, int c, int nt)
     return cudaSuccess;
 }
 
-// Enqueues the class launches on the class streams, forked from and joined back into s. The
-// classes must have been prepared for the block sizes used.
+// The classes a schedule runs: the separate classes, or the merged one.
+static bool runs_class(const vpm_batch *b, int c, bool merged)
+{
+    return !b->cls[c].items.empty() && (merged ? c == kNumClasses : c < kNumClasses);
+}
+
+// Enqueues the class launches on the class streams, forked from and joined back into s (the
+// merged schedule: one launch). The classes must have been prepared for the sizes used.
 static cudaError_t enqueue_classes(vpm_batch *b, int H, const float *ctrl, float *costs,
                                    int *count, double *final_glider, cudaStream_t s,
-                                   int only_class = -1, int nt_override = 0)
+                                   int only_class = -1, int nt_override = 0, int dt_override = 0,
+                                   int merged = -1)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * kNumClasses, s);
+    const bool mg = merged < 0 ? b->merged : merged != 0;
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * (kNumClasses + 1), s);
     if (!e) e = cudaEventRecord(b->fork, s);
-    for (int c = 0; c < kNumClasses && !e; ++c) {
+    for (int c = 0; c <= kNumClasses && !e; ++c) {
         BatchClass &k = b->cls[c];
-        if (k.items.empty() || (only_class >= 0 && c != only_class)) continue;
+        if (only_class >= 0 ? (c != only_class || k.items.empty()) : !runs_class(b, c, mg)) continue;
         const int nt = nt_override ? nt_override : k.nt;
+        const int dt = dt_override ? dt_override : k.dt;
         const int grid = k.grid;
         RolloutArgs a;
         batch_args(b, H, ctrl, costs, count, final_glider, a);
@@ -282,7 +298,7 @@ static cudaError_t enqueue_classes(vpm_batch *b, int H, const float *ctrl, float
         a.rev = k.d_rev;
         a.rev_stride = rollout_rev_slots(b->params.precision, k.cap);
         e = cudaStreamWaitEvent(k.stream, b->fork, 0);
-        if (!e) e = launch_uneven(b->params.precision, a, grid, nt, k.stream);
+        if (!e) e = launch_uneven(b->params.precision, a, grid, nt, dt, k.stream);
         if (!e) e = cudaEventRecord(k.done, k.stream);
         if (!e) e = cudaStreamWaitEvent(s, k.done, 0);
     }
@@ -296,8 +312,8 @@ extern "C" vpm_status vpm_batch_rollout(vpm_batch *b, int H, const float *d_cont
     vpm::TraceRange tr("vpm_batch_rollout");
     if (!b || !d_controls || !d_costs) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: null argument");
     if (H < 1 || H > b->max_h) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: need 1 <= H <= %d", b->max_h);
-    for (int c = 0; c < kNumClasses; ++c)
-        if (!b->cls[c].items.empty()) BTRY(prepare_class(b, c, b->cls[c].nt), "prepare class");
+    for (int c = 0; c <= kNumClasses; ++c)
+        if (runs_class(b, c, b->merged)) BTRY(prepare_class(b, c, b->cls[c].nt, b->cls[c].dt), "prepare class");
     if (!use_graph) {
         cudaError_t e = enqueue_classes(b, H, d_controls, d_costs, d_count, d_final_glider, stream);
         if (e) return bcuda(e, "vpm_batch_rollout");
@@ -324,9 +340,27 @@ extern "C" vpm_status vpm_batch_rollout(vpm_batch *b, int H, const float *d_cont
     return VPM_OK;
 }
 
-// Autotuner: for every class, times one launch of the class alone for each block size that
-// fits (128, 256, 512 threads) over min(H, 3) steps and keeps the fastest. Results of a rollout
-// do not depend on the block size, so tuning changes speed only. Synchronises `stream`.
+// Times one enqueue of the batch (or of one class) over Ht steps after one warm-up enqueue.
+static cudaError_t time_enqueue(vpm_batch *b, int Ht, const float *ctrl, float *costs, cudaStream_t s,
+                                cudaEvent_t t0, cudaEvent_t t1, float &ms, int only_class, int nt,
+                                int dt, int merged)
+{
+    cudaError_t e = enqueue_classes(b, Ht, ctrl, costs, nullptr, nullptr, s, only_class, nt, dt, merged);
+    if (!e) e = cudaEventRecord(t0, s);
+    if (!e) e = enqueue_classes(b, Ht, ctrl, costs, nullptr, nullptr, s, only_class, nt, dt, merged);
+    if (!e) e = cudaEventRecord(t1, s);
+    if (!e) e = cudaEventSynchronize(t1);
+    if (!e) e = cudaEventElapsedTime(&ms, t0, t1);
+    return e;
+}
+
+// Autotuner over the launch shape: for every class (and for the merged class that runs all
+// rollouts in one persistent launch), one launch of the class alone over min(H, 3) steps is timed
+// for each block size that fits (128, 256, 512 threads) and each diagonal-unit size (32, 64 or
+// 128 targets: 1, 2 or 4 per lane; the Vatistas kernel only, others keep 2); each keeps its
+// fastest. Then the whole batch is timed as concurrent class launches and as the one merged
+// launch, and the faster schedule is kept. A rollout's result depends on none of these choices,
+// so tuning changes speed only. Synchronises `stream`.
 extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_controls,
                                      cudaStream_t stream)
 {
@@ -340,31 +374,43 @@ extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_control
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
     vpm_status st = VPM_OK;
-    for (int c = 0; c < kNumClasses && st == VPM_OK; ++c) {
+    const bool vat = b->params.wake_kernel == VPM_KERNEL_VATISTAS;
+    int nonempty = 0;
+    for (int c = 0; c < kNumClasses; ++c) nonempty += !b->cls[c].items.empty();
+    for (int c = 0; c <= kNumClasses && st == VPM_OK; ++c) {
         BatchClass &k = b->cls[c];
-        if (k.items.empty()) continue;
+        if (k.items.empty() || (c == kNumClasses && nonempty < 2)) continue;
         const size_t smem = rollout_smem_bytes(b->params.precision, k.cap);
         float best = INFINITY;
-        int best_nt = k.nt;
+        int best_nt = k.nt, best_dt = k.dt;
         for (int nt : {128, 256, 512}) {
-            if (uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, smem) < 1) continue;
-            cudaError_t e = prepare_class(b, c, nt);
-            if (!e) e = enqueue_classes(b, Ht, d_controls, costs, nullptr, nullptr, stream, c, nt);
-            if (!e) e = cudaEventRecord(t0, stream);
-            if (!e) e = enqueue_classes(b, Ht, d_controls, costs, nullptr, nullptr, stream, c, nt);
-            if (!e) e = cudaEventRecord(t1, stream);
-            if (!e) e = cudaEventSynchronize(t1);
-            float ms = 0.f;
-            if (!e) e = cudaEventElapsedTime(&ms, t0, t1);
-            if (e) { st = bcuda(e, "vpm_batch_tune"); break; }
-            if (ms < best) { best = ms; best_nt = nt; }
+            for (int dt : {1, 2, 4}) {
+                if (dt != 2 && !vat) continue;
+                if (uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, dt, smem) < 1) continue;
+                float ms = 0.f;
+                cudaError_t e = prepare_class(b, c, nt, dt);
+                if (!e) e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, ms, c, nt, dt, -1);
+                if (e) { st = bcuda(e, "vpm_batch_tune"); break; }
+                if (ms < best) { best = ms; best_nt = nt; best_dt = dt; }
+            }
+            if (st != VPM_OK) break;
         }
         k.nt = best_nt;
+        k.dt = best_dt;
         k.tuned_ms = best;
         if (st == VPM_OK) {
-            cudaError_t e = prepare_class(b, c, best_nt);
+            cudaError_t e = prepare_class(b, c, best_nt, best_dt);
             if (e) st = bcuda(e, "vpm_batch_tune");
         }
+    }
+    // class launches side by side against the one merged launch
+    b->merged = false;
+    if (st == VPM_OK && nonempty >= 2) {
+        float split = 0.f, one = 0.f;
+        cudaError_t e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, split, -1, 0, 0, 0);
+        if (!e) e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, one, -1, 0, 0, 1);
+        if (e) st = bcuda(e, "vpm_batch_tune");
+        else { b->merged = one < split; b->split_ms = split; b->merged_ms = one; }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
@@ -376,19 +422,57 @@ extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_control
 }
 
 extern "C" vpm_status vpm_batch_schedule(const vpm_batch *b, int *h_nclasses, int *h_cap,
-                                         int *h_nt, int *h_items, float *h_tuned_ms)
+                                         int *h_nt, int *h_items, float *h_tuned_ms, int *h_diag_t,
+                                         int *h_ctas, int *h_merged)
 {
     if (!b || !h_nclasses) return bfail(VPM_ERR_INVALID, "vpm_batch_schedule: null argument");
     int m = 0;
-    for (const auto &k : b->cls) {
-        if (k.items.empty()) continue;
+    for (int c = 0; c <= kNumClasses; ++c) {
+        if (!runs_class(b, c, b->merged)) continue;
+        const BatchClass &k = b->cls[c];
         if (h_cap) h_cap[m] = k.cap;
         if (h_nt) h_nt[m] = k.nt;
         if (h_items) h_items[m] = (int)k.items.size();
         if (h_tuned_ms) h_tuned_ms[m] = k.tuned_ms;
+        if (h_diag_t) h_diag_t[m] = k.dt;
+        if (h_ctas) h_ctas[m] = 1;
         ++m;
     }
     *h_nclasses = m;
+    if (h_merged) *h_merged = b->merged ? 1 : 0;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_batch_tuned_modes(const vpm_batch *b, float *h_split_ms, float *h_merged_ms)
+{
+    if (!b || !h_split_ms || !h_merged_ms) return bfail(VPM_ERR_INVALID, "vpm_batch_tuned_modes: null argument");
+    *h_split_ms = b->split_ms;
+    *h_merged_ms = b->merged_ms;
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_batch_set_schedule(vpm_batch *b, int merged, int cls, int nt, int diag_t)
+{
+    if (!b) return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: null batch");
+    if (nt != 128 && nt != 256 && nt != 512) return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: threads must be 128, 256 or 512");
+    if (diag_t != 1 && diag_t != 2 && diag_t != 4) return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: diag_t must be 1, 2 or 4");
+    if (b->params.precision == VPM_FP64 && (nt != 128 || diag_t != 2))
+        return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: binary64 batches run 128 threads, diag_t 2");
+    if (b->params.wake_kernel != VPM_KERNEL_VATISTAS && diag_t != 2)
+        return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: diag_t other than 2 needs the Vatistas kernel");
+    int m = 0, target = -1;
+    for (int c = 0; c <= kNumClasses; ++c) {
+        if (!runs_class(b, c, merged != 0)) continue;
+        if (m++ == cls) target = c;
+    }
+    if (target < 0) return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: class %d does not exist in that schedule", cls);
+    const size_t smem = rollout_smem_bytes(b->params.precision, b->cls[target].cap);
+    if (uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, diag_t, smem) < 1)
+        return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: %d threads do not fit the class", nt);
+    b->merged = merged != 0;
+    b->cls[target].nt = nt;
+    b->cls[target].dt = diag_t;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     return VPM_OK;
 }
 

@@ -628,22 +628,23 @@ __device__ void offdiag_row(const DevParams &p, const float4 *part, float2 *scr,
 
 struct PairPlan {
     int rows_off;   // off-diagonal rows (units 0 .. rows_off - 1, longest first)
-    int nunits;     // then the diagonal groups of kDiagGroup targets
+    int nunits;     // then the diagonal groups of 32 DT targets
 };
 
+template <int DT = kDiagT>
 __device__ __forceinline__ PairPlan pair_plan(int n)
 {
     PairPlan c;
     const int rows = (n + kRow - 1) / kRow;
     c.rows_off = rows > 1 ? rows - 1 : 0;
-    c.nunits = c.rows_off + (n + kDiagGroup - 1) / kDiagGroup;
+    c.nunits = c.rows_off + (n + 32 * DT - 1) / (32 * DT);
     return c;
 }
 
 // Units are claimed from a counter that is never reset within a rollout: every warp makes
 // exactly one failing claim per step, so a step consumes nunits + nwarps claims and every
 // thread can track the counter's base for the next step without a barrier.
-template <int KER>
+template <int KER, int DT = kDiagT>
 __device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, float2 *vel,
                               float2 *scr, int cap32, int n, const PairPlan &pp, int claim_base)
 {
@@ -656,8 +657,8 @@ __device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, f
         if (c < pp.rows_off) {
             offdiag_row<KER>(p, part, scr, cap32, n, c);
         } else {
-            const int g = c - pp.rows_off, t0 = kDiagGroup * g, r0 = (t0 / kRow) * kRow;
-            old_pairs_chunk<KER, kDiagT>(p, part, vel, r0, min(r0 + kRow, n), t0, n);
+            const int g = c - pp.rows_off, t0 = 32 * DT * g, r0 = (t0 / kRow) * kRow;
+            old_pairs_chunk<KER, DT>(p, part, vel, r0, min(r0 + kRow, n), t0, n);
         }
     }
 }
@@ -987,7 +988,7 @@ __device__ __forceinline__ int plate_warp()
 
 // One full step of one rollout. All threads call it with the same particle count n (updated
 // here) and unit-claim base; returns with the block synchronised.
-template <class R, int KER>
+template <class R, int KER, int DT = kDiagT>
 __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *part,
                           typename Store<R>::V *vel, double u_ctrl, const RolloutArgs &a,
                           bool probe, int &n, int &claim_base)
@@ -1009,7 +1010,7 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
             if (lane == 0) w.n = m;
             fresh_velocities_f32<KER>(p, w, part, n, m);
         }
-        const PairPlan pp = pair_plan(n);
+        const PairPlan pp = pair_plan<DT>(n);
         const int cap32 = (a.cap + 31) & ~31;
         float2 *scr = a.rev ? a.rev + (size_t)blockIdx.x * a.rev_stride : nullptr;
 #if VPM_DEBUG_BOUNDS
@@ -1019,7 +1020,7 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
             return;
         }
 #endif
-        old_pairs_f32<KER>(p, w, part, vel, scr, cap32, n, pp, claim_base);
+        old_pairs_f32<KER, DT>(p, w, part, vel, scr, cap32, n, pp, claim_base);
         claim_base += pp.nunits + (int)(blockDim.x >> 5);
         __syncthreads();
         n1 = w.n;
@@ -1181,7 +1182,7 @@ __device__ void pace_step(const RolloutArgs &a, unsigned sm, int slot, int k)
 }
 
 // One rollout of a.H steps by the whole block, field resident in shared memory.
-template <class R, int KER>
+template <class R, int KER, int DT = kDiagT>
 __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P *part,
                             typename Store<R>::V *vel, int rid)
 {
@@ -1208,7 +1209,7 @@ __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P 
                 fb -= a.pol_gains[j * 7 + c] * (w.xg[c] - a.pol_xbar[j * 7 + c]);
             u = (a.controls ? u : 0.0) + fb;
         }
-        step_once<R, KER>(a.p, w, part, vel, u, a, a.H == 1, n, claim_base);
+        step_once<R, KER, DT>(a.p, w, part, vel, u, a, a.H == 1, n, claim_base);
         if (a.traj && threadIdx.x < 7)
             a.traj[((size_t)rid * a.H + k) * 7 + threadIdx.x] = w.xg[threadIdx.x];
     }
@@ -1247,7 +1248,7 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) rollout_kernel(const R
 
 // Persistent form for batches of uneven rollouts: each block claims the next rollout of
 // a.order until all a.n_items are done. Which block runs a rollout does not change its result.
-template <class R, int KER, int NT>
+template <class R, int KER, int NT, int DT = kDiagT>
 __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const RolloutArgs a)
 {
     using P = typename Store<R>::P;
@@ -1263,7 +1264,7 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const Ro
         const int q = s_item;
         __syncthreads();
         if (q >= a.n_items) break;
-        run_rollout<R, KER>(a, w, part, vel, a.order[q]);
+        run_rollout<R, KER, DT>(a, w, part, vel, a.order[q]);
     }
 }
 
@@ -1455,10 +1456,10 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
     });
 }
 
-template <class R, int KER, int NT>
+template <class R, int KER, int NT, int DT = kDiagT>
 static cudaError_t launch_u(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    auto k = uneven_kernel<R, KER, NT>;
+    auto k = uneven_kernel<R, KER, NT, DT>;
     static std::atomic<size_t> granted{0};
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
@@ -1470,15 +1471,27 @@ static cudaError_t launch_u(const RolloutArgs &a, int grid, size_t smem, cudaStr
     return cudaGetLastError();
 }
 
+// Block size nt and diagonal-unit targets per lane dt (1, 2 or 4; other than kDiagT only for the
+// Vatistas kernel of Eq. 5, the workloads' kernel) of the binary32 persistent launch.
 template <class R, int KER>
-static cudaError_t launch_u_nt(const RolloutArgs &a, int grid, int nt, size_t smem, cudaStream_t s)
+static cudaError_t launch_u_nt(const RolloutArgs &a, int grid, int nt, int dt, size_t smem, cudaStream_t s)
 {
+    if (KER == VPM_KERNEL_VATISTAS && dt == 1) {
+        if (nt == 512) return launch_u<R, KER, 512, 1>(a, grid, smem, s);
+        if (nt == 256) return launch_u<R, KER, 256, 1>(a, grid, smem, s);
+        return launch_u<R, KER, 128, 1>(a, grid, smem, s);
+    }
+    if (KER == VPM_KERNEL_VATISTAS && dt == 4) {
+        if (nt == 512) return launch_u<R, KER, 512, 4>(a, grid, smem, s);
+        if (nt == 256) return launch_u<R, KER, 256, 4>(a, grid, smem, s);
+        return launch_u<R, KER, 128, 4>(a, grid, smem, s);
+    }
     if (nt == 512) return launch_u<R, KER, 512>(a, grid, smem, s);
     if (nt == 256) return launch_u<R, KER, 256>(a, grid, smem, s);
     return launch_u<R, KER, 128>(a, grid, smem, s);
 }
 
-cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, cudaStream_t s)
+cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, int dt, cudaStream_t s)
 {
     const size_t smem = rollout_smem_bytes(precision, a.cap);
     const int ker = a.p.kernel;
@@ -1488,9 +1501,9 @@ cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt,
         return launch_u<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
     }
     return with_rev_scratch(a, grid, s, [&](const RolloutArgs &b) {
-        if (ker == VPM_KERNEL_GAUSSIAN) return launch_u_nt<float, VPM_KERNEL_GAUSSIAN>(b, grid, nt, smem, s);
-        if (ker == VPM_KERNEL_SINGULAR) return launch_u_nt<float, VPM_KERNEL_SINGULAR>(b, grid, nt, smem, s);
-        return launch_u_nt<float, VPM_KERNEL_VATISTAS>(b, grid, nt, smem, s);
+        if (ker == VPM_KERNEL_GAUSSIAN) return launch_u_nt<float, VPM_KERNEL_GAUSSIAN>(b, grid, nt, dt, smem, s);
+        if (ker == VPM_KERNEL_SINGULAR) return launch_u_nt<float, VPM_KERNEL_SINGULAR>(b, grid, nt, dt, smem, s);
+        return launch_u_nt<float, VPM_KERNEL_VATISTAS>(b, grid, nt, dt, smem, s);
     });
 }
 
@@ -1517,12 +1530,22 @@ static int occupancy_of(F k, int nt, size_t smem)
     return nb;
 }
 
-int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem)
+int uneven_blocks_per_sm(int precision, int kernel, int nt, int dt, size_t smem)
 {
     if (precision == VPM_FP64) {
         if (kernel == VPM_KERNEL_GAUSSIAN) return occupancy_of(uneven_kernel<double, VPM_KERNEL_GAUSSIAN, 128>, 128, smem);
         if (kernel == VPM_KERNEL_SINGULAR) return occupancy_of(uneven_kernel<double, VPM_KERNEL_SINGULAR, 128>, 128, smem);
         return occupancy_of(uneven_kernel<double, VPM_KERNEL_VATISTAS, 128>, 128, smem);
+    }
+    if (kernel == VPM_KERNEL_VATISTAS && (dt == 1 || dt == 4)) {
+        if (dt == 1) {
+            if (nt == 512) return occupancy_of(uneven_kernel<float, VPM_KERNEL_VATISTAS, 512, 1>, 512, smem);
+            if (nt == 256) return occupancy_of(uneven_kernel<float, VPM_KERNEL_VATISTAS, 256, 1>, 256, smem);
+            return occupancy_of(uneven_kernel<float, VPM_KERNEL_VATISTAS, 128, 1>, 128, smem);
+        }
+        if (nt == 512) return occupancy_of(uneven_kernel<float, VPM_KERNEL_VATISTAS, 512, 4>, 512, smem);
+        if (nt == 256) return occupancy_of(uneven_kernel<float, VPM_KERNEL_VATISTAS, 256, 4>, 256, smem);
+        return occupancy_of(uneven_kernel<float, VPM_KERNEL_VATISTAS, 128, 4>, 128, smem);
     }
 #define VPM_OCC(KER)                                                                         \
     if (nt == 512) return occupancy_of(uneven_kernel<float, KER, 512>, 512, smem);           \

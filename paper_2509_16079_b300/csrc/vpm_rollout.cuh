@@ -76,10 +76,13 @@ size_t lib_pool_idle_bytes();
 long long rollout_rev_slots(int precision, int cap);
 cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s);
 // Persistent launch over a.n_items rollouts with `nt` threads per block (128, 256 or 512; the
-// binary64 path uses 128); `grid` blocks claim rollouts in a.order through a.counter.
-cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, cudaStream_t s);
+// binary64 path uses 128) and diagonal pair units of 32 dt targets (dt = 1, 2 or 4: every
+// target's sum is formed in the same order whatever dt, so results do not change; dt other than
+// 2 runs as 2 except for the Vatistas kernel); `grid` blocks claim rollouts in a.order through
+// a.counter.
+cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, int dt, cudaStream_t s);
 // Resident blocks per SM of the persistent kernel for this configuration (0 if it cannot run).
-int uneven_blocks_per_sm(int precision, int kernel, int nt, size_t smem);
+int uneven_blocks_per_sm(int precision, int kernel, int nt, int dt, size_t smem);
 // Throughput probe of the binary32 pair loop (Vatistas kernel, core radius r_core): `grid`
 // blocks of 128 threads each load the n records of d_src into shared memory and form every
 // target's sum over all n sources `reps` times with t targets per lane (1, 2 or 4); block b

@@ -69,11 +69,44 @@ def test_graph_replay_and_tuning_do_not_change_results():
             assert torch.equal(outs[0][k], base[k])
     b.tune(controls)
     sched = b.schedule()
-    assert all(s["threads"] in (128, 256, 512) and s["tuned_ms"] > 0 for s in sched)
+    assert all(s["threads"] in (128, 256, 512) and s["tuned_ms"] > 0 and s["diag_t"] in (1, 2, 4)
+               and s["ctas"] == 1 for s in sched)
     tuned = b.rollout(controls)
     torch.cuda.synchronize()
     for k in base:
         assert torch.equal(tuned[k], base[k])
+
+
+def test_every_schedule_gives_the_same_bits():
+    """Each class launch at every block size and diagonal-unit size, and all rollouts in one merged
+    launch at every size, give the bits of the default schedule."""
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 4
+    counts = list(W.uneven_counts(8, 30, 64, 3000)) + [2500, 1400, 90]
+    fields, gliders = _roots(counts, 3)
+    controls = torch.tensor(W.mppi_noise(9, len(counts), H, W.MPPI_SIGMA_U), device="cuda")
+    b = V.Batch(p, fields, gliders, H)
+    base = {k: v.clone() for k, v in b.rollout(controls).items()}
+    checked = 0
+    for merged in (False, True):
+        nl = 1 if merged else len(b.schedule())
+        assert nl >= (1 if merged else 3)
+        for cls in range(nl):
+            for threads in (128, 256, 512):
+                for diag_t in (1, 2, 4):
+                    try:
+                        b.set_schedule(merged, cls, threads, diag_t)
+                    except V.VpmError:
+                        continue                        # the size does not fit this class
+                    out = b.rollout(controls)
+                    torch.cuda.synchronize()
+                    assert b.schedule()[0]["merged"] == merged
+                    for k in base:
+                        assert torch.equal(out[k], base[k]), (merged, cls, threads, diag_t, k)
+                    checked += 1
+    assert checked >= 20
+    b.status()
 
 
 def test_batch_fp64_against_oracle(ora):
