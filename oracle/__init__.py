@@ -78,6 +78,7 @@ def lib():
         L.ora_plate_geometry.argtypes = [C.POINTER(Params), _D, _D]
         L.ora_glider_rhs.argtypes = [C.POINTER(Params), _D, C.c_double, C.c_double, C.c_double,
                                      C.c_double, _D]
+        L.ora_plate_loads.argtypes = [C.POINTER(Params), _D, _D, _D, C.c_int, _D, _D]
         L.ora_terminal_cost.argtypes = [C.POINTER(Params), _D]
         L.ora_terminal_cost.restype = C.c_double
         L.ora_step.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_int), _D, _D, _D, _D, _D,
@@ -162,6 +163,17 @@ def plate_geometry(params: dict, xg):
     d["b"] = np.stack([out[k:k + nb], out[k + nb:k + 2 * nb]], axis=1); k += 2 * nb
     d["lev"] = out[k:k + 2].copy(); d["tev"] = out[k + 2:k + 4].copy()
     return d
+
+
+def plate_loads(params: dict, xg, gamma_s, gb_prev, has_prev: int, vtilde):
+    """Wing load and moment (F_w,x, F_w,z, M_w) of Eqs. 13-15 from given surface circulations
+    (N_b bound, Gamma_LEV, Gamma_TEV), previous bound circulations and plate-point relative
+    velocities (N_b + 1 collocation points, then N_b bound points, as (u, w) rows)."""
+    fm = np.zeros(3)
+    P = make_params(params)
+    lib().ora_plate_loads(C.byref(P), _f64(xg), _f64(gamma_s), _f64(gb_prev), int(has_prev),
+                          _f64(np.asarray(vtilde).reshape(-1)), fm)
+    return fm
 
 
 def glider_rhs(params: dict, xg, fw, mw, u):

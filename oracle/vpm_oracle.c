@@ -254,6 +254,49 @@ static void relative_velocity(const ora_params *p, const ora_geom *G, int n, con
     *w = ww + p->u_inf_z - G->vz - G->omega * ez;
 }
 
+/* ------------------------------------------------------------------ pressure and loads */
+
+/* Pressure jump of Eq. 13 on each panel and the wing load and moment of Eqs. 14-15, from the
+ * surface circulations gs (n_b bound, then Gamma_LEV, Gamma_TEV; 0 for an edge that shed
+ * nothing), the previous step's bound circulations gb_prev (has_prev = 0 on the first step)
+ * and the relative velocity (vbx, vbz) at the bound points (Eq. 12). fm = (F_w,x, F_w,z, M_w). */
+static void plate_loads(const ora_params *p, const ora_geom *G, const double *gs,
+                        const double *gb_prev, int has_prev, const double *vbx, const double *vbz,
+                        double *fm)
+{
+    int nb = p->n_b;
+    double dt = p->dt;
+    double fwx = 0.0, fwz = 0.0, mw = 0.0;
+    double cum = 0.0, cum_prev = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        cum += gs[i];
+        cum_prev += gb_prev[i];
+        double tang = (gs[i] / G->lb) * (vbx[i] * G->tx + vbz[i] * G->tz);
+        double dsum = has_prev ? (cum - cum_prev) / dt : 0.0;
+        double dlev = has_prev ? gs[nb] / dt : 0.0;     /* the new LEV's circulation over dt */
+        double dp = p->rho * (tang + dsum + dlev);
+        double fx = G->lb * p->span * dp * G->nx, fz = G->lb * p->span * dp * G->nz;
+        fwx += fx;
+        fwz += fz;
+        double ax = G->bx[i] - G->xw, az = G->bz[i] - G->zw;
+        mw += ax * fz - az * fx;
+    }
+    fm[0] = fwx; fm[1] = fwz; fm[2] = mw;
+}
+
+/* The loads above for glider state xg, with vt the relative velocities at the plate points as
+ * ora_step writes them (N_b + 1 collocation points, then N_b bound points, as (u, w) pairs). */
+void ora_plate_loads(const ora_params *p, const double *xg, const double *gs,
+                     const double *gb_prev, int has_prev, const double *vt, double *fm)
+{
+    ora_geom G;
+    plate_geometry(p, xg, &G);
+    int nb = p->n_b, nc = p->n_b + 1;
+    double vbx[ORA_MAXB], vbz[ORA_MAXB];
+    for (int j = 0; j < nb; ++j) { vbx[j] = vt[2 * (nc + j)]; vbz[j] = vt[2 * (nc + j) + 1]; }
+    plate_loads(p, &G, gs, gb_prev, has_prev, vbx, vbz, fm);
+}
+
 /* ------------------------------------------------------------------ dense LU solve */
 
 /* Solves A y = b in place (b <- y) by Gaussian elimination with partial pivoting. A is
@@ -485,21 +528,9 @@ static int step_impl(const ora_params *p, int capacity, int *n_io, double *x, do
 
     /* unsteady Bernoulli pressure jump (Eq. 13) and wing loads (Eqs. 14-15) */
     double dt = p->dt;
-    double fwx = 0.0, fwz = 0.0, mw = 0.0;
-    double cum = 0.0, cum_prev = 0.0;
-    for (int i = 0; i < nb; ++i) {
-        cum += gs[i];
-        cum_prev += gb_prev[i];
-        double tang = (gs[i] / G.lb) * (vbx[i] * G.tx + vbz[i] * G.tz);
-        double dsum = *has_prev ? (cum - cum_prev) / dt : 0.0;
-        double dlev = *has_prev ? gs[nb] / dt : 0.0;     /* the new LEV's circulation over dt */
-        double dp = p->rho * (tang + dsum + dlev);
-        double fx = G.lb * p->span * dp * G.nx, fz = G.lb * p->span * dp * G.nz;
-        fwx += fx;
-        fwz += fz;
-        double ax = G.bx[i] - G.xw, az = G.bz[i] - G.zw;
-        mw += ax * fz - az * fx;
-    }
+    double fm[3];
+    plate_loads(p, &G, gs, gb_prev, *has_prev, vbx, vbz, fm);
+    double fwx = fm[0], fwz = fm[1], mw = fm[2];
     if (out_fm) { out_fm[0] = fwx; out_fm[1] = fwz; out_fm[2] = mw; }
 
     /* W <- W u E (LEV first, then TEV) */

@@ -61,6 +61,7 @@ def test_step_parity(ora, case, precision):
     tol = VEL_TOL if precision == V.FP32 else 1e-11
     for k, snap, u in snaps:
         o = oracle_state(ora, params, snap, cap)
+        xg_before, gb_before, hp_before = o.xg.copy(), o.gb_prev.copy(), o.has_prev
         ref = o.step(u)
         g = gpu_state(V, params, snap, cap, precision)
         out = g.step(u, probe=True)
@@ -77,6 +78,15 @@ def test_step_parity(ora, case, precision):
         # circulation error by dt
         f_scale = max(1.0, np.abs(ref["fm"]).max())
         assert np.abs(fm - ref["fm"]).max() <= (tol / p_dt(params)) * f_scale, msg
+        # the oracle's Eqs. 13-15 applied to the kernel's own surface circulations and plate
+        # velocities: both sides form the loads in binary64 from identical inputs, so they agree
+        # to rounding (relative to the size of the panel terms, whose difference quotients
+        # divide Gamma by dt), and a wrong term, sign or running-sum order in the kernel's
+        # pressure, load or moment fails here in either precision
+        fm_same = ora.plate_loads(params, xg_before, gs, gb_before, hp_before, vt)
+        term = params["rho"] * params["span"] * params["chord"] * (
+            np.abs(gs).sum() / p_dt(params) + np.abs(gs).sum() * np.abs(vt).max())
+        assert np.abs(fm - fm_same).max() <= 1e-12 * max(1.0, term, np.abs(fm_same).max()), msg
         assert normwise(vel, ref["vel"]) <= tol, msg
         parts_g, xg_g, hist_g = g.read()
         assert len(parts_g) == o.n, msg

@@ -182,3 +182,18 @@ def test_merge_position_is_mean(ora):
     assert s.n == 3
     assert np.allclose(s.particles[0, :2], moved.mean(0), atol=1e-15)
     assert s.particles[0, 2] == pytest.approx(0.3, abs=1e-15)
+
+
+def test_plate_loads_entry_is_the_steps_own(ora):
+    """ora_plate_loads (the loads of Eqs. 13-15 from given circulations and plate velocities,
+    which the GPU step test feeds with the kernel's own values) returns exactly the loads the
+    oracle's step forms, on first and later steps, with both edges shedding and with gating."""
+    for params, seed in ((W.glider_params(), 0), (W.glider_params(shed_gate=2), 1)):
+        s = ora.State(params, W.background_field(seed, 200), np.array(W.GLIDER_X0), 260)
+        rng = np.random.default_rng(seed)
+        for k in range(6):
+            xg, gb, hp = s.xg.copy(), s.gb_prev.copy(), s.has_prev
+            out = s.step(float(rng.normal(0.0, 3.0)))
+            fm = ora.plate_loads(params, xg, out["gamma_s"], gb, hp, out["vtilde"])
+            assert np.array_equal(fm, out["fm"]), (seed, k)
+            assert k == 0 or np.abs(fm).max() > 0
