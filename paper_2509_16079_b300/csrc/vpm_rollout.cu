@@ -417,11 +417,33 @@ constexpr int kSrcUnroll = VPM_SRC_UNROLL;
                               // half as many with two blocks per round)
 #endif
 constexpr int kRotUnroll = VPM_ROT_UNROLL, kRotUnroll2 = VPM_ROT_UNROLL / 2;
-constexpr int kRow = 128;     // targets of an off-diagonal row (4 per lane)
-#ifndef VPM_DIAG_T
-#define VPM_DIAG_T 2          // targets per lane of a diagonal group (1, 2 or 4)
+#ifndef VPM_DIAG_UNROLL
+#define VPM_DIAG_UNROLL 2     // rounds in flight per iteration of the diagonal unit's block pairs
 #endif
-constexpr int kDiagT = VPM_DIAG_T, kDiagGroup = 32 * kDiagT;
+#ifndef VPM_DIAG_SELF_UNROLL
+#define VPM_DIAG_SELF_UNROLL 3   // and of its in-block rounds (15 of them before the last)
+#endif
+constexpr int kDiagUnroll = VPM_DIAG_UNROLL, kDiagSelfUnroll = VPM_DIAG_SELF_UNROLL;
+constexpr int kRow = 128;     // targets of an off-diagonal row (4 per lane)
+// Diagonal units (the pairs among a 128-particle row's own particles). A step with at least
+// kDiagPairMin old particles evaluates each such pair once for both particles, one unit per row;
+// smaller steps evaluate every pair once per target in groups of 32 DT targets (DT = 1, 2 or 4,
+// which give the same bits: each target's sum runs over the row's sources in order). The form
+// depends on the particle count alone, so a rollout's result does not depend on the launch
+// (block size, DT, batch schedule). Measured with the MPPI batch: fields of 1000-1200 particles
+// on 128-thread blocks (72 registers, 7 blocks per SM) run faster with groups of 64 targets,
+// fields of 1900-2100 on 256-thread blocks 3 % faster with the once-per-pair units.
+#ifndef VPM_DIAG_T
+#define VPM_DIAG_T 2          // targets per lane of a per-target diagonal group (1, 2 or 4)
+#endif
+#ifndef VPM_DIAG_PAIR_MIN
+#define VPM_DIAG_PAIR_MIN 1300
+#endif
+constexpr int kDiagT = VPM_DIAG_T, kDiagPairMin = VPM_DIAG_PAIR_MIN;
+// PD (a template flag of the binary32 kernels): the once-per-pair diagonal units are compiled in.
+// A launch whose capacity is below kDiagPairMin never needs them (n <= capacity), and leaving
+// them out of the 128-thread kernels keeps their row loop's code as fast as without them
+// (measured: 4 % on the MPPI batch).
 
 
 // Sources s0 .. s1-1; targets base + lane + 32 k below lim.
@@ -626,25 +648,150 @@ __device__ void offdiag_row(const DevParams &p, const float4 *part, float2 *scr,
     fold_row(kst, a, fu, fw, first);
 }
 
+// One pair of 32-particle blocks of a row's diagonal unit: targets (tx, tz, tg) of block k on
+// this lane against source s, forward terms into (fu, fw), reverse terms into the source's
+// running sum (ru, rw).
+template <int KER>
+__device__ __forceinline__ void diag_pair(float rc4s, float irc2, float tx, float tz, float tg,
+                                          const float4 &s, float &fu, float &fw, float &ru, float &rw)
+{
+    const float dx = tx - s.x, dz = tz - s.y;
+    const float q = PairF32<KER>::q(fmaf(dx, dx, dz * dz), rc4s, irc2);
+    const float gs = s.z * q, gt = tg * q;
+    fu = fmaf(-dz, gs, fu);
+    fw = fmaf(dx, gs, fw);
+    ru = fmaf(dz, gt, ru);
+    rw = fmaf(-dx, gt, rw);
+}
+
+// Diagonal unit of row g with each pair of the row's own particles evaluated once for both
+// particles (steps with at least kDiagPairMin particles). Lane l holds particles r0 + 32 k + l of the row's four
+// 32-particle blocks k = 0..3 (4 targets per lane, as in offdiag_row). The pairs between blocks
+// k < b rotate block b's sources through the lanes as the off-diagonal rows do, with one running
+// sum per later block (three); the pairs within a block rotate the block's own sources over 16
+// rounds, the 16th on lanes 0-15 only, so that lane l meets l + 16 once. Each particle's diagonal
+// sum (its forward terms over both phases, its block's reverse terms, then the reverse terms of
+// the earlier blocks, parked in vel) is formed by this warp in a fixed order and written raw to
+// vel. FULL: all kRow particles of the row exist; otherwise the missing ones take part with zero
+// circulation at a clamped position and nothing is written for them.
+template <int KER, bool FULL>
+__device__ void diag_row_pairs(const DevParams &p, const float4 *part, float2 *vel, int n, int g)
+{
+    const int lane = threadIdx.x & 31;
+    const int r0 = kRow * g;
+    const int nsb = FULL ? 4 : (min(kRow, n - r0) + 31) >> 5;
+    const float rc4s = (float)p.rc4, irc2 = (float)p.inv_rc2;
+    float tx[4], tz[4], tg[4], fu[4], fw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = r0 + 32 * k + lane;
+        const float4 q = part[FULL ? i : min(i, n - 1)];
+        tx[k] = q.x;
+        tz[k] = q.y;
+        tg[k] = (FULL || i < n) ? q.z : 0.f;
+        fu[k] = fw[k] = 0.f;
+    }
+    if (nsb > 1) {
+        // blocks b = 1..3 against the targets of the blocks before them
+        float ru[3] = {0.f, 0.f, 0.f}, rw[3] = {0.f, 0.f, 0.f};
+#pragma unroll kDiagUnroll
+        for (int r = 0; r < 32; ++r) {
+            const int jl = (lane + r) & 31;
+#pragma unroll
+            for (int b = 1; b < 4; ++b) {
+                if (!FULL && b >= nsb) continue;
+                const int j = r0 + 32 * b + jl;
+                float4 s = part[FULL ? j : min(j, n - 1)];
+                if (!FULL && j >= n) s.z = 0.f;
+#pragma unroll
+                for (int k = 0; k < b; ++k)
+                    diag_pair<KER>(rc4s, irc2, tx[k], tz[k], tg[k], s, fu[k], fw[k], ru[b - 1], rw[b - 1]);
+            }
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                ru[b] = __shfl_sync(0xffffffffu, ru[b], (lane + 1) & 31);
+                rw[b] = __shfl_sync(0xffffffffu, rw[b], (lane + 1) & 31);
+            }
+        }
+        // lane l now holds the reverse sums of particles r0 + 32 b + l; park them in vel
+#pragma unroll
+        for (int b = 1; b < 4; ++b) {
+            const int i = r0 + 32 * b + lane;
+            if (FULL || i < n) vel[i] = make_float2(ru[b - 1], rw[b - 1]);
+        }
+    }
+    // each block with itself: rounds 1..15 on every lane, then round 16 on lanes 0-15
+    float su[4] = {0.f, 0.f, 0.f, 0.f}, sw[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll kDiagSelfUnroll
+    for (int r = 1; r < 16; ++r) {
+        const int jl = (lane + r) & 31;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!FULL && k >= nsb) continue;
+            const int j = r0 + 32 * k + jl;
+            float4 s = part[FULL ? j : min(j, n - 1)];
+            if (!FULL && j >= n) s.z = 0.f;
+            diag_pair<KER>(rc4s, irc2, tx[k], tz[k], tg[k], s, fu[k], fw[k], su[k], sw[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            su[k] = __shfl_sync(0xffffffffu, su[k], (lane + 1) & 31);
+            sw[k] = __shfl_sync(0xffffffffu, sw[k], (lane + 1) & 31);
+        }
+    }
+    {
+        const bool on = lane < 16;
+        const int jl = (lane + 16) & 31;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!FULL && k >= nsb) continue;
+            const int j = r0 + 32 * k + jl;
+            float4 s = part[FULL ? j : min(j, n - 1)];
+            if ((!FULL && j >= n) || !on) s.z = 0.f;
+            diag_pair<KER>(rc4s, irc2, tx[k], tz[k], on ? tg[k] : 0.f, s, fu[k], fw[k], su[k], sw[k]);
+        }
+    }
+    // lane l holds the in-block reverse sum of particle (l + 16) mod 32 of each block
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        su[k] = __shfl_xor_sync(0xffffffffu, su[k], 16);
+        sw[k] = __shfl_xor_sync(0xffffffffu, sw[k], 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = r0 + 32 * k + lane;
+        if (!(FULL || i < n)) continue;
+        float vx = fu[k] + su[k], vz = fw[k] + sw[k];
+        if (k > 0) {
+            const float2 c = vel[i];
+            vx += c.x;
+            vz += c.y;
+        }
+        vel[i] = make_float2(vx, vz);
+    }
+}
+
 struct PairPlan {
     int rows_off;   // off-diagonal rows (units 0 .. rows_off - 1, longest first)
-    int nunits;     // then the diagonal groups of 32 DT targets
+    int nunits;     // then the diagonal units: one per row (pair_diag) or groups of 32 DT targets
+    bool pair_diag; // n >= kDiagPairMin: each pair of a row's own particles once
 };
 
-template <int DT = kDiagT>
+template <int DT = kDiagT, bool PD = false>
 __device__ __forceinline__ PairPlan pair_plan(int n)
 {
     PairPlan c;
     const int rows = (n + kRow - 1) / kRow;
     c.rows_off = rows > 1 ? rows - 1 : 0;
-    c.nunits = c.rows_off + (n + 32 * DT - 1) / (32 * DT);
+    c.pair_diag = PD && n >= kDiagPairMin;
+    c.nunits = c.rows_off + (c.pair_diag ? rows : (n + 32 * DT - 1) / (32 * DT));
     return c;
 }
 
 // Units are claimed from a counter that is never reset within a rollout: every warp makes
 // exactly one failing claim per step, so a step consumes nunits + nwarps claims and every
 // thread can track the counter's base for the next step without a barrier.
-template <int KER, int DT = kDiagT>
+template <int KER, int DT = kDiagT, bool PD = false>
 __device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, float2 *vel,
                               float2 *scr, int cap32, int n, const PairPlan &pp, int claim_base)
 {
@@ -656,6 +803,12 @@ __device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, f
         if (c >= pp.nunits) break;
         if (c < pp.rows_off) {
             offdiag_row<KER>(p, part, scr, cap32, n, c);
+        } else if (PD && pp.pair_diag) {
+            if constexpr (PD) {
+                const int g = c - pp.rows_off;
+                if (kRow * (g + 1) <= n) diag_row_pairs<KER, true>(p, part, vel, n, g);
+                else diag_row_pairs<KER, false>(p, part, vel, n, g);
+            }
         } else {
             const int g = c - pp.rows_off, t0 = 32 * DT * g, r0 = (t0 / kRow) * kRow;
             old_pairs_chunk<KER, DT>(p, part, vel, r0, min(r0 + kRow, n), t0, n);
@@ -988,7 +1141,7 @@ __device__ __forceinline__ int plate_warp()
 
 // One full step of one rollout. All threads call it with the same particle count n (updated
 // here) and unit-claim base; returns with the block synchronised.
-template <class R, int KER, int DT = kDiagT>
+template <class R, int KER, int DT = kDiagT, bool PD = false>
 __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *part,
                           typename Store<R>::V *vel, double u_ctrl, const RolloutArgs &a,
                           bool probe, int &n, int &claim_base)
@@ -1010,7 +1163,7 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
             if (lane == 0) w.n = m;
             fresh_velocities_f32<KER>(p, w, part, n, m);
         }
-        const PairPlan pp = pair_plan<DT>(n);
+        const PairPlan pp = pair_plan<DT, PD>(n);
         const int cap32 = (a.cap + 31) & ~31;
         float2 *scr = a.rev ? a.rev + (size_t)blockIdx.x * a.rev_stride : nullptr;
 #if VPM_DEBUG_BOUNDS
@@ -1020,7 +1173,7 @@ __device__ void step_once(const DevParams &p, Work &w, typename Store<R>::P *par
             return;
         }
 #endif
-        old_pairs_f32<KER, DT>(p, w, part, vel, scr, cap32, n, pp, claim_base);
+        old_pairs_f32<KER, DT, PD>(p, w, part, vel, scr, cap32, n, pp, claim_base);
         claim_base += pp.nunits + (int)(blockDim.x >> 5);
         __syncthreads();
         n1 = w.n;
@@ -1182,7 +1335,7 @@ __device__ void pace_step(const RolloutArgs &a, unsigned sm, int slot, int k)
 }
 
 // One rollout of a.H steps by the whole block, field resident in shared memory.
-template <class R, int KER, int DT = kDiagT>
+template <class R, int KER, int DT = kDiagT, bool PD = false>
 __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P *part,
                             typename Store<R>::V *vel, int rid)
 {
@@ -1209,7 +1362,7 @@ __device__ void run_rollout(const RolloutArgs &a, Work &w, typename Store<R>::P 
                 fb -= a.pol_gains[j * 7 + c] * (w.xg[c] - a.pol_xbar[j * 7 + c]);
             u = (a.controls ? u : 0.0) + fb;
         }
-        step_once<R, KER, DT>(a.p, w, part, vel, u, a, a.H == 1, n, claim_base);
+        step_once<R, KER, DT, PD>(a.p, w, part, vel, u, a, a.H == 1, n, claim_base);
         if (a.traj && threadIdx.x < 7)
             a.traj[((size_t)rid * a.H + k) * 7 + threadIdx.x] = w.xg[threadIdx.x];
     }
@@ -1234,7 +1387,7 @@ __host__ __device__ constexpr int min_blocks_for(int nt)
 }
 
 // K rollouts (blockIdx.x + rid0 = rollout), H steps each.
-template <class R, int KER, int NT>
+template <class R, int KER, int NT, bool PD>
 __global__ void __launch_bounds__(NT, min_blocks_for(NT)) rollout_kernel(const RolloutArgs a)
 {
     using P = typename Store<R>::P;
@@ -1243,12 +1396,12 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) rollout_kernel(const R
     P *part = reinterpret_cast<P *>(smem);
     V *vel = reinterpret_cast<V *>(smem + sizeof(P) * (size_t)a.cap);
     __shared__ Work w;
-    run_rollout<R, KER>(a, w, part, vel, blockIdx.x + a.rid0);
+    run_rollout<R, KER, kDiagT, PD>(a, w, part, vel, blockIdx.x + a.rid0);
 }
 
 // Persistent form for batches of uneven rollouts: each block claims the next rollout of
 // a.order until all a.n_items are done. Which block runs a rollout does not change its result.
-template <class R, int KER, int NT, int DT = kDiagT>
+template <class R, int KER, int NT, int DT = kDiagT, bool PD = true>
 __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const RolloutArgs a)
 {
     using P = typename Store<R>::P;
@@ -1264,7 +1417,7 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const Ro
         const int q = s_item;
         __syncthreads();
         if (q >= a.n_items) break;
-        run_rollout<R, KER, DT>(a, w, part, vel, a.order[q]);
+        run_rollout<R, KER, DT, PD>(a, w, part, vel, a.order[q]);
     }
 }
 
@@ -1288,10 +1441,10 @@ static cudaError_t grant_smem(F k, std::atomic<size_t> &granted, size_t smem)
     return cudaSuccess;
 }
 
-template <class R, int KER, int NT>
+template <class R, int KER, int NT, bool PD = true>
 static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    auto k = rollout_kernel<R, KER, NT>;
+    auto k = rollout_kernel<R, KER, NT, PD>;
     // raise the kernel's dynamic shared-memory limit once per size increase (per process;
     // the library runs on one device per process)
     static std::atomic<size_t> granted{0};
@@ -1341,7 +1494,8 @@ static cudaError_t launch_f32(const RolloutArgs &a, int grid, size_t smem, cudaS
 {
     if (a.cap > 3000) return launch_t<float, KER, 512>(a, grid, smem, s);
     if (a.cap > 1300) return launch_t<float, KER, 256>(a, grid, smem, s);
-    return launch_t<float, KER, 128>(a, grid, smem, s);
+    if (a.cap >= kDiagPairMin) return launch_t<float, KER, 128, true>(a, grid, smem, s);
+    return launch_t<float, KER, 128, false>(a, grid, smem, s);
 }
 
 long long rollout_rev_slots(int precision, int cap)
@@ -1456,10 +1610,10 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
     });
 }
 
-template <class R, int KER, int NT, int DT = kDiagT>
+template <class R, int KER, int NT, int DT = kDiagT, bool PD = true>
 static cudaError_t launch_u(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    auto k = uneven_kernel<R, KER, NT, DT>;
+    auto k = uneven_kernel<R, KER, NT, DT, PD>;
     static std::atomic<size_t> granted{0};
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
@@ -1479,15 +1633,18 @@ static cudaError_t launch_u_nt(const RolloutArgs &a, int grid, int nt, int dt, s
     if (KER == VPM_KERNEL_VATISTAS && dt == 1) {
         if (nt == 512) return launch_u<R, KER, 512, 1>(a, grid, smem, s);
         if (nt == 256) return launch_u<R, KER, 256, 1>(a, grid, smem, s);
+        if (a.cap < kDiagPairMin) return launch_u<R, KER, 128, 1, false>(a, grid, smem, s);
         return launch_u<R, KER, 128, 1>(a, grid, smem, s);
     }
     if (KER == VPM_KERNEL_VATISTAS && dt == 4) {
         if (nt == 512) return launch_u<R, KER, 512, 4>(a, grid, smem, s);
         if (nt == 256) return launch_u<R, KER, 256, 4>(a, grid, smem, s);
+        if (a.cap < kDiagPairMin) return launch_u<R, KER, 128, 4, false>(a, grid, smem, s);
         return launch_u<R, KER, 128, 4>(a, grid, smem, s);
     }
     if (nt == 512) return launch_u<R, KER, 512>(a, grid, smem, s);
     if (nt == 256) return launch_u<R, KER, 256>(a, grid, smem, s);
+    if (a.cap < kDiagPairMin) return launch_u<R, KER, 128, kDiagT, false>(a, grid, smem, s);
     return launch_u<R, KER, 128>(a, grid, smem, s);
 }
 

@@ -110,8 +110,12 @@ def p_dt(params):
 
 # Wake sizes at the edges of the binary32 pair phase: its rows of 128 particles (one pair
 # evaluation serves both particles across rows), diagonal groups of 64 targets and source
-# blocks of 32 (the last one ragged).
-ROW_EDGES = [1, 31, 63, 64, 65, 127, 128, 129, 191, 255, 256, 257, 383, 449]
+# blocks of 32 (the last one ragged). From 1300 particles on, the row's own pairs are evaluated
+# once for both particles too: each size is stepped at n and n + 2, which puts 1298 on both
+# sides of that threshold and the others at a last row of 128 (1408), 1 (1409), 32 (1440),
+# 33 (1441), 65 (1473) and 97 (1505) particles, i.e. full, empty-tailed and ragged 32-blocks.
+ROW_EDGES = [1, 31, 63, 64, 65, 127, 128, 129, 191, 255, 256, 257, 383, 449,
+             1298, 1406, 1407, 1438, 1439, 1471, 1503]
 
 
 @pytest.mark.parametrize("n", ROW_EDGES)
