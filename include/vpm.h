@@ -208,6 +208,15 @@ vpm_status vpm_rollout_scratch_bytes(const vpm_state *state, int K, int H, size_
  * capacity < 0, unknown precision). */
 vpm_status vpm_rollout_scratch_bytes_cap(int precision, int capacity, int K, size_t *bytes);
 
+/* The binary32 rollout kernel's own scratch index (host only; the paper has no counterpart: it
+ * serves checks of the scratch layout). For a block whose fields can reach `capacity` particles,
+ * in float2 slots from the block's scratch start: kind 0 gives the first of the two slots that
+ * hold the compensated forward sum of target `particle` (a particle of an off-diagonal row,
+ * particle < 128 (ceil(capacity / 128) - 1)); kind 1 gives the slot of the reverse sum of source
+ * `particle` over the targets of off-diagonal row `row` (particle >= 128 (row + 1)). The rows
+ * are the 128-particle rows of the pair phase. Errors: VPM_ERR_INVALID (null, or no such slot). */
+vpm_status vpm_rollout_scratch_slot(int capacity, int kind, int row, int particle, long long *slot);
+
 /*
  * K independent rollouts of H steps from the root model, which is not modified. Rollout i
  * applies elevator rates d_controls[i*H + k] (binary32, K x H row-major). One thread block

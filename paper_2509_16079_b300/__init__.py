@@ -80,6 +80,7 @@ _SIGNATURES = {
     "vpm_rollout_batch": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_rollout_scratch_bytes": ([_VP, _I, _I, C.POINTER(C.c_size_t)], _I),
     "vpm_rollout_scratch_bytes_cap": ([_I, _I, _I, C.POINTER(C.c_size_t)], _I),
+    "vpm_rollout_scratch_slot": ([_I, _I, _I, _I, C.POINTER(C.c_longlong)], _I),
     "vpm_rollout_batch_x0": ([_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "vpm_state_set_glider": ([_VP, _VP, _VP], _I),
     "vpm_state_inject_pair": ([_VP, _VP, _VP], _I),

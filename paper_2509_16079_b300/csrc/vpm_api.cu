@@ -602,6 +602,18 @@ extern "C" vpm_status vpm_rollout_scratch_bytes_cap(int precision, int capacity,
     return VPM_OK;
 }
 
+extern "C" vpm_status vpm_rollout_scratch_slot(int capacity, int kind, int row, int particle,
+                                               long long *slot)
+{
+    const int rows = (capacity + 127) / 128;
+    const bool ok = slot && capacity > 0 && particle >= 0 && particle < capacity &&
+                    ((kind == 0 && particle < 128 * (rows - 1)) ||
+                     (kind == 1 && row >= 0 && row < rows - 1 && particle >= 128 * (row + 1)));
+    if (!ok) return fail(VPM_ERR_INVALID, "vpm_rollout_scratch_slot: no such slot");
+    *slot = rollout_scratch_slot(capacity, kind, row, particle);
+    return VPM_OK;
+}
+
 extern "C" vpm_status vpm_rollout_scratch_bytes(const vpm_state *s, int K, int H, size_t *bytes)
 {
     if (!s || !bytes || K < 1 || H < 1) return fail(VPM_ERR_INVALID, "vpm_rollout_scratch_bytes: null or K, H < 1");

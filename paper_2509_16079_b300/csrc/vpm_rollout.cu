@@ -501,6 +501,14 @@ __host__ __device__ inline long long rev_row_base(int a, int cap32)
     return (long long)cap32 * (a + 2) - (long long)(kRow / 2) * a * (a + 1);
 }
 
+// Slot of the reverse sum of source j (kRow (a + 1) <= j < cap) over the targets of row a, and
+// the float4 index of target i's compensated forward sum (float2 slots 2 i and 2 i + 1).
+__host__ __device__ inline long long rev_slot(int a, int j, int cap32)
+{
+    return rev_row_base(a, cap32) - (long long)kRow * (a + 1) + j;
+}
+__host__ __device__ inline int fwd_index(int i) { return i; }
+
 __host__ __device__ inline long long rev_slots(int cap)
 {
     if (cap <= kRow) return 0;                 // a single row: no off-diagonal work
@@ -553,10 +561,10 @@ __device__ __forceinline__ void fold_row(float4 *kst, int a, float (&fu)[4], flo
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        float4 st = first ? make_float4(0.f, 0.f, 0.f, 0.f) : kst[kRow * a + 32 * k + lane];
+        float4 st = first ? make_float4(0.f, 0.f, 0.f, 0.f) : kst[fwd_index(kRow * a + 32 * k + lane)];
         kahan_add(st.x, st.z, fu[k]);
         kahan_add(st.y, st.w, fw[k]);
-        kst[kRow * a + 32 * k + lane] = st;
+        kst[fwd_index(kRow * a + 32 * k + lane)] = st;
         fu[k] = fw[k] = 0.f;
     }
 }
@@ -623,7 +631,7 @@ __device__ void offdiag_row(const DevParams &p, const float4 *part, float2 *scr,
         fu[k] = fw[k] = 0.f;
     }
     float4 *kst = reinterpret_cast<float4 *>(scr);
-    float2 *rrow = scr + (rev_row_base(a, cap32) - (long long)kRow * (a + 1));   // by source index
+    float2 *rrow = scr + rev_slot(a, 0, cap32);   // by source index
     int b0 = kRow * (a + 1);                   // a multiple of 64: fold after every two blocks
     bool first = true;
     for (; b0 + 64 <= n; b0 += 64) {
@@ -826,12 +834,12 @@ __device__ __forceinline__ float2 old_sum(const float2 *vel, const float2 *scr, 
     if (row == 0 && rows_off == 0) return v;
     float cu = 0.f, cw = 0.f;
     if (row < rows_off) {
-        const float4 f = reinterpret_cast<const float4 *>(scr)[i];
+        const float4 f = reinterpret_cast<const float4 *>(scr)[fwd_index(i)];
         kahan_add(v.x, cu, f.x - f.z);
         kahan_add(v.y, cw, f.y - f.w);
     }
     for (int a = 0; a < row; ++a) {
-        const float2 r = scr[rev_row_base(a, cap32) + i - (long long)kRow * (a + 1)];
+        const float2 r = scr[rev_slot(a, i, cap32)];
         kahan_add(v.x, cu, r.x);
         kahan_add(v.y, cw, r.y);
     }
@@ -1501,6 +1509,11 @@ static cudaError_t launch_f32(const RolloutArgs &a, int grid, size_t smem, cudaS
 long long rollout_rev_slots(int precision, int cap)
 {
     return precision == VPM_FP64 ? 0 : rev_slots(cap);
+}
+
+long long rollout_scratch_slot(int cap, int kind, int row, int particle)
+{
+    return kind == 0 ? 2LL * fwd_index(particle) : rev_slot(row, particle, (cap + 31) & ~31);
 }
 
 // The library's own memory pool, one per device, for the stream-ordered scratch of its launches.

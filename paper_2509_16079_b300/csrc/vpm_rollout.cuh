@@ -74,6 +74,9 @@ size_t lib_pool_idle_bytes();
 // float2 slots of pair-sum scratch one block of the binary32 path needs for capacity cap
 // (0: none; the binary64 path needs none).
 long long rollout_rev_slots(int precision, int cap);
+// Scratch slot (float2 units) of a binary32 block with capacity cap: kind 0 = the first of the
+// two slots of target `particle`'s forward sum; kind 1 = source `particle`'s reverse sum over row `row`.
+long long rollout_scratch_slot(int cap, int kind, int row, int particle);
 cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaStream_t s);
 // Persistent launch over a.n_items rollouts with `nt` threads per block (128, 256 or 512; the
 // binary64 path uses 128) and diagonal pair units of 32 dt targets (dt = 1, 2 or 4: every
