@@ -460,6 +460,16 @@ def run_gpu(args):
             northstar = northstar_replans(V, torch, args.n0, args.northstar_replans, args.per_launch_subset)
         northstar["clocks"] = clk_ns.summary()
 
+    serving = None
+    if args.serve_line_seconds > 0 and world == 1:
+        with ClockSampler(local) as clk_sv:
+            serving = serving_at_rates(V, args.serve_line_rates, args.serve_line_seconds)
+        serving = {"workload": "16 scenarios of 500-5000 resident particles, K in {256, 1024, 4096}, "
+                               "H=100, Poisson arrivals; continuous batching (16 in flight) against the "
+                               "plain per-request form (1 in flight) on the same trace",
+                   "seconds_of_arrivals": args.serve_line_seconds, "runs": serving,
+                   "clocks": clk_sv.summary()}
+
     if rank != 0:
         return
     clocks = clk.summary()
@@ -504,6 +514,8 @@ def run_gpu(args):
     }
     if northstar is not None:
         line["northstar_replan_ms"] = northstar
+    if serving is not None:
+        line["serving"] = serving
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"], line["error_vs_fp64_oracle"] = cpu_baseline(V=V)
     print(json.dumps(line), flush=True)
@@ -893,7 +905,11 @@ def northstar_replans(V, torch, n0: int, replans: int, per_launch_subset: int):
         "workload": "K=1024 x H=100, fields %d -> %d particles, 3 MPPI iterations per replan" % (n0, n0 + 2 * Hh),
         "persistent": {"p50": p50, "p99": float(np.percentile(lat, 99)), "replans": len(lat),
                        "pairs_per_s": 3 * pairs_iter / (p50 / 1e3), "form": "eager launches",
-                       "l2": "flushed between replans"},
+                       "l2": "flushed between replans",
+                       # 12 flops per pair interaction over the whole replan (the MPPI kernels
+                       # between the rollout launches included), against the derived FP32 peak
+                       "fp32_frac_of_replan": 3 * pairs_iter * FLOPS_PER_PAIR / (p50 / 1e3) / 1e12
+                       / fp32_peak_tflops()},
         "persistent_graph": graph,
         "one_rollout_per_launch": {"replan_ms_scaled": 3 * per_launch_iter_ms,
                                    "timed_rollouts": ks, "scaled_to": K,
@@ -975,6 +991,63 @@ def run_uneven(args):
         "speedup": per_launch_ms / ms, "clocks": clk.summary()}), flush=True)
 
 
+SERVE_H = 100
+
+
+def serving_setup(V):
+    """The serving workload's 16 scenarios (500-5000 particles, merging caps growth at n + 300)
+    and its noise per request size K in {256, 1024, 4096}."""
+    fields = W.serving_scenarios(0)
+    noise = {k: [W.mppi_noise(100 + 7 * j + k, k, SERVE_H, W.MPPI_SIGMA_U) for j in range(3)]
+             for k in (256, 1024, 4096)}
+    return fields, noise
+
+
+def serve_trace(V, fields, noise, arrivals, streams, sizes, slots):
+    """Replays an arrival trace in real time against a server with `slots` requests in flight
+    (16: continuous batching; 1: the plain per-request form). Each request first advances its
+    scenario by 2 steps, then replans with K = sizes[j] rollouts over SERVE_H steps."""
+    srv = V.Server(max_inflight=slots, max_rollouts=4096, max_horizon=SERVE_H)
+    for f in fields:
+        p = W.glider_params(n_wake_max=len(f) + 300)
+        srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 300 + 2 * SERVE_H + 8)
+    tickets, t0 = [], time.perf_counter()
+    for j, (ta, sc) in enumerate(zip(arrivals, streams)):
+        dt = ta - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        k = int(sizes[j])
+        tickets.append(srv.submit(int(sc), noise[k][j % 3], advance_steps=2, advance_u=0.0))
+    lat, done_k, superseded = [], 0, 0
+    for tk in tickets:
+        r = srv.poll(tk)
+        if r[0]["status"] == V.VPM_OK:
+            lat.append(r[0]["t_done_ms"] - r[0]["t_submit_ms"])
+            done_k += r[0]["K"]
+        else:
+            superseded += 1
+    wall = time.perf_counter() - t0
+    srv.close()
+    return {"offered": int(len(arrivals)), "completed": len(lat), "superseded": superseded,
+            "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+            "rollouts_per_s": done_k / wall, "wall_s": wall}
+
+
+def serving_at_rates(V, rates, seconds):
+    """Continuous batching against the per-request form at total request rates around one GPU's
+    capacity (same scenarios, request mix and arrival seeds as the sweep of --workload serving)."""
+    fields, noise = serving_setup(V)
+    out = []
+    for rate in rates:
+        arr, strm = W.poisson_arrivals(11, rate / len(fields), seconds, len(fields))
+        ks = W.request_sizes(12, len(arr))
+        out.append({"offered_hz": rate,
+                    "continuous": serve_trace(V, fields, noise, arr, strm, ks, 16),
+                    "per_request": serve_trace(V, fields, noise, arr, strm, ks, 1)})
+    return out
+
+
 def run_serving(args):
     """Serving: 16 scenarios with resident fields of 500-5000 particles (merging caps growth
     at n + 300), replanning requests arriving as Poisson streams at 50 Hz each, K drawn from
@@ -982,48 +1055,20 @@ def run_serving(args):
     arrival trace is replayed in real time against the continuous-batching server (16 slots)
     and then against the plain per-request form (1 slot). The offered load is far above one
     GPU's capacity, so a newer request for a scenario supersedes its queued one."""
-    import threading as th
     import torch
     import paper_2509_16079_b300 as V
     from paper_2509_16079_b300 import build
     build.build()
-    Hh, T = 100, args.serve_seconds
-    fields = W.serving_scenarios(0)
+    T = args.serve_seconds
+    fields, noise = serving_setup(V)
     arrivals, streams = W.poisson_arrivals(1, 50.0, T, len(fields))
     sizes = W.request_sizes(2, len(arrivals))
-    noise = {k: [W.mppi_noise(100 + 7 * j + k, k, Hh, W.MPPI_SIGMA_U) for j in range(3)]
-             for k in (256, 1024, 4096)}
     out = {"metric": "MPPI replan latency under load", "unit": "ms", "higher_is_better": False,
            "config": {"workload": "serving: 16 scenarios, 500-5000 particles, Poisson 50 Hz each, "
                                   "K in {256, 1024, 4096}, H=100", "seconds": T,
                       "offered_requests": int(len(arrivals))}}
     for label, slots in (("continuous", 16), ("per_request", 1)):
-        srv = V.Server(max_inflight=slots, max_rollouts=4096, max_horizon=Hh)
-        for f in fields:
-            p = W.glider_params(n_wake_max=len(f) + 300)
-            srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 300 + 2 * Hh + 8)
-        tickets = []
-        t0 = time.perf_counter()
-        for j, (ta, sc) in enumerate(zip(arrivals, streams)):
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            k = int(sizes[j])
-            tickets.append(srv.submit(int(sc), noise[k][j % 3], advance_steps=2, advance_u=0.0))
-        lat, done_k, superseded = [], 0, 0
-        for t in tickets:
-            r = srv.poll(t)
-            if r[0]["status"] == V.VPM_OK:
-                lat.append(r[0]["t_done_ms"] - r[0]["t_submit_ms"])
-                done_k += r[0]["K"]
-            else:
-                superseded += 1
-        wall = time.perf_counter() - t0
-        srv.close()
-        out[label] = {"completed": len(lat), "superseded": superseded,
-                      "p50_ms": float(np.percentile(lat, 50)) if lat else None,
-                      "p99_ms": float(np.percentile(lat, 99)) if lat else None,
-                      "rollouts_per_s": done_k / wall, "wall_s": wall}
+        out[label] = serve_trace(V, fields, noise, arrivals, streams, sizes, slots)
     # sustainable-rate sweep: the same scenarios and request mix at total rates around one GPU's
     # capacity (a request averages ~1.7e12 pair interactions, ~0.5 s of the device); a rate is
     # sustained when no request is superseded and the p99 latency stays within twice the p99
@@ -1032,36 +1077,16 @@ def run_serving(args):
     for rate in args.serve_rates:
         arr, strm = W.poisson_arrivals(11, rate / len(fields), args.serve_sweep_seconds, len(fields))
         ks = W.request_sizes(12, len(arr))
-        srv = V.Server(max_inflight=16, max_rollouts=4096, max_horizon=Hh)
-        for f in fields:
-            p = W.glider_params(n_wake_max=len(f) + 300)
-            srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 300 + 2 * Hh + 8)
-        tickets, t0 = [], time.perf_counter()
-        for j, (ta, sc) in enumerate(zip(arr, strm)):
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            k = int(ks[j])
-            tickets.append(srv.submit(int(sc), noise[k][j % 3], advance_steps=2, advance_u=0.0))
-        lat, done_k, sup = [], 0, 0
-        for t in tickets:
-            r = srv.poll(t)
-            if r[0]["status"] == V.VPM_OK:
-                lat.append(r[0]["t_done_ms"] - r[0]["t_submit_ms"])
-                done_k += r[0]["K"]
-            else:
-                sup += 1
-        wall = time.perf_counter() - t0
-        srv.close()
-        p99 = float(np.percentile(lat, 99)) if lat else None
+        r = serve_trace(V, fields, noise, arr, strm, ks, 16)
+        p99 = r["p99_ms"]
         if base_p99 is None:
             base_p99 = p99
-        ok = sup == 0 and p99 is not None and base_p99 is not None and p99 <= 2.0 * base_p99
+        ok = r["superseded"] == 0 and p99 is not None and base_p99 is not None and p99 <= 2.0 * base_p99
         if ok:
             sustained = rate
-        sweep.append({"offered_hz": rate, "offered": int(len(arr)), "completed": len(lat), "superseded": sup,
-                      "p50_ms": float(np.percentile(lat, 50)) if lat else None, "p99_ms": p99,
-                      "rollouts_per_s": done_k / wall, "sustained": ok})
+        sweep.append({"offered_hz": rate, "offered": r["offered"], "completed": r["completed"],
+                      "superseded": r["superseded"], "p50_ms": r["p50_ms"], "p99_ms": p99,
+                      "rollouts_per_s": r["rollouts_per_s"], "sustained": ok})
     out["rate_sweep"] = sweep
     out["sustainable_rate_hz"] = sustained
     print(json.dumps(out), flush=True)
@@ -1131,6 +1156,10 @@ def main():
     ap.add_argument("--northstar-replans", type=int, default=200,
                     help="north-star replans timed in the main line (0: skip)")
     ap.add_argument("--rollouts", type=int, default=K_ROLL)
+    ap.add_argument("--serve-line-seconds", type=float, default=8.0,
+                    help="seconds of arrivals per serving run in the main line (0: skip)")
+    ap.add_argument("--serve-line-rates", type=float, nargs="*", default=[1.5, 4.0],
+                    help="total request rates (Hz) of the main line's serving runs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
