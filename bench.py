@@ -527,10 +527,10 @@ def run_profile_case(args):
     import paper_2509_16079_b300 as V
     from paper_2509_16079_b300 import build
     build.build()
-    K, Hh = args.rollouts, args.horizon
-    p, field, xg0, _ = W.mppi_c2(0, K=1, H=1, n=N0)
+    K, Hh, n0 = args.rollouts, args.horizon, args.profile_n0
+    p, field, xg0, _ = W.mppi_c2(0, K=1, H=1, n=n0)
     eps = torch.tensor(W.mppi_noise(1000, K, Hh, W.MPPI_SIGMA_U), device="cuda")
-    root = V.State(p, field, xg0, N0 + 2 * Hh, V.FP32)
+    root = V.State(p, field, xg0, n0 + 2 * Hh, V.FP32)
     mu = torch.zeros(Hh, dtype=torch.float32, device="cuda")
     for j in range(args.warmup + args.steps):
         c = V.mppi_perturb(mu, eps)
@@ -539,7 +539,7 @@ def run_profile_case(args):
         mu = V.mppi_update(w, c)
     torch.cuda.synchronize()
     root.status()
-    print(json.dumps({"profile_case": True, "K": K, "H": Hh, "launches": 4 * (args.warmup + args.steps)}))
+    print(json.dumps({"profile_case": True, "K": K, "H": Hh, "n0": n0, "launches": 4 * (args.warmup + args.steps)}))
 
 
 
@@ -1156,6 +1156,7 @@ def main():
     ap.add_argument("--northstar-replans", type=int, default=200,
                     help="north-star replans timed in the main line (0: skip)")
     ap.add_argument("--rollouts", type=int, default=K_ROLL)
+    ap.add_argument("--profile-n0", type=int, default=N0, help="root field size of --profile-case")
     ap.add_argument("--serve-line-seconds", type=float, default=8.0,
                     help="seconds of arrivals per serving run in the main line (0: skip)")
     ap.add_argument("--serve-line-rates", type=float, nargs="*", default=[1.5, 4.0],
