@@ -332,26 +332,28 @@ vpm_status mppi_perturb(const float *d_mu, const float *d_eps, int K, int H,
  * Free-field velocities (Eq. 3 with the chosen kernel, self term excluded) of n particles
  * d_particles[n*4] = (x, z, Gamma, unused) binary32; d_vel[n*2] receives (u, w). Binary32
  * pair sums, compensated across source tiles. One evaluation of each particle pair serves both
- * particles; every particle's partial sums are added exactly into a 128-bit fixed-point
- * accumulator per velocity component, so the result does not depend on the order in which the
- * partial sums arrive. The call allocates vpm_freefield_scratch_bytes(n) bytes (32 n + 64) of
- * device scratch on `stream` from the library's memory pool and frees it after it
- * (stream-ordered). Non-finite input gives NaN velocities. Errors: VPM_ERR_INVALID,
- * VPM_ERR_CUDA (including an allocation that does not fit).
+ * particles; every particle's partial sums are added exactly into a fixed-point accumulator per
+ * velocity component (a 128-bit integer held as three 64-bit digit words), so the result does
+ * not depend on the order in which the partial sums arrive. The call allocates
+ * vpm_freefield_scratch_bytes(n) bytes (48 n + 64) of device scratch on `stream` from the
+ * library's memory pool and frees it after it (stream-ordered). Non-finite input gives NaN
+ * velocities. Errors: VPM_ERR_INVALID, VPM_ERR_CAPACITY (n > 2^30, where the digit words could
+ * overflow), VPM_ERR_CUDA (including an allocation that does not fit).
  */
 vpm_status vpm_freefield_velocity(const float *d_particles, int n, int kernel, double r_core,
                                   float *d_vel, cudaStream_t stream);
 
-/* Device bytes of scratch one free-field velocity evaluation of n particles uses: two 128-bit
- * accumulators per particle and the call's scale (32 n + 64; 0 for n = 0). Errors:
- * VPM_ERR_INVALID (n < 0, null). */
+/* Device bytes of scratch one free-field velocity evaluation of n particles uses: two
+ * accumulators of three 64-bit words per particle and the call's scale (48 n + 64; 0 for
+ * n = 0). Errors: VPM_ERR_INVALID (n < 0, null). */
 vpm_status vpm_freefield_scratch_bytes(int n, size_t *bytes);
 
 /*
  * `steps` Heun (explicit trapezoidal RK2) steps of a free field in place:
  * v1 = V(r), r* = r + dt v1, v2 = V(r*), r <- r + dt (v1 + v2) / 2. d_particles as above.
  * Uses 24 n bytes plus vpm_freefield_scratch_bytes(n) bytes of library-allocated scratch
- * (stream-ordered allocation); vpm_freefield_heun_noalloc allocates nothing.
+ * (stream-ordered allocation); vpm_freefield_heun_noalloc allocates nothing. n <= 2^30
+ * (VPM_ERR_CAPACITY beyond).
  */
 vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, double r_core, double dt,
                               int steps, cudaStream_t stream);
@@ -368,9 +370,10 @@ vpm_status vpm_pool_trim(size_t *bytes_held);
 
 /*
  * Host-only checks of the free-field accumulators (no device needed; the paper has no
- * counterpart). vpm_fixed_sum converts h_v[count] to fixed point with unit 2^-e, adds them as
- * 128-bit integers in the given order and returns the total as a double in *h_sum (*h_bad = 1 if a
- * value was NaN or infinite). vpm_fixed_exponent gives the e the kernels use for n particles whose
+ * counterpart). vpm_fixed_sum converts h_v[count] to fixed point with unit 2^-e, splits each into
+ * the kernels' digits (bits 0-41, 42-83, 84-127 of the 128-bit integer, signed), adds them word by
+ * word in the given order as the kernels' 64-bit reductions do, combines the three words into the
+ * 128-bit total and returns it as a double in *h_sum (*h_bad = 1 if a value was NaN or infinite). vpm_fixed_exponent gives the e the kernels use for n particles whose
  * largest |Gamma| is gmax: with B = n gmax kappa (kappa = 1 / r_core for the regularised kernels,
  * 2^40 for the singular one) and B < 2^eb, e = 125 - eb. Errors: VPM_ERR_INVALID.
  */

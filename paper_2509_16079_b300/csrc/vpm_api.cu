@@ -21,6 +21,7 @@ cudaError_t launch_freefield_heun(float *p, int n, int kernel, double r_core, do
                                   int steps, float *scratch_mid, float *scratch_v1,
                                   cudaStream_t s);
 size_t freefield_sym_scratch_bytes(int n);
+int freefield_sym_max_n();
 cudaError_t launch_freefield_sym_velocity(const float *p, int n, int kernel, double r_core,
                                           float *vel, void *scratch, cudaStream_t s);
 cudaError_t launch_freefield_sym_heun(float *p, int n, int kernel, double r_core, double dt,
@@ -862,6 +863,8 @@ extern "C" vpm_status vpm_freefield_velocity(const float *d_particles, int n, in
     if (n < 0 || (n > 0 && (!d_particles || !d_vel))) return fail(VPM_ERR_INVALID, "bad arguments");
     if (kernel < 0 || kernel > 2 || (kernel != VPM_KERNEL_SINGULAR && !(r_core > 0)))
         return fail(VPM_ERR_INVALID, "bad kernel or core radius");
+    if (n > freefield_sym_max_n())
+        return fail(VPM_ERR_CAPACITY, "vpm_freefield_velocity: n = %d exceeds %d particles", n, freefield_sym_max_n());
     if (n == 0) return VPM_OK;
     void *scratch = nullptr;
     CUDA_TRY(lib_malloc_async(&scratch, freefield_sym_scratch_bytes(n), stream), "freefield scratch");
@@ -879,6 +882,8 @@ extern "C" vpm_status vpm_freefield_heun(float *d_particles, int n, int kernel, 
         return fail(VPM_ERR_INVALID, "bad arguments");
     if (kernel < 0 || kernel > 2 || (kernel != VPM_KERNEL_SINGULAR && !(r_core > 0)))
         return fail(VPM_ERR_INVALID, "bad kernel or core radius");
+    if (n > freefield_sym_max_n())
+        return fail(VPM_ERR_CAPACITY, "vpm_freefield_heun: n = %d exceeds %d particles", n, freefield_sym_max_n());
     if (n == 0 || steps == 0) return VPM_OK;
     // stage positions (16 n bytes), first-stage velocities (8 n bytes), then the accumulators
     char *scratch = nullptr;

@@ -159,10 +159,10 @@ cudaError_t launch_freefield_heun(float *p, int n, int kernel, double r_core, do
 //     w' > w by rotation and its own 4 blocks once per target (both orders), and leaves the
 //     blocks of warps w' < w to them.
 // Every partial sum (a tile's reverse sums of a source, a unit's forward sums of a target) is
-// added into its particle's exact accumulator: two 128-bit two's-complement fixed-point
-// integers (u, w) per particle, 32 bytes. Integer addition is exact and associative, so each
-// particle's total is the exact sum of its binary32 partial sums whatever order the CTAs run
-// in, and the scratch grows like n, not like n^2. A second kernel turns each accumulator into
+// added into its particle's exact accumulator: a fixed-point integer per velocity component,
+// held as three signed 64-bit digit words of radix 2^42, 48 bytes per particle. Integer
+// addition is exact and associative, so each particle's total is the exact sum of its binary32
+// partial sums whatever order the CTAs run in, and the scratch grows like n, not like n^2. A second kernel turns each accumulator into
 // the velocity, applies the step's epilogue and clears the accumulator for the next evaluation.
 constexpr int kFsWarps = 8, kFsThreads = 32 * kFsWarps;
 constexpr int kFsRow = 128 * kFsWarps;      // targets of a row (4 per lane)
@@ -190,13 +190,21 @@ __host__ __device__ inline FsGeom fs_geom(int n)
 
 // ------------------------------------------------------------------ exact accumulation
 //
-// A particle's accumulator holds its velocity sums (u, w) in units of 2^-e as 128-bit
-// two's-complement integers: acc[4 j + 0, 1] are the low and high words of u, [2, 3] of w. The
-// exponent e is fixed for a call by a bound B on every partial sum and on every total: no term
+// A particle's accumulator holds its velocity sums (u, w) in units of 2^-e as integers, each
+// kept as kFsDigits signed 64-bit words d_0, d_1, d_2 of weight 2^0, 2^42, 2^84 (acc[6 j + 0..2]
+// for u, [6 j + 3..5] for w): the value is d_0 + d_1 2^42 + d_2 2^84 as a 128-bit integer. A
+// partial sum's integer has 24 significant bits, so it adds a digit below 2^42 to at most two
+// words, with a plain 64-bit reduction each (no carry between words, no atomic with return).
+// A word stays exact while it receives fewer than 2^21 additions: a particle receives one per
+// row of 1024 particles before its own plus one per unit of its own row (at most n / 1024 +
+// n / 16384 + 3 for n particles), below 2^21 for n <= kFsMaxN = 2^30. The exponent e is fixed for a call by a bound B on every partial sum and on every total: no term
 // of the sums exceeds max|Gamma| kappa, with kappa = 1 / r_core for the regularised kernels
 // (|r q(r)| peaks at 1 / (sqrt(2) r_core) for Eq. 5 and at 0.64 / r_core for the Gaussian core)
 // and 2^40 for the singular kernel (distances down to 2^-40), so |sum| <= B = n max|Gamma| kappa.
 // With B < 2^eb, e = 125 - eb keeps every value below 2^126 and the resolution at B 2^-125.
+constexpr int kFsDigitBits = 42, kFsDigits = 3, kFsWords = 2 * kFsDigits;
+constexpr int kFsMaxN = 1 << 30;
+
 struct FsScale {
     int gmax_bits;                          // max |Gamma| of the call (binary32 bits, >= 0)
     int nonfinite;                          // set when a partial sum is NaN or infinite
@@ -243,6 +251,37 @@ __host__ __device__ inline void fs_to_fixed(float v, int e, unsigned long long &
     }
 }
 
+// The digits of v 2^e (v's integer from fs_to_fixed): the value's 128 bits cut at bits 42 and
+// 84. Each digit is added to its word as a signed 64-bit integer (two's complement).
+__host__ __device__ inline void fs_to_digits(float v, int e, unsigned long long (&d)[kFsDigits], bool &bad)
+{
+    unsigned long long lo, hi;
+    fs_to_fixed(fabsf(v), e, lo, hi, bad);
+    const unsigned long long mask = (1ull << kFsDigitBits) - 1ull;
+    d[0] = lo & mask;
+    d[1] = ((lo >> kFsDigitBits) | (hi << (64 - kFsDigitBits))) & mask;
+    d[2] = hi >> (2 * kFsDigitBits - 64);
+    if (signbit(v)) {
+        for (int k = 0; k < kFsDigits; ++k) d[k] = 0ull - d[k];
+    }
+}
+
+// The digit words w[0..2] as one 128-bit two's-complement integer (lo, hi).
+__host__ __device__ inline void fs_from_digits(const unsigned long long (&w)[kFsDigits],
+                                               unsigned long long &lo, unsigned long long &hi)
+{
+    lo = hi = 0ull;
+    for (int k = 0; k < kFsDigits; ++k) {
+        const int sh = kFsDigitBits * k;
+        const unsigned long long x = w[k], ext = (long long)x < 0 ? ~0ull : 0ull;   // sign extension
+        const unsigned long long xl = sh >= 64 ? 0ull : (sh ? x << sh : x);
+        const unsigned long long xh = sh >= 64 ? x << (sh - 64) : (sh ? (x >> (64 - sh)) | (ext << sh) : ext);
+        const unsigned long long old = lo;
+        lo += xl;
+        hi += xh + (lo < old ? 1ull : 0ull);
+    }
+}
+
 // The accumulator (lo, hi) as a double (one rounding), in units of 1.
 __host__ __device__ inline double fs_from_fixed(unsigned long long lo, unsigned long long hi, int e)
 {
@@ -255,22 +294,20 @@ __host__ __device__ inline double fs_from_fixed(unsigned long long lo, unsigned 
     return ldexp(neg ? -d : d, -e);
 }
 
-// Adds v (units of 1) to the 128-bit accumulator at a: the low words' carry goes to the high
-// word, so concurrent additions in any order leave the exact sum.
+// Adds v (units of 1) to the digit words at a: concurrent additions in any order leave the
+// exact sum (each word's additions commute; nothing carries between words until the combine).
 __device__ __forceinline__ void fs_acc_add(unsigned long long *a, float v, int e, int *nonfinite)
 {
-    unsigned long long lo, hi;
+    unsigned long long d[kFsDigits];
     bool bad = false;
-    fs_to_fixed(v, e, lo, hi, bad);
+    fs_to_digits(v, e, d, bad);
     if (bad) {
         atomicOr(nonfinite, 1);
         return;
     }
-    if (lo) {
-        const unsigned long long old = atomicAdd(a, lo);
-        if (old + lo < old) hi += 1ull;
-    }
-    if (hi) atomicAdd(a + 1, hi);
+#pragma unroll
+    for (int k = 0; k < kFsDigits; ++k)
+        if (d[k]) atomicAdd(a + k, d[k]);
 }
 
 // Stages sources t0 .. t0 + kFsTile - 1 (past n: the last particle's position, zero strength).
@@ -454,16 +491,16 @@ freefield_sym_kernel(const float4 *src, int n, float rc4, float irc2, unsigned l
                 ru += stage[w][q].x;
                 rw += stage[w][q].y;
             }
-            fs_acc_add(acc + 4 * (size_t)j, ru, s_e, &scale->nonfinite);
-            fs_acc_add(acc + 4 * (size_t)j + 2, rw, s_e, &scale->nonfinite);
+            fs_acc_add(acc + kFsWords * (size_t)j, ru, s_e, &scale->nonfinite);
+            fs_acc_add(acc + kFsWords * (size_t)j + kFsDigits, rw, s_e, &scale->nonfinite);
         }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int i = I * kFsRow + 128 * warp + 32 * k + lane;
         if (i >= n) continue;
-        fs_acc_add(acc + 4 * (size_t)i, su[k] - cu[k], s_e, &scale->nonfinite);
-        fs_acc_add(acc + 4 * (size_t)i + 2, sw[k] - cw[k], s_e, &scale->nonfinite);
+        fs_acc_add(acc + kFsWords * (size_t)i, su[k] - cu[k], s_e, &scale->nonfinite);
+        fs_acc_add(acc + kFsWords * (size_t)i + kFsDigits, sw[k] - cw[k], s_e, &scale->nonfinite);
     }
 }
 
@@ -477,9 +514,17 @@ __global__ void __launch_bounds__(256) freefield_combine_kernel(const FfArgs a, 
     const int n = a.n;
     if (j >= n) return;
     const int e = fs_exponent(__int_as_float(scale->gmax_bits), n, a.kernel, a.r_core);
-    unsigned long long *q = acc + 4 * (size_t)j;
-    const double su = fs_from_fixed(q[0], q[1], e), sw = fs_from_fixed(q[2], q[3], e);
-    q[0] = q[1] = q[2] = q[3] = 0ull;
+    unsigned long long *q = acc + kFsWords * (size_t)j;
+    unsigned long long du[kFsDigits], dw[kFsDigits], ul, uh, wl, wh;
+#pragma unroll
+    for (int k = 0; k < kFsDigits; ++k) {
+        du[k] = q[k];
+        dw[k] = q[kFsDigits + k];
+        q[k] = q[kFsDigits + k] = 0ull;
+    }
+    fs_from_digits(du, ul, uh);
+    fs_from_digits(dw, wl, wh);
+    const double su = fs_from_fixed(ul, uh, e), sw = fs_from_fixed(wl, wh, e);
     float vu = (float)(su * kInv2Pi), vw = (float)(sw * kInv2Pi);
     if (scale->nonfinite) vu = vw = __int_as_float(0x7fc00000);
     if (MODE == kFfVelocity) {
@@ -508,18 +553,21 @@ __global__ void __launch_bounds__(256) freefield_gmax_kernel(const float4 *src, 
     if ((threadIdx.x & 31) == 0) atomicMax(&scale->gmax_bits, m);
 }
 
-// Scratch of one call: the accumulators (32 bytes per particle), then the call's scale.
+// Scratch of one call: the accumulators (48 bytes per particle), then the call's scale.
+constexpr size_t kFsAccBytes = sizeof(unsigned long long) * kFsWords;
 size_t freefield_sym_scratch_bytes(int n)
 {
-    return n > 0 ? 32 * (size_t)n + sizeof(FsScale) : 0;
+    return n > 0 ? kFsAccBytes * (size_t)n + sizeof(FsScale) : 0;
 }
+
+int freefield_sym_max_n() { return kFsMaxN; }
 
 // Zeroes the call's scratch and finds max |Gamma| (the strengths do not change during a call).
 static cudaError_t sym_begin(const float4 *src, int n, void *scratch, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(scratch, 0, freefield_sym_scratch_bytes(n), s);
     if (e != cudaSuccess) return e;
-    FsScale *scale = reinterpret_cast<FsScale *>(static_cast<unsigned char *>(scratch) + 32 * (size_t)n);
+    FsScale *scale = reinterpret_cast<FsScale *>(static_cast<unsigned char *>(scratch) + kFsAccBytes * (size_t)n);
     const int grid = min((n + 255) / 256, 1184);
     freefield_gmax_kernel<<<grid, 256, 0, s>>>(src, n, scale);
     return cudaGetLastError();
@@ -531,7 +579,7 @@ static cudaError_t sym_eval(int kernel, const FfArgs &a, void *scratch, cudaStre
     const FsGeom g = fs_geom(a.n);
     if (a.n == 0) return cudaSuccess;
     unsigned long long *acc = static_cast<unsigned long long *>(scratch);
-    FsScale *scale = reinterpret_cast<FsScale *>(static_cast<unsigned char *>(scratch) + 32 * (size_t)a.n);
+    FsScale *scale = reinterpret_cast<FsScale *>(static_cast<unsigned char *>(scratch) + kFsAccBytes * (size_t)a.n);
     const dim3 grid(1 + g.max_seg, g.rows);
     if (kernel == VPM_KERNEL_GAUSSIAN)
         freefield_sym_kernel<VPM_KERNEL_GAUSSIAN><<<grid, kFsThreads, 0, s>>>(a.src, a.n, a.rc4, a.inv_rc2, acc, scale, kernel, a.r_core);
@@ -596,21 +644,22 @@ cudaError_t launch_freefield_sym_heun(float *p, int n, int kernel, double r_core
 }  // namespace vpm
 
 // Host-side check of the exact accumulation (no device needed): the values h_v[count] converted
-// with exponent e and added as 128-bit integers in the given order, returned as a double.
+// with exponent e into the kernels' digits, added word by word in the given order as the kernels'
+// reductions do, and the words combined into the 128-bit total, returned as a double.
 extern "C" vpm_status vpm_fixed_sum(const float *h_v, int count, int e, double *h_sum, int *h_bad)
 {
     if ((!h_v && count > 0) || count < 0 || !h_sum || !h_bad) return VPM_ERR_INVALID;
-    unsigned long long lo = 0ull, hi = 0ull;
+    unsigned long long w[vpm::kFsDigits] = {0ull, 0ull, 0ull};
     int bad = 0;
     for (int i = 0; i < count; ++i) {
-        unsigned long long l, h;
+        unsigned long long d[vpm::kFsDigits];
         bool b = false;
-        vpm::fs_to_fixed(h_v[i], e, l, h, b);
+        vpm::fs_to_digits(h_v[i], e, d, b);
         if (b) { bad = 1; continue; }
-        const unsigned long long old = lo;
-        lo += l;
-        hi += h + (lo < old ? 1ull : 0ull);
+        for (int k = 0; k < vpm::kFsDigits; ++k) w[k] += d[k];
     }
+    unsigned long long lo, hi;
+    vpm::fs_from_digits(w, lo, hi);
     *h_sum = vpm::fs_from_fixed(lo, hi, e);
     *h_bad = bad;
     return VPM_OK;

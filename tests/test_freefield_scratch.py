@@ -1,10 +1,12 @@
 """The free-field accumulators: linear scratch and exact, order-independent sums (host only).
 
 The one-evaluation-per-pair free-field kernels add every partial sum of a particle's velocity
-into two 128-bit fixed-point integers (unit 2^-e) with 64-bit atomic additions and a carry into
-the high word. vpm_fixed_sum runs the same conversion and addition on the host; these tests
+into a fixed-point integer (unit 2^-e) per component, kept as three signed 64-bit digit words of
+radix 2^42 that receive plain 64-bit additions (no carry until they are combined). vpm_fixed_sum
+runs the same conversion, digit split, word additions and combination on the host; these tests
 compare it with the exact sum of the same binary32 values (Python fractions), permute the
-order, force carries between the words, and check the exponent's bound. No device is needed.
+order, cross the digit boundaries, load the words with the most additions the kernels make, and
+check the exponent's bound. No device is needed.
 """
 import ctypes as C
 import math
@@ -36,7 +38,7 @@ def test_scratch_is_linear(n):
     V, L = _lib()
     b = C.c_size_t()
     V.check(L.vpm_freefield_scratch_bytes(n, C.byref(b)))
-    assert b.value == (32 * n + 64 if n else 0)
+    assert b.value == (48 * n + 64 if n else 0)
 
 
 def test_sum_is_exact_and_order_independent():
@@ -109,3 +111,47 @@ def test_exponent_of_a_field_without_circulation():
     e = C.c_int(7)
     V.check(L.vpm_fixed_exponent(C.c_float(0.0), 100, 1, 0.05, C.byref(e)))
     assert e.value == 0
+
+
+def test_digit_boundaries_and_the_top_of_the_range():
+    """Integers whose 24 significant bits straddle bit 42 or 84 of the 128-bit value, and values
+    up to 2^125 units (the exponent leaves |sum| below 2^125), of both signs, sum exactly."""
+    e = 0
+    vals = []
+    for top in (41, 42, 43, 50, 60, 65, 83, 84, 85, 100, 110, 124):
+        for s in (1.0, -1.0):
+            vals.append(np.float32(s * (2.0 ** top) * 1.4142135))   # 24 bits ending near bit `top`
+    v = np.array(vals, dtype=np.float32)
+    for perm in range(3):
+        p = np.random.default_rng(perm).permutation(len(v))
+        for sub in (v[p], v[p][::2], v[p][1::3]):
+            s, bad = _fixed_sum(sub, e)
+            assert bad == 0
+            exact = _exact(sub)
+            assert abs(Fraction(s) - exact) <= abs(exact) * Fraction(1, 2 ** 52), (perm, sub)
+
+
+def test_words_hold_the_most_additions_a_particle_receives():
+    """At n = 2^30 particles a particle receives at most n / 1024 + n / 16384 + 3 partial sums.
+    That many of the largest values one word can take, all positive (the low word then reaches
+    about 2^62 and must not overflow), sum exactly; so does a mixed-sign set of the same count
+    that loads the middle and top words, with a total inside the 128-bit range."""
+    n = 1 << 30
+    count = n // 1024 + n // 16384 + 3
+    e = 0
+    top0 = np.float32((2.0 ** 24 - 1) * 2.0 ** 18)          # 2^42 - 2^18: bits 18..41, word 0 only
+    v = np.full(count, top0, dtype=np.float32)
+    s, bad = _fixed_sum(v, e)
+    assert bad == 0 and Fraction(s) == Fraction(float(top0)) * count
+    rng = np.random.default_rng(5)
+    w = (rng.choice([-1.0, 1.0], count) * 2.0 ** rng.integers(60, 105, count) * 1.3).astype(np.float32)
+    s, bad = _fixed_sum(w, e)
+    exact = _exact(w)
+    assert bad == 0 and abs(Fraction(s) - exact) <= abs(exact) * Fraction(1, 2 ** 52)
+
+
+def test_free_field_rejects_fields_beyond_the_digit_headroom():
+    import paper_2509_16079_b300 as V
+    L = V.lib()
+    st = L.vpm_freefield_velocity(None, (1 << 30) + 1, V.KERNEL_VATISTAS, 0.05, None, None)
+    assert st in (V.VPM_ERR_INVALID, V.VPM_ERR_CAPACITY)
