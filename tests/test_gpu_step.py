@@ -141,6 +141,35 @@ def test_pair_rows_edges(ora, n):
         g.close()
 
 
+@pytest.mark.parametrize("n", [1298, 1439])
+@pytest.mark.parametrize("kernel", ["gaussian", "singular"])
+def test_pair_diagonal_other_wake_kernels(ora, kernel, n):
+    """The once-per-pair diagonal units (fields of 1300 particles and more) with the Gaussian core
+    and the singular kernel of Eq. 4 as the wake kernel: one step at n and n + 2 against the
+    oracle. The singular kernel's field is a jittered lattice (no two particles closer than half
+    a cell), since binary32 positions leave the 1/r velocity of near-coincident pairs without a
+    relative error bound."""
+    torch, V = cuda()
+    if kernel == "gaussian":
+        params = W.glider_params(wake_kernel=W.KERNEL_GAUSSIAN)
+        field = W.background_field(70 + n, n)
+    else:
+        params = W.glider_params(wake_kernel=W.KERNEL_SINGULAR)
+        field = W.lattice_field(71 + n, n)
+    snaps, cap = _snapshots(ora, params, field, np.array(W.GLIDER_X0), [0, 1])
+    for k, snap, u in snaps:
+        o = oracle_state(ora, params, snap, cap)
+        ref = o.step(u)
+        g = gpu_state(V, params, snap, cap, V.FP32)
+        out = g.step(u, probe=True)
+        torch.cuda.synchronize()
+        n1 = len(ref["vel"])
+        vel = out["vel"].cpu().numpy()[:2 * n1].reshape(-1, 2)
+        msg = "%s n=%d step %d" % (kernel, n, k)
+        assert normwise(vel, ref["vel"]) <= VEL_TOL, msg
+        g.close()
+
+
 def test_step_commits_and_rollout_agree(ora):
     """Ten vpm_step calls advance the resident state exactly as a 10-step rollout does."""
     torch, V = cuda()

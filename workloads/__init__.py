@@ -92,6 +92,22 @@ def background_field(seed: int, n: int, box=BOX, gamma_std: float = 0.01) -> np.
     return np.stack([x, z, g], axis=1)
 
 
+def lattice_field(seed: int, n: int, box=BOX, gamma_std: float = 0.01, jitter: float = 0.25) -> np.ndarray:
+    """n particles on a jittered lattice over `box`: the first n cells of a near-square grid with
+    at least n cells, each point moved by up to `jitter` cell widths per axis, so no two particles
+    come closer than (1 - 2 jitter) cells; Gamma ~ N(0, gamma_std^2); rows (x, z, Gamma)."""
+    r = _rng(seed)
+    w, h = box[1] - box[0], box[3] - box[2]
+    nx = int(np.ceil(np.sqrt(n * w / h)))
+    nz = int(np.ceil(n / nx))
+    i = np.arange(n)
+    cx, cz = w / nx, h / nz
+    x = box[0] + (i % nx + 0.5 + r.uniform(-jitter, jitter, n)) * cx
+    z = box[2] + (i // nx + 0.5 + r.uniform(-jitter, jitter, n)) * cz
+    g = r.normal(0.0, gamma_std, n)
+    return np.stack([x, z, g], axis=1)
+
+
 def mppi_noise(seed: int, K: int, H: int, sigma: float) -> np.ndarray:
     """Control perturbations eps[K, H] ~ N(0, sigma^2), rounded to float32 once."""
     return _rng(seed).normal(0.0, sigma, (K, H)).astype(np.float32)
