@@ -451,10 +451,10 @@ vpm_status vpm_batch_status(vpm_batch *batch, cudaStream_t stream);
 /* ------------------------------------------------------------------ replanning server
  * Serves replanning requests (§IV-C: re-running the MPPI iteration of §IV-A from each
  * scenario's current vortex state) from many scenarios at once. Each scenario's field stays
- * resident on the device between requests. A worker thread admits queued requests in arrival
- * order whenever a slot is free, the scenario has nothing on the device, and the request's
- * device buffers fit the memory budget; admitted requests run on their own streams and overlap
- * on the GPU. A newer request for a scenario supersedes its older request still in the queue
+ * resident on the device between requests. A worker thread admits queued requests (in arrival
+ * order, or least estimated work first: vpm_server_config.policy) whenever a slot is free, the
+ * scenario has nothing on the device, and the request's device buffers fit the memory budget;
+ * admitted requests run on their own streams and overlap on the GPU. A newer request for a scenario supersedes its older request still in the queue
  * (that one completes with VPM_ERR_BUSY). Results do not depend on what else runs.
  */
 typedef struct vpm_server vpm_server;
@@ -472,7 +472,16 @@ typedef struct {
                                    total stays within it or when nothing else runs. 0: the rollout
                                    blocks the device holds at once (SMs x 7), beyond which more
                                    concurrency only adds latency                                */
+    int policy;           /* admission order: VPM_ADMIT_ARRIVAL (0) admits queued requests in
+                             arrival order; VPM_ADMIT_LEAST_WORK (1) admits, among the queued
+                             requests whose scenario is idle and whose bytes fit, the one with the
+                             fewest estimated pair interactions (K H n^2, n the scenario's
+                             particle count at mid-horizon) first                              */
+    double max_wait_ms;   /* with VPM_ADMIT_LEAST_WORK: a request queued longer than this is
+                             admitted first, in arrival order (<= 0: no such bound)              */
 } vpm_server_config;
+
+enum { VPM_ADMIT_ARRIVAL = 0, VPM_ADMIT_LEAST_WORK = 1 };
 
 typedef struct {
     int status;           /* VPM_OK, VPM_ERR_BUSY (superseded), or the error that stopped it     */

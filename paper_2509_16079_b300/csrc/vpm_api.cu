@@ -593,6 +593,16 @@ size_t rollout_scratch_bytes(const vpm_state *s, int K, int H, int advance)
     if (cap > s->capacity) cap = s->capacity;
     return sizeof(float2) * (size_t)K * (size_t)rollout_rev_slots(s->params.precision, (int)cap);
 }
+
+// Pair interactions of K rollouts of H steps taken after `advance` more committed steps,
+// estimated from the host's count bound at mid-horizon: K H n^2 (the serving loop's
+// least-work-first admission).
+double rollout_work_estimate(const vpm_state *s, int K, int H, int advance)
+{
+    long long n = grown(s, advance + H / 2);
+    if (n > s->capacity) n = s->capacity;
+    return (double)K * (double)H * (double)n * (double)n;
+}
 }  // namespace vpm
 
 extern "C" vpm_status vpm_rollout_scratch_bytes_cap(int precision, int capacity, int K, size_t *bytes)

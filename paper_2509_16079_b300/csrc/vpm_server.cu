@@ -32,6 +32,7 @@
 namespace vpm {
 vpm_status report_error(vpm_status st, const char *msg);
 size_t rollout_scratch_bytes(const vpm_state *s, int K, int H, int advance);
+double rollout_work_estimate(const vpm_state *s, int K, int H, int advance);
 cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
 size_t lib_pool_idle_bytes();
 }
@@ -57,6 +58,7 @@ struct Request {
     std::vector<float> mu, eps;
     size_t bytes = 0;                 // device bytes the request holds while in flight
     size_t buf_bytes = 0;             // of which its own buffers (the rest: rollout scratch)
+    double work = 0;                  // estimated pair interactions (least-work-first admission)
     double t_submit = 0, t_start = 0, t_done = 0;
 };
 
@@ -199,8 +201,47 @@ static void worker_loop(vpm_server *s)
             sl.busy = false;
             progressed = true;
         }
+        // least work first: among the queued requests whose scenario is idle and whose bytes fit,
+        // the one with the fewest estimated pair interactions, unless one has waited longer than
+        // max_wait_ms (then the longest-waiting of those); admission stops at a request that would
+        // overfill the device, as in arrival order
+        while (s->cfg.policy == VPM_ADMIT_LEAST_WORK && !s->queue.empty()) {
+            Slot *free_slot = nullptr;
+            for (auto &sl : s->slots)
+                if (!sl.busy) { free_slot = &sl; break; }
+            if (!free_slot) break;
+            const double now = s->now_ms();
+            const size_t avail = live_available(s);
+            auto least = s->queue.end(), aged = s->queue.end();
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+                if (s->scenario_busy[it->scenario] || s->in_flight_bytes + it->bytes > s->budget ||
+                    it->bytes > avail)
+                    continue;
+                if (s->cfg.max_wait_ms > 0 && now - it->t_submit > s->cfg.max_wait_ms && aged == s->queue.end())
+                    aged = it;                // the queue is in arrival order
+                if (least == s->queue.end() || it->work < least->work) least = it;
+            }
+            auto it = aged != s->queue.end() ? aged : least;
+            if (it == s->queue.end()) break;
+            if (s->in_flight_rollouts > 0 && s->in_flight_rollouts + it->K > s->rollout_budget) break;
+            Request r = std::move(*it);
+            s->queue.erase(it);
+            r.t_start = s->now_ms();
+            vpm_status v = start_request(s, *free_slot, r);
+            if (v != VPM_OK) {
+                finish(s, r, v, nullptr, 0.f);
+                continue;
+            }
+            free_slot->req = std::move(r);
+            free_slot->req.eps.clear();
+            free_slot->busy = true;
+            s->in_flight_bytes += free_slot->req.bytes;
+            s->in_flight_rollouts += free_slot->req.K;
+            s->scenario_busy[free_slot->req.scenario] = 1;
+            progressed = true;
+        }
         // admission in arrival order: free slot, idle scenario, memory budget
-        for (auto it = s->queue.begin(); it != s->queue.end();) {
+        for (auto it = s->queue.begin(); s->cfg.policy != VPM_ADMIT_LEAST_WORK && it != s->queue.end();) {
             Slot *free_slot = nullptr;
             for (auto &sl : s->slots)
                 if (!sl.busy) { free_slot = &sl; break; }
@@ -248,6 +289,8 @@ extern "C" vpm_status vpm_server_create(const vpm_server_config *cfg, vpm_server
 {
     if (!cfg || !out || cfg->max_inflight < 1 || cfg->max_rollouts < 1 || cfg->max_horizon < 1)
         return sfail(VPM_ERR_INVALID, "vpm_server_create: need max_inflight, max_rollouts, max_horizon >= 1");
+    if (cfg->policy != VPM_ADMIT_ARRIVAL && cfg->policy != VPM_ADMIT_LEAST_WORK)
+        return sfail(VPM_ERR_INVALID, "vpm_server_create: unknown admission policy %d", cfg->policy);
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
         cudaGetLastError();
@@ -321,6 +364,7 @@ extern "C" vpm_status vpm_server_submit(vpm_server *s, int scenario, int K, int 
     if (scenario < 0 || scenario >= (int)s->scenarios.size())
         return sfail(VPM_ERR_INVALID, "vpm_server_submit: unknown scenario %d", scenario);
     r.bytes = r.buf_bytes + vpm::rollout_scratch_bytes(s->scenarios[scenario], K, H, advance_steps);
+    r.work = vpm::rollout_work_estimate(s->scenarios[scenario], K, H, advance_steps);
     if (r.bytes > s->budget || r.bytes + s->reserve > s->total_mem)
         return sfail(VPM_ERR_CAPACITY, "vpm_server_submit: request needs %zu bytes; budget %zu, device %zu less %zu "
                      "kept free", r.bytes, s->budget, s->total_mem, s->reserve);

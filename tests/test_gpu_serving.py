@@ -141,3 +141,33 @@ def test_admission_waits_for_memory_taken_after_creation():
     res = srv.poll(t, timeout_ms=60000)
     assert res is not None and res[0]["status"] == V.VPM_OK
     srv.close()
+
+
+@pytest.mark.parametrize("policy,max_wait_ms,small_first", [(0, 0.0, False), (1, 0.0, True), (1, 1.0, False)])
+def test_admission_order_by_policy(policy, max_wait_ms, small_first):
+    """One slot: while a long request runs, a large request B and then a small one C queue up.
+    In arrival order B starts first; least work first starts C first (it needs about 1/30 of B's
+    pair interactions); with a 1 ms bound on waiting, both have waited longer when the slot frees,
+    so arrival order holds again. C's result is the same bits under every policy."""
+    torch, V = cuda()
+    srv = V.Server(max_inflight=1, max_rollouts=2048, max_horizon=100, policy=policy, max_wait_ms=max_wait_ms)
+    p = W.glider_params()
+    fields = [W.background_field(80, 1000), W.background_field(81, 1000), W.background_field(82, 300)]
+    for f in fields:
+        srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 2 * 100 + 10)
+    ta = srv.submit(0, W.mppi_noise(90, 2048, 100, W.MPPI_SIGMA_U))
+    tb = srv.submit(1, W.mppi_noise(91, 2048, 100, W.MPPI_SIGMA_U))
+    eps_c = W.mppi_noise(92, 256, 100, W.MPPI_SIGMA_U)
+    tc = srv.submit(2, eps_c)
+    (ra, _), (rb, _), (rc, mu_c) = srv.poll(ta), srv.poll(tb), srv.poll(tc)
+    srv.close()
+    assert ra["status"] == rb["status"] == rc["status"] == V.VPM_OK
+    assert (rc["t_start_ms"] < rb["t_start_ms"]) == small_first, (policy, rb, rc)
+    mu_d, jmin_d = _direct_mu(V, torch, p, fields[2], eps_c, 10.0)
+    assert np.array_equal(mu_c, mu_d) and rc["j_min"] == jmin_d
+
+
+def test_unknown_admission_policy_is_rejected():
+    torch, V = cuda()
+    with pytest.raises(V.VpmError):
+        V.Server(max_inflight=1, policy=7)
