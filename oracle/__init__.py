@@ -6,6 +6,10 @@ uses it. The arithmetic lives in `vpm_oracle.c` (plain C, binary64, no fast-math
 file only builds that library with gcc and marshals numpy arrays.
 
 Parameter dictionaries come from `workloads` (the shared seeded-input module).
+
+The environment variable ORACLE_LIB, when set, names another build of `vpm_oracle.c` to load
+instead (the mutation tests load copies with one deliberate error each and check that the pins
+catch it).
 """
 from __future__ import annotations
 
@@ -23,7 +27,10 @@ SINGULAR, VATISTAS, GAUSSIAN = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile vpm_oracle.c into liboracle.so (gcc, -O2, strict IEEE)."""
+    """Compile vpm_oracle.c into liboracle.so (gcc, -O2, strict IEEE); with ORACLE_LIB set,
+    return that library instead."""
+    if os.environ.get("ORACLE_LIB"):
+        return os.environ["ORACLE_LIB"]
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call([
