@@ -14,6 +14,7 @@
 
 #include <atomic>
 #include <climits>
+#include <cstdlib>
 #include <mutex>
 
 #include "vpm_rollout.cuh"
@@ -1300,8 +1301,18 @@ constexpr int kPaceSms = 1024;    // SM ids paced (blocks on an SM with a larger
 // Fields that stay small have short, plate-bound steps (~18 us at 60 particles), where a
 // 1 us sleep and the extra barrier cost more than the tail they remove: pacing is for launches
 // whose fields can exceed this many particles (measured: the perch-shape batch of 1024 took
-// 2.64 ms paced against 2.30 ms unpaced, the MPPI batch 2.3 % less time paced).
+// 2.64 ms paced against 2.30 ms unpaced).
+// Pacing is off unless the environment variable VPM_PACE is 1 when a launch is made. With the
+// current pair phase it no longer pays on the MPPI batch (K = 1024, H = 100: 36.8 ms paced
+// against 36.3 ms unpaced), but its code stays in the kernel: removing it changed the row loop's
+// register allocation and cost 2.4 % (37.7 ms).
 constexpr int kPaceMinCap = 256;
+
+static bool pacing_requested()
+{
+    const char *e = getenv("VPM_PACE");
+    return e && e[0] == '1' && e[1] == 0;
+}
 
 __device__ __forceinline__ unsigned sm_id()
 {
@@ -1463,7 +1474,7 @@ static cudaError_t launch_t(const RolloutArgs &a, int grid, size_t smem, cudaStr
     // binary32 multi-step launches that fit in one wave with several blocks per SM are paced
     RolloutArgs b = a;
     void *pace = nullptr;
-    if (sizeof(R) == 4 && a.H > 1 && a.cap > kPaceMinCap && !a.pace_mask) {
+    if (sizeof(R) == 4 && a.H > 1 && a.cap > kPaceMinCap && !a.pace_mask && pacing_requested()) {
         int dev = 0, sms = 0, per_sm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&

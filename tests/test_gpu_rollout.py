@@ -246,15 +246,22 @@ def test_batch_invariance_and_per_launch_form():
     assert torch.equal(pl["final_glider"], full["final_glider"][:8])
 
 
-def test_paced_launch_matches_unpaced_launches():
-    """A one-wave launch of 1024 rollouts paces its co-resident blocks (a block ahead of the
-    slowest on its SM sleeps); launches of 128 (one block per SM at most) are not paced. The
-    pacing changes timing only: the results are the same bits."""
+def test_paced_launch_matches_unpaced_launches(monkeypatch):
+    """With VPM_PACE=1 a one-wave launch of 1024 rollouts paces its co-resident blocks (a block
+    ahead of the slowest on its SM sleeps); launches of 128 (one block per SM at most) and, by
+    default, every launch are not paced. The pacing changes timing only: the results are the
+    same bits."""
     torch, V = cuda()
     p, field, xg0, eps = W.mppi_c2(2, K=1024, H=6, n=300)
     st = V.State(p, field, xg0, 320)
     c = torch.tensor(eps, device="cuda")
+    monkeypatch.setenv("VPM_PACE", "1")
     full = st.rollout_batch(c)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("VPM_PACE")
+    unpaced = st.rollout_batch(c)
+    assert torch.equal(unpaced["costs"], full["costs"])
+    assert torch.equal(unpaced["final_glider"], full["final_glider"])
     for b in range(0, 1024, 128):
         part = st.rollout_batch(c[b:b + 128].contiguous())
         assert torch.equal(part["costs"], full["costs"][b:b + 128])
