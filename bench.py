@@ -466,7 +466,8 @@ def run_gpu(args):
             serving = serving_at_rates(V, args.serve_line_rates, args.serve_line_seconds)
         serving = {"workload": "16 scenarios of 500-5000 resident particles, K in {256, 1024, 4096}, "
                                "H=100, Poisson arrivals; continuous batching (16 in flight; arrival "
-                               "order, and least estimated work first with a 4 s bound on waiting) "
+                               "order, and least estimated work first with a 4 s bound on waiting and a "
+                               "high-priority lane for K <= 256) "
                                "against the plain per-request form (1 in flight) on the same trace",
                    "seconds_of_arrivals": args.serve_line_seconds, "runs": serving,
                    "clocks": clk_sv.summary()}
@@ -994,6 +995,7 @@ def run_uneven(args):
 
 SERVE_H = 100
 SERVE_MAX_WAIT_MS = 4000.0   # least-work-first admission: a request queued this long goes first
+SERVE_SMALL_ROLLOUTS = 256   # and requests of up to this many rollouts take the high-priority lane
 
 
 def serving_setup(V):
@@ -1005,13 +1007,14 @@ def serving_setup(V):
     return fields, noise
 
 
-def serve_trace(V, fields, noise, arrivals, streams, sizes, slots, policy=0, max_wait_ms=0.0):
+def serve_trace(V, fields, noise, arrivals, streams, sizes, slots, policy=0, max_wait_ms=0.0,
+                small_rollouts=0):
     """Replays an arrival trace in real time against a server with `slots` requests in flight
     (16: continuous batching; 1: the plain per-request form) and the given admission policy.
     Each request first advances its scenario by 2 steps, then replans with K = sizes[j] rollouts
     over SERVE_H steps."""
     srv = V.Server(max_inflight=slots, max_rollouts=4096, max_horizon=SERVE_H, policy=policy,
-                   max_wait_ms=max_wait_ms)
+                   max_wait_ms=max_wait_ms, small_rollouts=small_rollouts)
     for f in fields:
         p = W.glider_params(n_wake_max=len(f) + 300)
         srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 300 + 2 * SERVE_H + 8)
@@ -1040,7 +1043,7 @@ def serve_trace(V, fields, noise, arrivals, streams, sizes, slots, policy=0, max
 
 def serving_at_rates(V, rates, seconds):
     """Continuous batching (arrival order, and least estimated work first with a 4 s bound on
-    waiting) against the per-request form at total request rates around one GPU's capacity (same
+    waiting and a high-priority lane for requests of up to 256 rollouts) against the per-request form at total request rates around one GPU's capacity (same
     scenarios, request mix and arrival seeds as the sweep of --workload serving)."""
     fields, noise = serving_setup(V)
     out = []
@@ -1050,7 +1053,8 @@ def serving_at_rates(V, rates, seconds):
         out.append({"offered_hz": rate,
                     "continuous": serve_trace(V, fields, noise, arr, strm, ks, 16),
                     "continuous_least_work": serve_trace(V, fields, noise, arr, strm, ks, 16,
-                                                         V.ADMIT_LEAST_WORK, SERVE_MAX_WAIT_MS),
+                                                         V.ADMIT_LEAST_WORK, SERVE_MAX_WAIT_MS,
+                                                         SERVE_SMALL_ROLLOUTS),
                     "per_request": serve_trace(V, fields, noise, arr, strm, ks, 1)})
     return out
 

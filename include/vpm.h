@@ -479,6 +479,11 @@ typedef struct {
                              particle count at mid-horizon) first                              */
     double max_wait_ms;   /* with VPM_ADMIT_LEAST_WORK: a request queued longer than this is
                              admitted first, in arrival order (<= 0: no such bound)              */
+    int small_rollouts;   /* with VPM_ADMIT_LEAST_WORK: requests of at most this many rollouts
+                             take a lane of their own, admitted while that lane's rollouts stay
+                             within max_inflight_rollouts whatever the other requests hold, on
+                             streams of the highest priority, so that their blocks start ahead of
+                             the waiting blocks of larger launches. 0: no such lane              */
 } vpm_server_config;
 
 enum { VPM_ADMIT_ARRIVAL = 0, VPM_ADMIT_LEAST_WORK = 1 };

@@ -358,7 +358,7 @@ def pool_trim() -> int:
 class ServerConfig(C.Structure):
     _fields_ = [("max_inflight", C.c_int), ("hbm_budget", C.c_size_t), ("max_rollouts", C.c_int),
                 ("max_horizon", C.c_int), ("max_inflight_rollouts", C.c_int), ("policy", C.c_int),
-                ("max_wait_ms", C.c_double)]
+                ("max_wait_ms", C.c_double), ("small_rollouts", C.c_int)]
 
 
 ADMIT_ARRIVAL, ADMIT_LEAST_WORK = 0, 1
@@ -375,9 +375,9 @@ class Server:
 
     def __init__(self, max_inflight: int = 8, max_rollouts: int = 4096, max_horizon: int = 100,
                  hbm_budget: int = 0, max_inflight_rollouts: int = 0, policy: int = ADMIT_ARRIVAL,
-                 max_wait_ms: float = 0.0):
+                 max_wait_ms: float = 0.0, small_rollouts: int = 0):
         cfg = ServerConfig(int(max_inflight), int(hbm_budget), int(max_rollouts), int(max_horizon),
-                           int(max_inflight_rollouts), int(policy), float(max_wait_ms))
+                           int(max_inflight_rollouts), int(policy), float(max_wait_ms), int(small_rollouts))
         h = C.c_void_p()
         check(lib().vpm_server_create(C.byref(cfg), C.byref(h)))
         self._h = h

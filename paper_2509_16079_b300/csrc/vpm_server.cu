@@ -71,7 +71,10 @@ struct Result {
 
 struct Slot {
     bool busy = false;
-    cudaStream_t stream = nullptr;
+    bool small = false;               // the current request runs on the small requests' lane
+    cudaStream_t stream = nullptr;    // default priority
+    cudaStream_t stream_hi = nullptr; // highest priority (the small requests' lane), if enabled
+    cudaStream_t active = nullptr;    // the current request's stream
     cudaEvent_t done = nullptr;
     float *pinned = nullptr;          // eps + mu in, mu + costs out
     size_t pinned_floats = 0;
@@ -87,6 +90,7 @@ struct vpm_server {
     size_t budget = 0, in_flight_bytes = 0;   // budget: the configured cap (SIZE_MAX: none)
     size_t reserve = 0, total_mem = 0;       // device memory admission leaves free, and the total
     long long rollout_budget = 0, in_flight_rollouts = 0;
+    long long in_flight_small = 0;            // of which on the small requests' lane
     Clock::time_point t0;
     std::vector<vpm_state *> scenarios;
     std::vector<int> scenario_busy;
@@ -120,26 +124,26 @@ static vpm_status start_request(vpm_server *s, Slot &sl, const Request &r)
     float *pin = sl.pinned;
     memcpy(pin, r.eps.data(), sizeof(float) * (size_t)K * H);
     memcpy(pin + (size_t)K * H, r.mu.data(), sizeof(float) * H);
-    cudaError_t e = vpm::lib_malloc_async((void **)&sl.d_buf, r.buf_bytes, sl.stream);
+    cudaError_t e = vpm::lib_malloc_async((void **)&sl.d_buf, r.buf_bytes, sl.active);
     if (e) { cudaGetLastError(); return sfail(VPM_ERR_OOM, "server: allocation: %s", cudaGetErrorString(e)); }
     float *d_eps = sl.d_buf, *d_ctrl = d_eps + (size_t)K * H, *d_costs = d_ctrl + (size_t)K * H;
     float *d_w = d_costs + K, *d_mu = d_w + K;
-    e = cudaMemcpyAsync(d_eps, pin, sizeof(float) * (size_t)K * H, cudaMemcpyHostToDevice, sl.stream);
-    if (!e) e = cudaMemcpyAsync(d_mu, pin + (size_t)K * H, sizeof(float) * H, cudaMemcpyHostToDevice, sl.stream);
+    e = cudaMemcpyAsync(d_eps, pin, sizeof(float) * (size_t)K * H, cudaMemcpyHostToDevice, sl.active);
+    if (!e) e = cudaMemcpyAsync(d_mu, pin + (size_t)K * H, sizeof(float) * H, cudaMemcpyHostToDevice, sl.active);
     if (e) { cudaGetLastError(); return sfail(VPM_ERR_CUDA, "server: upload: %s", cudaGetErrorString(e)); }
     vpm_state *st = s->scenarios[r.scenario];
     vpm_status v = VPM_OK;
     for (int k = 0; k < r.advance_steps && v == VPM_OK; ++k)
-        v = vpm_step(st, (double)r.advance_u, nullptr, nullptr, nullptr, nullptr, sl.stream);
-    if (v == VPM_OK) v = mppi_perturb(d_mu, d_eps, K, H, d_ctrl, sl.stream);
-    if (v == VPM_OK) v = vpm_rollout_batch(st, K, H, d_ctrl, d_costs, nullptr, nullptr, nullptr, nullptr, sl.stream);
-    if (v == VPM_OK) v = mppi_weights(d_costs, K, r.lambda, d_w, sl.stream);
-    if (v == VPM_OK) v = mppi_update(d_w, d_ctrl, K, H, d_mu, sl.stream);
+        v = vpm_step(st, (double)r.advance_u, nullptr, nullptr, nullptr, nullptr, sl.active);
+    if (v == VPM_OK) v = mppi_perturb(d_mu, d_eps, K, H, d_ctrl, sl.active);
+    if (v == VPM_OK) v = vpm_rollout_batch(st, K, H, d_ctrl, d_costs, nullptr, nullptr, nullptr, nullptr, sl.active);
+    if (v == VPM_OK) v = mppi_weights(d_costs, K, r.lambda, d_w, sl.active);
+    if (v == VPM_OK) v = mppi_update(d_w, d_ctrl, K, H, d_mu, sl.active);
     if (v != VPM_OK) return v;
-    e = cudaMemcpyAsync(pin, d_mu, sizeof(float) * H, cudaMemcpyDeviceToHost, sl.stream);
-    if (!e) e = cudaMemcpyAsync(pin + H, d_costs, sizeof(float) * K, cudaMemcpyDeviceToHost, sl.stream);
-    if (!e) e = cudaFreeAsync(sl.d_buf, sl.stream);
-    if (!e) e = cudaEventRecord(sl.done, sl.stream);
+    e = cudaMemcpyAsync(pin, d_mu, sizeof(float) * H, cudaMemcpyDeviceToHost, sl.active);
+    if (!e) e = cudaMemcpyAsync(pin + H, d_costs, sizeof(float) * K, cudaMemcpyDeviceToHost, sl.active);
+    if (!e) e = cudaFreeAsync(sl.d_buf, sl.active);
+    if (!e) e = cudaEventRecord(sl.done, sl.active);
     if (e) { cudaGetLastError(); return sfail(VPM_ERR_CUDA, "server: enqueue: %s", cudaGetErrorString(e)); }
     return VPM_OK;
 }
@@ -188,7 +192,7 @@ static void worker_loop(vpm_server *s)
             if (q != cudaSuccess) {
                 cudaGetLastError();
                 status = VPM_ERR_CUDA;
-            } else if (vpm_state_status(s->scenarios[r.scenario], sl.stream) != VPM_OK) {
+            } else if (vpm_state_status(s->scenarios[r.scenario], sl.active) != VPM_OK) {
                 status = VPM_ERR_NONFINITE;
             }
             float jmin = INFINITY;
@@ -197,6 +201,7 @@ static void worker_loop(vpm_server *s)
             finish(s, r, status, sl.pinned, jmin);
             s->in_flight_bytes -= r.bytes;
             s->in_flight_rollouts -= r.K;
+            if (sl.small) s->in_flight_small -= r.K;
             s->scenario_busy[r.scenario] = 0;
             sl.busy = false;
             progressed = true;
@@ -221,12 +226,34 @@ static void worker_loop(vpm_server *s)
                     aged = it;                // the queue is in arrival order
                 if (least == s->queue.end() || it->work < least->work) least = it;
             }
+            // a request fits its lane: the small requests' lane (if enabled) by its own rollouts,
+            // the others by theirs, whatever the other lane holds
+            const long long normal = s->in_flight_rollouts - s->in_flight_small;
+            auto is_small = [&](const Request &q) { return s->cfg.small_rollouts > 0 && q.K <= s->cfg.small_rollouts; };
+            auto fits = [&](const Request &q) {
+                if (is_small(q)) return s->in_flight_small == 0 || s->in_flight_small + q.K <= s->rollout_budget;
+                return normal == 0 || normal + q.K <= s->rollout_budget;
+            };
             auto it = aged != s->queue.end() ? aged : least;
             if (it == s->queue.end()) break;
-            if (s->in_flight_rollouts > 0 && s->in_flight_rollouts + it->K > s->rollout_budget) break;
+            if (!fits(*it)) {
+                // the small requests' lane still admits its least-work candidate
+                auto sm = s->queue.end();
+                for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+                    if (!is_small(*q) || s->scenario_busy[q->scenario] || s->in_flight_bytes + q->bytes > s->budget ||
+                        q->bytes > avail)
+                        continue;
+                    if (sm == s->queue.end() || q->work < sm->work) sm = q;
+                }
+                if (sm == s->queue.end() || !fits(*sm)) break;
+                it = sm;
+            }
+            const bool small = is_small(*it);
             Request r = std::move(*it);
             s->queue.erase(it);
             r.t_start = s->now_ms();
+            free_slot->small = small;
+            free_slot->active = small && free_slot->stream_hi ? free_slot->stream_hi : free_slot->stream;
             vpm_status v = start_request(s, *free_slot, r);
             if (v != VPM_OK) {
                 finish(s, r, v, nullptr, 0.f);
@@ -237,6 +264,7 @@ static void worker_loop(vpm_server *s)
             free_slot->busy = true;
             s->in_flight_bytes += free_slot->req.bytes;
             s->in_flight_rollouts += free_slot->req.K;
+            if (small) s->in_flight_small += free_slot->req.K;
             s->scenario_busy[free_slot->req.scenario] = 1;
             progressed = true;
         }
@@ -257,6 +285,8 @@ static void worker_loop(vpm_server *s)
             Request r = std::move(*it);
             it = s->queue.erase(it);
             r.t_start = s->now_ms();
+            free_slot->small = false;
+            free_slot->active = free_slot->stream;
             vpm_status v = start_request(s, *free_slot, r);
             if (v != VPM_OK) {
                 finish(s, r, v, nullptr, 0.f);
@@ -291,6 +321,8 @@ extern "C" vpm_status vpm_server_create(const vpm_server_config *cfg, vpm_server
         return sfail(VPM_ERR_INVALID, "vpm_server_create: need max_inflight, max_rollouts, max_horizon >= 1");
     if (cfg->policy != VPM_ADMIT_ARRIVAL && cfg->policy != VPM_ADMIT_LEAST_WORK)
         return sfail(VPM_ERR_INVALID, "vpm_server_create: unknown admission policy %d", cfg->policy);
+    if (cfg->small_rollouts < 0 || (cfg->small_rollouts > 0 && cfg->policy != VPM_ADMIT_LEAST_WORK))
+        return sfail(VPM_ERR_INVALID, "vpm_server_create: small_rollouts needs VPM_ADMIT_LEAST_WORK and must be >= 0");
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
         cudaGetLastError();
@@ -312,6 +344,12 @@ extern "C" vpm_status vpm_server_create(const vpm_server_config *cfg, vpm_server
     const size_t pf = (size_t)cfg->max_rollouts * cfg->max_horizon + cfg->max_horizon + cfg->max_rollouts;
     for (auto &sl : s->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (!e && cfg->small_rollouts > 0) {
+            int least = 0, greatest = 0;
+            e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            if (!e) e = cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, greatest);
+        }
+        sl.active = sl.stream;
         if (!e) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (!e) e = cudaMallocHost((void **)&sl.pinned, sizeof(float) * pf);
         if (e) {
@@ -461,6 +499,7 @@ extern "C" vpm_status vpm_server_destroy(vpm_server *s)
     cudaDeviceSynchronize();
     for (auto &sl : s->slots) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.stream_hi) cudaStreamDestroy(sl.stream_hi);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }

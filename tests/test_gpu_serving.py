@@ -171,3 +171,37 @@ def test_unknown_admission_policy_is_rejected():
     torch, V = cuda()
     with pytest.raises(V.VpmError):
         V.Server(max_inflight=1, policy=7)
+
+
+@pytest.mark.parametrize("lane", [False, True])
+def test_small_request_lane_overtakes_a_large_launch(lane):
+    """Least work first with and without the small requests' lane. A request of 4096 rollouts
+    (four waves of blocks) runs; a request of 256 rollouts arrives just after. Without the lane it
+    waits until the large one is done (the device's rollout budget is full); with the lane it is
+    admitted at once on a high-priority stream, its blocks start as the first wave's blocks
+    finish, and it completes before the large request. Its result is the same bits either way."""
+    torch, V = cuda()
+    srv = V.Server(max_inflight=4, max_rollouts=4096, max_horizon=100, policy=V.ADMIT_LEAST_WORK,
+                   small_rollouts=256 if lane else 0)
+    p = W.glider_params()
+    fields = [W.background_field(85, 1000), W.background_field(86, 300)]
+    for f in fields:
+        srv.add_scenario(p, f, W.GLIDER_X0, len(f) + 2 * 100 + 10)
+    ta = srv.submit(0, W.mppi_noise(95, 4096, 100, W.MPPI_SIGMA_U))
+    eps_c = W.mppi_noise(96, 256, 20, W.MPPI_SIGMA_U)
+    tc = srv.submit(1, eps_c)
+    (ra, _), (rc, mu_c) = srv.poll(ta), srv.poll(tc)
+    srv.close()
+    assert ra["status"] == rc["status"] == V.VPM_OK
+    if lane:
+        assert rc["t_done_ms"] < ra["t_done_ms"], (ra, rc)
+    else:
+        assert rc["t_start_ms"] >= ra["t_done_ms"], (ra, rc)
+    mu_d, jmin_d = _direct_mu(V, torch, p, fields[1], eps_c, 10.0)
+    assert np.array_equal(mu_c, mu_d) and rc["j_min"] == jmin_d
+
+
+def test_small_lane_needs_least_work_policy():
+    torch, V = cuda()
+    with pytest.raises(V.VpmError):
+        V.Server(max_inflight=2, small_rollouts=256)
