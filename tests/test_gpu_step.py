@@ -170,6 +170,30 @@ def test_pair_diagonal_other_wake_kernels(ora, kernel, n):
         g.close()
 
 
+@pytest.mark.parametrize("n", [3500, 8000])
+def test_pair_phase_large_fields(ora, n):
+    """Fields above 3000 particles run 512-thread blocks (one per SM) with the once-per-pair
+    diagonal units: one step at n and n + 2 from the oracle's state against the oracle, every
+    particle's convection velocity and advanced position."""
+    torch, V = cuda()
+    params = W.glider_params()
+    snaps, cap = _snapshots(ora, params, W.background_field(60 + n, n), np.array(W.GLIDER_X0), [0, 1])
+    for k, snap, u in snaps:
+        o = oracle_state(ora, params, snap, cap)
+        ref = o.step(u)
+        g = gpu_state(V, params, snap, cap, V.FP32)
+        out = g.step(u, probe=True)
+        torch.cuda.synchronize()
+        n1 = len(ref["vel"])
+        vel = out["vel"].cpu().numpy()[:2 * n1].reshape(-1, 2)
+        msg = "n=%d step %d" % (n, k)
+        assert normwise(vel, ref["vel"]) <= VEL_TOL, msg
+        vmax = np.linalg.norm(ref["vel"], axis=1).max()
+        parts_g = g.read()[0]
+        assert np.abs(parts_g[:, :2] - o.particles[:, :2]).max() <= params["dt"] * VEL_TOL * vmax + 1e-9, msg
+        g.close()
+
+
 def test_step_commits_and_rollout_agree(ora):
     """Ten vpm_step calls advance the resident state exactly as a 10-step rollout does."""
     torch, V = cuda()
