@@ -1078,8 +1078,11 @@ def run_serving(args):
            "config": {"workload": "serving: 16 scenarios, 500-5000 particles, Poisson 50 Hz each, "
                                   "K in {256, 1024, 4096}, H=100", "seconds": T,
                       "offered_requests": int(len(arrivals))}}
-    for label, slots in (("continuous", 16), ("per_request", 1)):
-        out[label] = serve_trace(V, fields, noise, arrivals, streams, sizes, slots)
+    pol = (V.ADMIT_LEAST_WORK, SERVE_MAX_WAIT_MS, SERVE_SMALL_ROLLOUTS) if args.serve_policy == "least_work" \
+        else (V.ADMIT_ARRIVAL, 0.0, 0)
+    out["config"]["policy"] = args.serve_policy
+    out["continuous"] = serve_trace(V, fields, noise, arrivals, streams, sizes, 16, *pol)
+    out["per_request"] = serve_trace(V, fields, noise, arrivals, streams, sizes, 1)
     # sustainable-rate sweep: the same scenarios and request mix at total rates around one GPU's
     # capacity (a request averages ~1.7e12 pair interactions, ~0.5 s of the device); a rate is
     # sustained when no request is superseded and the p99 latency stays within twice the p99
@@ -1088,7 +1091,7 @@ def run_serving(args):
     for rate in args.serve_rates:
         arr, strm = W.poisson_arrivals(11, rate / len(fields), args.serve_sweep_seconds, len(fields))
         ks = W.request_sizes(12, len(arr))
-        r = serve_trace(V, fields, noise, arr, strm, ks, 16)
+        r = serve_trace(V, fields, noise, arr, strm, ks, 16, *pol)
         p99 = r["p99_ms"]
         if base_p99 is None:
             base_p99 = p99
@@ -1158,6 +1161,8 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0, 1.5, 2.0, 3.0],
                     help="total request rates (Hz) of the serving workload's sustainable-rate sweep")
     ap.add_argument("--serve-sweep-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-policy", default="arrival", choices=["arrival", "least_work"],
+                    help="admission of the continuous-batching server in --workload serving")
     ap.add_argument("--rollouts-uneven", type=int, default=4096)
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
     ap.add_argument("--n", type=int, default=1 << 20, help="free-field particle count")
