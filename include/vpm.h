@@ -570,7 +570,8 @@ vpm_status vpm_freefield_heun_noalloc(float *d_particles, int n, int kernel, dou
  * state, projected `latency` steps ahead under the current policy. A plan is `iterations` MPPI
  * reweightings (Eq. 25) of `rollouts` rollouts over the remaining steps, warm-started from the
  * previous nominal controls, and the least-squares / TVLQR synthesis (§IV-B) around the new
- * nominal; its policy takes effect `latency` steps after the replan started.
+ * nominal; its policy takes effect `latency` steps after the replan started, before a replan
+ * due at that same step begins (so that replan projects under the new policy).
  * threaded = 0: the plan runs inside vpm_nmpc_control (deterministic);
  * threaded = 1: a planning thread with its own stream runs it while control continues (the
  *               two-thread split of §IV-C); a replan that falls due while the planner is still
@@ -579,7 +580,9 @@ vpm_status vpm_freefield_heun_noalloc(float *d_particles, int n, int kernel, dou
 typedef struct {
     int horizon;          /* N: steps of the manoeuvre */
     int replan_every;     /* P: steps between replans */
-    int latency;          /* L: projection steps (the replanning time) */
+    int latency;          /* L: projection steps (the replanning time), 0 <= L <= P
+                             (a longer latency would replace a plan before it took effect;
+                             VPM_ERR_INVALID) */
     int rollouts;         /* K: MPPI and synthesis rollouts per plan (>= 6) */
     int iterations;       /* MPPI iterations per plan */
     float lambda;         /* MPPI temperature */

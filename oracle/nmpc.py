@@ -2,8 +2,11 @@
 
 TEST INFRASTRUCTURE: only the tests use this module. It strings together the oracle's pinned
 parts (rollouts, MPPI weights and update, least-squares Jacobians, TVLQR) in the order §IV-C
-gives; it shares nothing with the CUDA library. Parity unpinned beyond those parts: a closed
-loop has no closed form to check against.
+gives; it shares nothing with the CUDA library. A closed loop has no closed form; the loop is
+pinned through the cases that reduce to its pinned parts (the plant equal to the model, no
+latency, a vanishing MPPI temperature, the projection recomputed as a policy rollout from each
+replan's snapshot, the schedule by hand). The tracking instance's wake under an unknown
+disturbance is checked only against its definition restated.
 
 The loop, as read from §IV-C (N steps of a fixed-length manoeuvre, controls u = phidot):
   * a tracking instance of the model follows the plant: at every control step its glider state
@@ -13,8 +16,10 @@ The loop, as read from §IV-C (N steps of a fixed-length manoeuvre, controls u =
     closed-loop policy (the replanning time), then MPPI (`iterations` reweightings of K
     rollouts over the remaining N - t - L steps, warm-started from the previous nominal
     controls) and the least-squares / TVLQR synthesis around the new nominal run from it;
-  * the new policy takes effect at step t + L; the control at step t is
-    ubar_t - H_t (x_t - xbar_t) of the policy in effect.
+  * the new policy takes effect at step t + L (at once when L = 0), before the replan due at
+    that step (when L = P) starts, so that replan projects under it; the control at step t is
+    ubar_t - H_t (x_t - xbar_t) of the policy in effect. L <= P: with a longer latency a plan
+    would be replaced before it took effect.
 Random draws are inputs: per plan p, noise[p] = (eps (iterations, K, N) binary32 MPPI
 perturbations, xi (K, 7) initial-state perturbations, zeta (K, N) binary32 control
 perturbations of the synthesis rollouts); plan p uses the first H_r columns.
@@ -88,8 +93,12 @@ def run(cfg: Config, params: dict, parts, x0, mu0, noise, capacity: int, pair=No
     """Closed loop against a plant model (the same model). With `pair` = (x1, z1, g1, x2, z2,
     g2) the plant's wake holds that disturbance pair from the start; with `compensate` the
     tracking instance holds it too, so the planner knows of it. Returns dict(x (N + 1, 7) plant
-    states, u (N,) applied controls, cost, plans (list of t0))."""
+    states, u (N,) applied controls, cost, plans (list of t0), policies (the plans' Policy
+    objects, in the same order), snapshots (for each replan after the first, the tracking
+    instance's copy with the observed glider state, before its projection))."""
     N, Pn, L = cfg.horizon, cfg.replan_every, cfg.latency
+    if L > Pn:
+        raise ValueError("the latency must not exceed the replanning period")
     tracking = State(params, parts, x0, capacity)
     plant = State(params, parts, x0, capacity)
     if pair is not None:
@@ -97,24 +106,29 @@ def run(cfg: Config, params: dict, parts, x0, mu0, noise, capacity: int, pair=No
         if compensate:
             tracking.inject_pair(*pair)
     mu, pol = plan(cfg, params, tracking.copy(), mu0, 0, noise[0])
-    plans, pending, used = [0], None, 1
+    plans, policies, snapshots, pending, used = [0], [pol], [], None, 1
     xs, us = [plant.xg.copy()], []
     for t in range(N):
         x_obs = plant.xg.copy()
+        if pending is not None and t == pending.t0:
+            pol, pending = pending, None
         if t > 0 and t % Pn == 0 and t + L < N and used < len(noise):
             snap = tracking.copy()
             snap.xg[:] = x_obs
+            snapshots.append(snap.copy())
             for k in range(L):
                 snap.step(pol.control(t + k, snap.xg))
             mu, pending = plan(cfg, params, snap, mu, t + L, noise[used])
             used += 1
             plans.append(t + L)
-        if pending is not None and t == pending.t0:
-            pol, pending = pending, None
+            policies.append(pending)
+            if L == 0:
+                pol, pending = pending, None
         u = pol.control(t, x_obs)
         tracking.xg[:] = x_obs
         tracking.step(u)
         plant.step(u)
         us.append(u)
         xs.append(plant.xg.copy())
-    return dict(x=np.array(xs), u=np.array(us), cost=terminal_cost(params, plant.xg), plans=plans)
+    return dict(x=np.array(xs), u=np.array(us), cost=terminal_cost(params, plant.xg), plans=plans,
+                policies=policies, snapshots=snapshots)

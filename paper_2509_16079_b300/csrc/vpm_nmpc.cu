@@ -220,6 +220,19 @@ void planner_loop(vpm_nmpc *nm)
     }
 }
 
+// The pending policy becomes the active one once its first step is reached.
+vpm_status take_due_plan(vpm_nmpc *nm, int t)
+{
+    std::unique_lock<std::mutex> lk(nm->m, std::defer_lock);
+    if (nm->cfg.threaded) lk.lock();
+    if (nm->cfg.threaded && nm->planner_error != VPM_OK) return nm->planner_error;
+    if (nm->has_pending && t >= nm->pending.t0) {
+        nm->active = std::move(nm->pending);
+        nm->has_pending = false;
+    }
+    return VPM_OK;
+}
+
 bool due(const vpm_nmpc *nm, int t)
 {
     return t > 0 && t % nm->cfg.replan_every == 0 && t + nm->cfg.latency < nm->N &&
@@ -236,7 +249,8 @@ extern "C" vpm_status vpm_nmpc_create(const vpm_nmpc_config *cfg, const vpm_para
 {
     if (!cfg || !params || !h_x0 || !h_mu0 || !h_eps || !h_xi || !h_zeta || !out)
         return fail(VPM_ERR_INVALID, "vpm_nmpc_create: null argument");
-    if (cfg->horizon < 2 || cfg->replan_every < 1 || cfg->latency < 0 || cfg->rollouts < 6 ||
+    if (cfg->horizon < 2 || cfg->replan_every < 1 || cfg->latency < 0 ||
+        cfg->latency > cfg->replan_every || cfg->rollouts < 6 ||
         cfg->iterations < 1 || !(cfg->lambda > 0.f) || !(cfg->rc > 0.0) || n_plans < 1)
         return fail(VPM_ERR_INVALID, "vpm_nmpc_create: bad configuration");
     vpm_nmpc *nm = new vpm_nmpc();
@@ -299,6 +313,10 @@ extern "C" vpm_status vpm_nmpc_control(vpm_nmpc *nm, int t, const double *h_x_ob
         nm->planned = true;
         record_plan(nm, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count());
     }
+    // a plan due at this step takes effect before this step's replan starts, so that the
+    // replan projects under the policy that will be in effect (replan_every == latency), and
+    // again after it, so that a plan made with no latency acts at once
+    NTRY(take_due_plan(nm, t));
     if (due(nm, t)) {
         if (!nm->cfg.threaded) {
             NCUDA(cudaStreamSynchronize(nm->ctl), "control stream");
@@ -330,15 +348,7 @@ extern "C" vpm_status vpm_nmpc_control(vpm_nmpc *nm, int t, const double *h_x_ob
             }
         }
     }
-    {
-        std::unique_lock<std::mutex> lk(nm->m, std::defer_lock);
-        if (nm->cfg.threaded) lk.lock();
-        if (nm->cfg.threaded && nm->planner_error != VPM_OK) return nm->planner_error;
-        if (nm->has_pending && t >= nm->pending.t0) {
-            nm->active = std::move(nm->pending);
-            nm->has_pending = false;
-        }
-    }
+    NTRY(take_due_plan(nm, t));
     const Policy &p = nm->active;
     double u = (double)p.ubar[t];
     for (int c = 0; c < 7; ++c) u -= p.gains[(size_t)t * 7 + c] * (h_x_obs[c] - p.xbar[(size_t)t * 7 + c]);

@@ -67,6 +67,15 @@ def test_host_side_rejections(vlib):
     assert vlib.vpm_probe_rate(V.PROBE_PAIRS_SYM + 1, 1, C.byref(r)) == V.VPM_ERR_INVALID
     assert vlib.vpm_probe_rate(V.PROBE_FFMA, 0, C.byref(r)) == V.VPM_ERR_INVALID
     assert vlib.vpm_probe_rate(V.PROBE_FFMA, 8, C.byref(r)) == V.VPM_ERR_INVALID
+    # NMPC: a latency longer than the replanning period would replace plans before they act
+    N, K = 20, 8
+    noise = W.nmpc_noise(1, 2, 1, K, N)
+    for latency, want in ((6, V.VPM_ERR_INVALID), (-1, V.VPM_ERR_INVALID)):
+        with pytest.raises(V.VpmError) as e:
+            V.NMPC(W.glider_params(), np.zeros((0, 3)), 40, W.GLIDER_X0, np.zeros(N, np.float32),
+                   noise, horizon=N, replan_every=5, latency=latency, rollouts=K, iterations=1,
+                   lam=10.0, qc=W.TVLQR_QC, qf=W.TVLQR_QF, rc=W.TVLQR_RC)
+        assert e.value.status == want and "configuration" in str(e.value)
 
 
 def test_no_silent_cpu_fallback(vlib):

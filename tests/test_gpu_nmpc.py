@@ -45,21 +45,24 @@ def test_closed_loop_rollouts_and_advance_match_oracle(ora):
     st.close()
 
 
-def _cfg(N, threaded=False):
-    return dict(horizon=N, replan_every=10, latency=5, rollouts=16, iterations=2, lam=10.0,
+def _cfg(N, threaded=False, latency=5):
+    return dict(horizon=N, replan_every=10, latency=latency, rollouts=16, iterations=2, lam=10.0,
                 qc=W.TVLQR_QC, qf=W.TVLQR_QF, rc=W.TVLQR_RC, threaded=threaded)
 
 
-@pytest.mark.parametrize("pair", [None, "uncompensated", "compensated"])
-def test_nmpc_synchronous_matches_oracle(ora, pair):
+@pytest.mark.parametrize("pair,latency", [(None, 5), ("uncompensated", 5), ("compensated", 5),
+                                          ("uncompensated", 10), ("uncompensated", 0)])
+def test_nmpc_synchronous_matches_oracle(ora, pair, latency):
+    """latency 10 = the replanning period: each plan takes effect at the step the next replan
+    starts and that replan projects under it; latency 0: each plan acts at once."""
     torch, V = cuda()
     p = dict(W.glider_params(), n_wake_max=60)
     N = 40
-    c = _cfg(N)
+    c = _cfg(N, latency=latency)
     noise = W.nmpc_noise(41, 4, c["iterations"], c["rollouts"], N)
     field, x0, mu0 = np.zeros((0, 3)), np.array(W.GLIDER_X0), np.zeros(N, np.float32)
     ring = (2.5, 0.3, -1.0, 2.5, -0.3, 1.0) if pair else None
-    ref = ON.run(ON.Config(N, 10, 5, 16, 2, 10.0, W.TVLQR_QC, W.TVLQR_QF, W.TVLQR_RC),
+    ref = ON.run(ON.Config(N, 10, latency, 16, 2, 10.0, W.TVLQR_QC, W.TVLQR_QF, W.TVLQR_RC),
                  p, field, x0, mu0.astype(np.float64), noise, 64, pair=ring,
                  compensate=pair == "compensated")
     nm = V.NMPC(p, field, 64, x0, mu0, noise, precision=V.FP64, **c)
@@ -77,7 +80,7 @@ def test_nmpc_synchronous_matches_oracle(ora, pair):
     st = nm.stats()
     nm.close()
     plant.close()
-    assert st["plans_done"] == len(ref["plans"]) == 4
+    assert st["plans_done"] == len(ref["plans"]) == {0: 4, 5: 4, 10: 3}[latency]
     assert np.abs(np.array(us) - ref["u"]).max() <= 1e-5 * (1.0 + np.abs(ref["u"]).max())
     assert np.abs(np.array(xs) - ref["x"]).max() <= 1e-6
 

@@ -6,11 +6,15 @@ surface system and Kelvin's row (Eqs. 6-11), the pressure jump and loads (Eqs. 1
 decay and merging (Eqs. 16-17), the glider's elevator force, moment arms and equations of motion
 (Eqs. 18-22), the terminal cost (Eq. 24), MPPI (Eq. 25), the separation gate or the linear solve. It
 builds the copy with the oracle's own compiler flags into a temporary directory and runs the
-oracle's pin tests against it (ORACLE_LIB). Each mutant must fail at least one pin. Host only; the
-oracle under oracle/ is not modified.
+oracle's pin tests against it (ORACLE_LIB). The Python parts of the oracle (the tracking policy of
+§IV-B in oracle/policy.py, the NMPC loop of §IV-C in oracle/nmpc.py) get the same treatment: each
+case edits a copy of the oracle, the tests and the input generators in a temporary directory and
+runs the pins there. Each mutant must fail at least one pin. Host only; the oracle under oracle/ is
+not modified.
 """
 import glob
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -80,6 +84,54 @@ MUTATIONS = [
  ("MPPI update transposed", "s += w[i] * xi[(size_t)i * H + k];", "s += w[i] * xi[(size_t)k * K + i];"),
 ]
 
+# (name, file under oracle/, [(exact text, replacement), ...])
+PY_MUTATIONS = [
+    ("policy law: feedback sign", "policy.py",
+     [("return float(ubar[k]) - float(", "return float(ubar[k]) + float(")]),
+    ("policy rollout: feedback sign", "policy.py",
+     [("u = float(ubar[j]) - float(np.asarray(gains[j])", "u = float(ubar[j]) + float(np.asarray(gains[j])")]),
+    ("policy rollout: policy rows one step ahead", "policy.py",
+     [("        j = offset + k\n", "        j = min(offset + k + 1, len(gains) - 1)\n")]),
+    ("policy rollout: nominal states one step behind", "policy.py",
+     [("(s.xg - np.asarray(xbar[j])))", "(s.xg - np.asarray(xbar[max(j - 1, 0)])))")]),
+    ("Euler discretisation: B not scaled by dt", "policy.py",
+     [("return np.eye(STATE) + dt * A, dt * B", "return np.eye(STATE) + dt * A, B")]),
+    ("TVLQR: control weight dropped", "policy.py", [("denom = rc + B @ Sn @ B", "denom = B @ Sn @ B")]),
+    ("TVLQR: running cost dropped", "policy.py",
+     [("np.outer(A.T @ Sn @ B, B @ Sn @ A) / denom + Qc", "np.outer(A.T @ Sn @ B, B @ Sn @ A) / denom")]),
+    ("least squares: derivative of the nominal one step late", "policy.py",
+     [("xbar_dot = (xbar[k + 1] - xbar[k]) / dt", "xbar_dot = (xbar[min(k + 2, len(xbar) - 1)] - xbar[k + 1]) / dt")]),
+    ("structure: kinematic identity on the positions", "policy.py",
+     [("A[0, 4] = A[1, 5] = A[2, 6] = 1.0", "A[0, 0] = A[1, 1] = A[2, 2] = 1.0")]),
+    ("NMPC: policy rows one step ahead", "nmpc.py",
+     [("        j = t - self.t0\n", "        j = min(t - self.t0 + 1, len(self.gains) - 1)\n")]),
+    ("NMPC: a plan takes effect the step after it is made", "nmpc.py",
+     [("        if pending is not None and t == pending.t0:\n", "        if pending is not None:\n")]),
+    ("NMPC: a due plan takes effect after the replan of its step", "nmpc.py",
+     [("        if pending is not None and t == pending.t0:\n            pol, pending = pending, None\n"
+       "        if t > 0", "        if t > 0"),
+      ("        u = pol.control(t, x_obs)\n", "        if pending is not None and t == pending.t0:\n"
+       "            pol, pending = pending, None\n        u = pol.control(t, x_obs)\n")]),
+    ("NMPC: a plan made with no latency waits a step", "nmpc.py",
+     [("            if L == 0:\n                pol, pending = pending, None\n", "")]),
+    ("NMPC: projection one step short", "nmpc.py", [("            for k in range(L):\n", "            for k in range(max(L - 1, 0)):\n")]),
+    ("NMPC: projection under the nominal controls alone", "nmpc.py",
+     [("snap.step(pol.control(t + k, snap.xg))", "snap.step(float(pol.ubar[t + k]))")]),
+    ("NMPC: projection from the tracking instance's own glider state", "nmpc.py",
+     [("            snap.xg[:] = x_obs\n", "")]),
+    ("NMPC: tracking instance not reset to the observed state", "nmpc.py",
+     [("        tracking.xg[:] = x_obs\n", "")]),
+    ("NMPC: warm start from the initial controls", "nmpc.py",
+     [("plan(cfg, params, snap, mu, t + L, noise[used])", "plan(cfg, params, snap, mu0, t + L, noise[used])")]),
+    ("NMPC: a replan reuses the previous plan's draws", "nmpc.py",
+     [("plan(cfg, params, snap, mu, t + L, noise[used])", "plan(cfg, params, snap, mu, t + L, noise[used - 1])")]),
+    ("NMPC: perturbations indexed by absolute step", "nmpc.py", [("eps[it][:, :Hr]", "eps[it][:, t0:]")]),
+    ("NMPC: nominal states without the snapshot's state", "nmpc.py",
+     [('xbar = np.vstack([snap.xg, nom["traj"]])', 'xbar = np.vstack([nom["traj"][:1], nom["traj"]])')]),
+    ("NMPC: replan at t = 0", "nmpc.py", [("if t > 0 and t % Pn == 0", "if t % Pn == 0")]),
+    ("NMPC: replan while t + L <= N", "nmpc.py", [("t + L < N and used", "t + L <= N - 1 + (L > 0) and used")]),
+]
+
 
 def _mutant(tmp, k, old, new):
     src = open(SRC).read()
@@ -92,10 +144,27 @@ def _mutant(tmp, k, old, new):
     return lib
 
 
-def _pins_against(lib):
+def _py_mutant(tmp, k, rel, edits):
+    """A copy of oracle/, tests/, workloads/ and pytest.ini with the edits made to oracle/rel."""
+    dst = os.path.join(tmp, "py%d" % k)
+    skip = shutil.ignore_patterns("__pycache__", "*.so", "*.tmp*")
+    for d in ("oracle", "tests", "workloads"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(dst, d), ignore=skip)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), dst)
+    path = os.path.join(dst, "oracle", rel)
+    src = open(path).read()
+    for old, new in edits:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    open(path, "w").write(src)
+    return dst
+
+
+def _pins_against(lib, cwd=ROOT):
     env = dict(os.environ, ORACLE_LIB=lib)
+    env.pop("PYTHONPATH", None)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "-m", "not gpu"] + PINS, cwd=ROOT, env=env, capture_output=True, text=True,
+                        "-m", "not gpu"] + PINS, cwd=cwd, env=env, capture_output=True, text=True,
                        timeout=600)
     return r.returncode, r.stdout[-400:]
 
@@ -108,4 +177,19 @@ def test_every_single_term_mutation_fails_a_pin():
     survivors = [(name, out) for (name, _, _), (rc, out) in zip(MUTATIONS, results) if rc == 0]
     assert not survivors, survivors
     # every run failed a test, none died on something else
+    assert all(rc == 1 for rc, _ in results), [out for rc, out in results if rc != 1]
+
+
+def test_every_python_oracle_mutation_fails_a_pin(ora):
+    lib = ora.build()
+    with tempfile.TemporaryDirectory() as tmp:
+        dirs = [_py_mutant(tmp, k, rel, edits) for k, (_, rel, edits) in enumerate(PY_MUTATIONS)]
+        # the unmodified copy passes, so the failures below come from the edits
+        clean = _py_mutant(tmp, len(PY_MUTATIONS), "nmpc.py", [])
+        with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+            results = list(ex.map(lambda d: _pins_against(lib, d), dirs + [clean]))
+    assert results[-1][0] == 0, results[-1][1]
+    results = results[:-1]
+    survivors = [(name, out) for (name, _, _), (rc, out) in zip(PY_MUTATIONS, results) if rc == 0]
+    assert not survivors, survivors
     assert all(rc == 1 for rc, _ in results), [out for rc, out in results if rc != 1]
