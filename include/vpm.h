@@ -313,7 +313,10 @@ vpm_status vpm_rollout_batch_per_launch(const vpm_state *root, int K, int H,
 /*
  * MPPI weights of §IV-A, Eq. 25: w_i = eta exp(-(J_i - J_min) / lambda), eta normalising the
  * sum to 1. d_costs[K] binary32 in, d_weights[K] binary32 out; exponentials and sums in
- * binary64 in a fixed order (deterministic). Errors: VPM_ERR_INVALID (K < 1, lambda <= 0).
+ * binary64 in a fixed order (deterministic). J_min and the sum run over the finite costs; a
+ * cost that is NaN or infinite (vpm_rollout_batch stores NaN for a rollout that diverged) gets
+ * weight 0, the limit of Eq. 25 as its cost grows without bound. If no cost is finite every
+ * weight is NaN. Errors: VPM_ERR_INVALID (K < 1, lambda <= 0).
  */
 vpm_status mppi_weights(const float *d_costs, int K, float lambda, float *d_weights,
                         cudaStream_t stream);

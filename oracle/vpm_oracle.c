@@ -639,13 +639,18 @@ int ora_rollout(const ora_params *p, int capacity, int n0, const double *x0, con
 
 /* ------------------------------------------------------------------ MPPI (§IV-A, Eq. 25) */
 
-/* w_i = eta exp(-(J_i - J_min)/lambda), eta = 1 / sum_i exp(-(J_i - J_min)/lambda). */
+/* w_i = eta exp(-(J_i - J_min)/lambda), eta = 1 / sum_i exp(-(J_i - J_min)/lambda), J_min and
+ * the sum over the finite costs. A cost that is not finite (a rollout that diverged) takes the
+ * limit of Eq. 25 as J_i -> +inf: weight 0. With no finite cost every weight is NaN. */
 void ora_mppi_weights(int K, const double *J, double lambda, double *w)
 {
-    double jmin = J[0];
-    for (int i = 1; i < K; ++i) if (J[i] < jmin) jmin = J[i];
+    double jmin = INFINITY;
+    int finite = 0;
+    for (int i = 0; i < K; ++i)
+        if (isfinite(J[i])) { finite = 1; if (J[i] < jmin) jmin = J[i]; }
+    if (!finite) { for (int i = 0; i < K; ++i) w[i] = NAN; return; }
     double s = 0.0;
-    for (int i = 0; i < K; ++i) { w[i] = exp(-(J[i] - jmin) / lambda); s += w[i]; }
+    for (int i = 0; i < K; ++i) { w[i] = isfinite(J[i]) ? exp(-(J[i] - jmin) / lambda) : 0.0; s += w[i]; }
     double eta = 1.0 / s;
     for (int i = 0; i < K; ++i) w[i] *= eta;
 }

@@ -33,22 +33,31 @@ struct SumOp {
     __device__ double operator()(double a, double b) const { return a + b; }
 };
 
-// w_i = exp(-(J_i - J_min) / lambda) / sum_j exp(-(J_j - J_min) / lambda). One block.
+// w_i = exp(-(J_i - J_min) / lambda) / sum_j exp(-(J_j - J_min) / lambda), J_min and the sum
+// over the finite costs. A cost that is not finite (a rollout that diverged; the rollout kernel
+// stores NaN) takes the limit of Eq. 25 as J_i -> +inf: weight 0. With no finite cost every
+// weight is NaN. One block.
 __global__ void __launch_bounds__(kMppiThreads) mppi_weights_kernel(const float *J, int K,
-                                                                    double lambda, float *w)
+                                                                   double lambda, float *w)
 {
     __shared__ double sd[32];
     __shared__ float sf[32];
     float m = INFINITY;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) m = fminf(m, J[i]);
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+        if (isfinite(J[i])) m = fminf(m, J[i]);
     m = block_reduce(m, MinOp(), (float)INFINITY, sf);
+    if (!isfinite(m)) {
+        for (int i = threadIdx.x; i < K; i += blockDim.x) w[i] = __int_as_float(0x7fc00000);
+        return;
+    }
     const double jmin = (double)m;
     double s = 0.0;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) s += exp(-((double)J[i] - jmin) / lambda);
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+        if (isfinite(J[i])) s += exp(-((double)J[i] - jmin) / lambda);
     s = block_reduce(s, SumOp(), 0.0, sd);
     const double eta = 1.0 / s;
     for (int i = threadIdx.x; i < K; i += blockDim.x)
-        w[i] = (float)(exp(-((double)J[i] - jmin) / lambda) * eta);
+        w[i] = isfinite(J[i]) ? (float)(exp(-((double)J[i] - jmin) / lambda) * eta) : 0.f;
 }
 
 // mu[k] = sum_i w_i xi[i, k]. Block (32, 32): x indexes k (coalesced rows), y strides over i.

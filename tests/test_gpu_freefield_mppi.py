@@ -78,6 +78,27 @@ def test_mppi_weights(ora, K):
         assert abs(w.astype(np.float64).sum() - 1.0) <= 1e-5
 
 
+@pytest.mark.parametrize("K", [5, 1024, 5000])
+def test_mppi_weights_with_diverged_rollouts(ora, K):
+    """Costs that are NaN (a diverged rollout) or infinite get weight 0 on both sides; the
+    others match the oracle; with no finite cost every weight is NaN."""
+    torch, V = cuda()
+    J = W.costs_synthetic(K + 7, K)
+    rng = np.random.default_rng(K)
+    bad = rng.choice(K, size=max(2, K // 50), replace=False)
+    J[bad[0::3]] = np.nan
+    J[bad[1::3]] = np.inf
+    J[bad[2::3]] = -np.inf
+    w = V.mppi_weights(torch.tensor(J, device="cuda"), 10.0).cpu().numpy()
+    ref = ora.mppi_weights(J.astype(np.float64), 10.0)
+    assert np.all(w[bad] == 0.0) and np.all(ref[bad] == 0.0)
+    assert np.abs(w - ref).max() <= W_TOL
+    assert abs(w.astype(np.float64).sum() - 1.0) <= 1e-5
+    none = np.full(K, np.nan, np.float32)
+    none[: K // 2] = np.inf
+    assert np.isnan(V.mppi_weights(torch.tensor(none, device="cuda"), 10.0).cpu().numpy()).all()
+
+
 @pytest.mark.parametrize("K,H", [(1, 1), (16, 100), (1024, 100), (4096, 37)])
 def test_mppi_update_and_perturb(ora, K, H):
     torch, V = cuda()

@@ -182,6 +182,26 @@ def test_mppi_weights_properties(ora):
     assert w0[J.argmin()] == pytest.approx(1.0) and w0.sum() == pytest.approx(1.0)
 
 
+def test_mppi_weights_exclude_diverged_rollouts(ora):
+    """Eq. 25 sends a weight to 0 as its cost grows without bound; a cost that is not finite
+    (NaN from a rollout that diverged, or an infinity) gets weight 0, and the other weights are
+    those of the finite costs alone, bit for bit. With no finite cost the weights are NaN."""
+    J = W.costs_synthetic(3, 64).astype(np.float64)
+    bad = [0, 5, 17, 63]
+    Jb = J.copy()
+    Jb[bad] = [np.nan, np.inf, -np.inf, np.nan]
+    keep = np.setdiff1d(np.arange(len(J)), bad)
+    for lam in (0.5, 10.0):
+        w = ora.mppi_weights(Jb, lam)
+        assert np.all(w[bad] == 0.0)
+        assert np.array_equal(w[keep], ora.mppi_weights(J[keep], lam))
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)
+    # a non-finite cost below every finite one does not move J_min
+    Jc = np.array([np.nan, 2.0, 3.0, -np.inf])
+    assert ora.mppi_weights(Jc, 1.0)[1] == pytest.approx(1.0 / (1.0 + math.exp(-1.0)), rel=1e-14)
+    assert np.isnan(ora.mppi_weights(np.array([np.nan, np.inf]), 1.0)).all()
+
+
 def test_mppi_two_sample_closed_form(ora):
     J = np.array([3.0, 5.5])
     lam = 2.0

@@ -76,7 +76,10 @@ MUTATIONS = [
  ("merge averages the circulation", "g[d] = g[d] + g[d + 1];", "g[d] = 0.5 * (g[d] + g[d + 1]);"),
  ("gravity sign", "f[5] = (fwz + fez) / p->mass - p->g;", "f[5] = (fwz + fez) / p->mass + p->g;"),
  ("pitch divided by the mass", "f[6] = torque / p->inertia;", "f[6] = torque / p->mass;"),
- ("MPPI exponent sign", "w[i] = exp(-(J[i] - jmin) / lambda);", "w[i] = exp((J[i] - jmin) / lambda);"),
+ ("MPPI exponent sign", "? exp(-(J[i] - jmin) / lambda) : 0.0;", "? exp((J[i] - jmin) / lambda) : 0.0;"),
+ ("MPPI: a diverged rollout keeps a weight", "? exp(-(J[i] - jmin) / lambda) : 0.0;", "? exp(-(J[i] - jmin) / lambda) : 1e-300;"),
+ ("MPPI: J_min taken over every cost", "if (isfinite(J[i])) { finite = 1; if (J[i] < jmin) jmin = J[i]; }",
+  "{ finite |= isfinite(J[i]) != 0; if (J[i] < jmin) jmin = J[i]; }"),
  ("MPPI not normalised", "double eta = 1.0 / s;", "double eta = 1.0;"),
  ("cost weights squared", "J += d * p->q[k] * d;", "J += d * p->q[k] * p->q[k] * d;"),
  ("gate mode 2 stops the TEV too", "int shed_tev = (p->shed_gate != 1) || open;", "int shed_tev = (p->shed_gate == 0) || open;"),
