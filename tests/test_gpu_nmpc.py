@@ -85,6 +85,40 @@ def test_nmpc_synchronous_matches_oracle(ora, pair, latency):
     assert np.abs(np.array(xs) - ref["x"]).max() <= 1e-6
 
 
+@pytest.mark.parametrize("latency", [5, 10])
+def test_nmpc_threaded_matches_synchronous_when_the_planner_keeps_up(latency):
+    """With control calls spaced well beyond a plan's time, every plan of the two-thread form
+    is ready before its first step: it takes the same snapshot, policy and draws as the
+    synchronous form, so the applied controls and the plant agree bit for bit."""
+    import time
+    torch, V = cuda()
+    p = dict(W.glider_params(), n_wake_max=60)
+    N = 40
+    noise = W.nmpc_noise(43, 4, 2, 16, N)
+    x0 = np.array(W.GLIDER_X0)
+    ring = (2.5, 0.3, -1.0, 2.5, -0.3, 1.0)
+    runs = []
+    for threaded in (False, True):
+        nm = V.NMPC(p, np.zeros((0, 3)), 64, x0, np.zeros(N, np.float32), noise, precision=V.FP64,
+                    **_cfg(N, threaded=threaded, latency=latency))
+        plant = V.State(p, np.zeros((0, 3)), x0, 64, V.FP64)
+        plant.inject_pair(*ring)
+        us = []
+        for t in range(N):
+            us.append(nm.control(t, plant.glider()))
+            plant.step(us[-1])
+            if threaded:
+                time.sleep(0.03)
+        st = nm.stats()
+        runs.append((np.array(us), plant.glider(), st))
+        nm.close()
+        plant.close()
+    (u0, x_0, s0), (u1, x_1, s1) = runs
+    assert s1["plans_skipped"] == 0 and s1["plans_done"] == s0["plans_done"] >= 3
+    assert np.array_equal(u0, u1)
+    assert np.array_equal(x_0, x_1)
+
+
 def test_nmpc_threaded_completes():
     """The two-thread form: planning on its own thread and stream while control continues.
     Timing decides which replans run, so only completion and sanity are checked."""
