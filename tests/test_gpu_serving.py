@@ -12,9 +12,9 @@ pytestmark = pytest.mark.gpu
 SIZES = [300, 500, 800, 400, 1000, 600]
 
 
-def _server(V, max_inflight, budget=0, H=20, max_rollouts_inflight=0):
+def _server(V, max_inflight, budget=0, H=20, max_rollouts_inflight=0, **admission):
     srv = V.Server(max_inflight=max_inflight, max_rollouts=2048, max_horizon=100, hbm_budget=budget,
-                   max_inflight_rollouts=max_rollouts_inflight)
+                   max_inflight_rollouts=max_rollouts_inflight, **admission)
     p = W.glider_params()
     fields = [W.background_field(50 + i, n) for i, n in enumerate(SIZES)]
     for f in fields:
@@ -30,10 +30,16 @@ def _direct_mu(V, torch, p, field, eps, lam):
     return mu.cpu().numpy(), out["costs"].min().item()
 
 
-def test_same_result_alone_in_mix_and_per_request():
+@pytest.mark.parametrize("admission", ["arrival", "least_work", "least_work_lane"])
+def test_same_result_alone_in_mix_and_per_request(admission):
+    """Under every admission policy (least work first with the small-request lane runs the
+    128-rollout request on its own high-priority stream) the result does not depend on what
+    else is on the device."""
     torch, V = cuda()
     eps_x = W.mppi_noise(1, 128, 20, W.MPPI_SIGMA_U)
-    srv, p, fields = _server(V, 8, max_rollouts_inflight=100000)
+    kw = {"arrival": {}, "least_work": dict(policy=V.ADMIT_LEAST_WORK),
+          "least_work_lane": dict(policy=V.ADMIT_LEAST_WORK, small_rollouts=256)}[admission]
+    srv, p, fields = _server(V, 8, max_rollouts_inflight=100000, **kw)
     res_a, mu_a = srv.poll(srv.submit(0, eps_x))
     assert res_a["status"] == V.VPM_OK
     # the same request among others on the device
