@@ -108,7 +108,7 @@ def test_nmpc_threaded_matches_synchronous_when_the_planner_keeps_up(latency):
             us.append(nm.control(t, plant.glider()))
             plant.step(us[-1])
             if threaded:
-                time.sleep(0.03)
+                time.sleep(0.05)
         st = nm.stats()
         runs.append((np.array(us), plant.glider(), st))
         nm.close()
