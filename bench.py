@@ -454,11 +454,11 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = job_throughput(pairs_iter * e2e_steps, world, e2e_s)
 
-    northstar = None
-    if args.northstar_replans > 0:
+    replan2000 = None
+    if args.replan2000_replans > 0:
         with ClockSampler(local) as clk_ns:
-            northstar = northstar_replans(V, torch, args.n0, args.northstar_replans, args.per_launch_subset)
-        northstar["clocks"] = clk_ns.summary()
+            replan2000 = replans_2000_particles(V, torch, args.n0, args.replan2000_replans, args.per_launch_subset)
+        replan2000["clocks"] = clk_ns.summary()
 
     serving = None
     if args.serve_line_seconds > 0 and world == 1:
@@ -514,8 +514,8 @@ def run_gpu(args):
                      "rollout_ms": statistics.mean(roll_ms)},
         "clocks": clocks,
     }
-    if northstar is not None:
-        line["northstar_replan_ms"] = northstar
+    if replan2000 is not None:
+        line["replan2000_ms"] = replan2000
     if serving is not None:
         line["serving"] = serving
     if not args.no_cpu_baseline and world == 1:
@@ -851,7 +851,7 @@ def run_plate(args):
         "clocks": clk.summary()}), flush=True)
 
 
-def northstar_replans(V, torch, n0: int, replans: int, per_launch_subset: int):
+def replans_2000_particles(V, torch, n0: int, replans: int, per_launch_subset: int):
     """Replan latency at K = 1024 rollouts x H = 100 steps with ~2000-particle fields (n0 -> n0 +
     200), three MPPI iterations per replan: eager launches and one CUDA graph replayed, against the
     one-rollout-per-launch form. The latter issues K x H single-block launches per iteration on
@@ -926,14 +926,14 @@ def northstar_replans(V, torch, n0: int, replans: int, per_launch_subset: int):
         "speedup_p50": 3 * per_launch_iter_ms / p50}
 
 
-def run_northstar(args):
-    """The spec replan latency alone (see northstar_replans)."""
+def run_replan2000(args):
+    """The replan latency on ~2000-particle fields alone (see replans_2000_particles)."""
     import torch
     import paper_2509_16079_b300 as V
     from paper_2509_16079_b300 import build
     build.build()
     with ClockSampler(0) as clk:
-        r = northstar_replans(V, torch, args.n0, args.replans, args.per_launch_subset)
+        r = replans_2000_particles(V, torch, args.n0, args.replans, args.per_launch_subset)
     print(json.dumps({"metric": "MPPI replan latency (3 iterations)", "unit": "ms",
                       "higher_is_better": False, **r, "clocks": clk.summary()}), flush=True)
 
@@ -1162,7 +1162,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "northstar", "uneven", "serving", "alu", "table1", "policy", "nmpc", "plate"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "replan2000", "uneven", "serving", "alu", "table1", "policy", "nmpc", "plate"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0, 1.5, 2.0, 3.0],
                     help="total request rates (Hz) of the serving workload's sustainable-rate sweep")
@@ -1173,10 +1173,10 @@ def main():
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
     ap.add_argument("--n", type=int, default=1 << 20, help="free-field particle count")
     ap.add_argument("--ff-steps", type=int, default=10)
-    ap.add_argument("--n0", type=int, default=1900, help="north-star root field size")
+    ap.add_argument("--n0", type=int, default=1900, help="root field size of the ~2000-particle replans")
     ap.add_argument("--per-launch-subset", type=int, default=16)
-    ap.add_argument("--northstar-replans", type=int, default=200,
-                    help="north-star replans timed in the main line (0: skip)")
+    ap.add_argument("--replan2000-replans", type=int, default=200,
+                    help="replans of ~2000-particle fields timed in the main line (0: skip)")
     ap.add_argument("--rollouts", type=int, default=K_ROLL)
     ap.add_argument("--profile-n0", type=int, default=N0, help="root field size of --profile-case")
     ap.add_argument("--serve-line-seconds", type=float, default=8.0,
@@ -1190,8 +1190,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "freefield":
         run_freefield(args)
-    elif args.workload == "northstar":
-        run_northstar(args)
+    elif args.workload == "replan2000":
+        run_replan2000(args)
     elif args.workload == "uneven":
         run_uneven(args)
     elif args.workload == "serving":

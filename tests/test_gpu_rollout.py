@@ -344,7 +344,7 @@ def test_full_size_batch_properties(ora):
     assert normwise(vel, ref["vel"]) <= VEL_TOL
 
 
-def test_north_star_size_batch_properties(ora):
+def test_2000_particle_batch_properties(ora):
     """K = 1024 rollouts x 100 steps from 1900 particles (fields up to 2100), the replan
     benchmark's launch (256-thread blocks, more than one wave, one evaluation per pair across
     16 rows): counts and costs, sampled rollouts rerun alone bitwise, and a step from a sampled
