@@ -235,7 +235,7 @@ def cpu_baseline(rollouts: int = 16, threads: int | None = None, V=None):
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     oracle.build()
-    p, field, xg0, eps = W.mppi_c2(0, K=rollouts, H=H, n=N0)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=rollouts, H=H, n=N0)
     cap = N0 + 2 * H
     threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
@@ -360,7 +360,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     V.lib()
 
-    p, field, xg0, eps_np = W.mppi_c2(rank, K=K_ROLL, H=H, n=N0)
+    p, field, xg0, eps_np = W.mppi_batch_inputs(rank, K=K_ROLL, H=H, n=N0)
     n_iter_noise = 4
     eps_all = [torch.tensor(W.mppi_noise(1000 + 7 * j + rank, K_ROLL, H, W.MPPI_SIGMA_U), device=dev)
                for j in range(n_iter_noise)]
@@ -478,8 +478,8 @@ def run_gpu(args):
     roll_avg_s = statistics.mean(roll_ms) / 1e3
     achieved = pairs_iter * FLOPS_PER_PAIR / roll_avg_s / 1e12
     peak = fp32_peak_tflops()
-    traffic = profiled_traffic("rollout_kernel_mppi_c2.md", "vpm_rollout.cu")
-    pipes = profiled_pipes("rollout_kernel_mppi_c2.md", "vpm_rollout.cu")
+    traffic = profiled_traffic("rollout_kernel_mppi_batch.md", "vpm_rollout.cu")
+    pipes = profiled_pipes("rollout_kernel_mppi_batch.md", "vpm_rollout.cu")
     line = {
         "metric": "Biot-Savart pair-interactions/s",
         "value": value,
@@ -530,7 +530,7 @@ def run_profile_case(args):
     from paper_2509_16079_b300 import build
     build.build()
     K, Hh, n0 = args.rollouts, args.horizon, args.profile_n0
-    p, field, xg0, _ = W.mppi_c2(0, K=1, H=1, n=n0)
+    p, field, xg0, _ = W.mppi_batch_inputs(0, K=1, H=1, n=n0)
     eps = torch.tensor(W.mppi_noise(1000, K, Hh, W.MPPI_SIGMA_U), device="cuda")
     root = V.State(p, field, xg0, n0 + 2 * Hh, V.FP32)
     mu = torch.zeros(Hh, dtype=torch.float32, device="cuda")
@@ -800,7 +800,7 @@ def run_nmpc(args):
 
 
 def run_plate(args):
-    """Configuration 1: the fixed flat plate at 45 degrees in a unit stream with the disturbance pair
+    """The fixed flat plate at 45 degrees in a unit stream with the disturbance pair
     (Gaussian core 0.05 c, no decay, shedding every step), 200 steps in binary64 on the GPU, one
     block; the FP64 oracle runs the same input on the host for the error and the CPU time."""
     import torch
@@ -809,9 +809,9 @@ def run_plate(args):
     import oracle
     build.build()
     oracle.build()
-    p = W.plate_c1_params()
+    p = W.fixed_plate_params()
     steps = 200
-    parts, xg, cap = W.plate_c1_initial(0, steps)
+    parts, xg, cap = W.fixed_plate_initial(0, steps)
     st = V.State(p, parts, xg, cap, V.FP64)
     zero = torch.zeros((1, steps), dtype=torch.float32, device="cuda")
     st.rollout_batch(zero, want_final=False)                      # warm-up
@@ -857,7 +857,7 @@ def replans_2000_particles(V, torch, n0: int, replans: int, per_launch_subset: i
     one-rollout-per-launch form. The latter issues K x H single-block launches per iteration on
     one stream, so its time is linear in K: it is timed on per_launch_subset rollouts and scaled."""
     K, Hh = 1024, 100
-    p, field, xg0, _ = W.mppi_c2(0, K=1, H=1, n=n0)
+    p, field, xg0, _ = W.mppi_batch_inputs(0, K=1, H=1, n=n0)
     root = V.State(p, field, xg0, n0 + 2 * Hh, V.FP32)
     eps = [torch.tensor(W.mppi_noise(3000 + j, K, Hh, W.MPPI_SIGMA_U), device="cuda") for j in range(3)]
     mu = torch.zeros(Hh, dtype=torch.float32, device="cuda")

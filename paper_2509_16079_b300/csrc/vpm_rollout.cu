@@ -1740,7 +1740,7 @@ int uneven_blocks_per_sm(int precision, int kernel, int nt, int dt, size_t smem)
 
 // ------------------------------------------------------------------ one binary64 rollout per cluster
 
-// A few binary64 rollouts (a single simulation, configuration 1) spread over a thread-block
+// A few binary64 rollouts (a single simulation, such as the fixed plate in a stream) spread over a thread-block
 // cluster: every CTA holds the whole field; the plate-point sums and the convection targets are
 // split across the CTAs, each CTA broadcasts its results (plate velocities, advected records) to
 // every CTA's shared memory through distributed shared memory, and hardware cluster barriers

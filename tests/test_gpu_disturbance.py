@@ -12,8 +12,8 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("precision", [1, 0])
 def test_pair_terminated_at_the_same_step(ora, precision):
     torch, V = cuda()
-    p = W.plate_c1_params()
-    pair, xg, cap = W.plate_c1_initial(1)
+    p = W.fixed_plate_params()
+    pair, xg, cap = W.fixed_plate_initial(1)
     o = ora.State(p, np.zeros((0, 3)), xg, cap)
     o.inject_pair(*pair[0], *pair[1])
     g = V.State(p, np.zeros((0, 3)), xg, cap, precision)

@@ -83,7 +83,7 @@ def test_fp64_ungated(ora, H, min_conditioned):
     move by 1e-13, so the check is conditioning-aware (_conditioned_check): pointwise where the
     oracle's result is well conditioned, within 100 times its own movement everywhere."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(0, K=16, H=H, n=1000)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=16, H=H, n=1000)
     res = _run_gpu(V, torch, p, field, xg0, eps, V.FP64)
     assert (res["count"] == 1000 + 2 * H).all()
     assert len(_conditioned_check(ora, p, field, xg0, eps, res, 1e-13, 1e-6, 1e-6)) >= min_conditioned
@@ -98,7 +98,7 @@ def test_fp32_lev_gated_100_steps(ora):
     and the cost are compared too."""
     from concurrent.futures import ThreadPoolExecutor
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(0, K=8, H=100, n=1000)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=8, H=100, n=1000)
     p = dict(p, shed_gate=2)
     res = _run_gpu(V, torch, p, field, xg0, eps, V.FP32)
     cap = len(field) + 200
@@ -126,9 +126,9 @@ def test_fp32_lev_gated_100_steps(ora):
 def test_fp64_plate_c1_200_steps(ora):
     """Fixed plate at 45 deg with the disturbance pair (Gaussian core), 200 steps, binary64."""
     torch, V = cuda()
-    p = W.plate_c1_params()
+    p = W.fixed_plate_params()
     for seed in (0, 1):
-        parts, xg, cap = W.plate_c1_initial(seed)
+        parts, xg, cap = W.fixed_plate_initial(seed)
         res = _run_gpu(V, torch, p, parts, xg, np.zeros((1, 200), np.float32), V.FP64, cap)
         ref = ora.rollout(p, parts, xg, np.zeros(200), want_field=True)
         n = int(res["count"][0])
@@ -157,20 +157,20 @@ def _binary32_envelope(ora, p, parts, xg, u, checkpoints, cap):
     return out
 
 
-@pytest.mark.parametrize("case", ["c1", "c2", "table1"])
+@pytest.mark.parametrize("case", ["fixed_plate", "mppi_batch", "table1"])
 def test_fp32_within_model_sensitivity(ora, case):
     """On the chaotic workloads the binary32 path is held to the envelope of the model's own
     sensitivity: after H steps its distance from the FP64 oracle must be below
     max(1e-4 c, 3 x the spread of the oracle run with its state rounded to binary32 every
     step)."""
     torch, V = cuda()
-    if case == "c1":
-        p = W.plate_c1_params()
-        parts, xg, cap = W.plate_c1_initial(0)
+    if case == "fixed_plate":
+        p = W.fixed_plate_params()
+        parts, xg, cap = W.fixed_plate_initial(0)
         u = np.zeros(200)
         checkpoints = [50, 100, 200]
-    elif case == "c2":
-        p, parts, xg, eps = W.mppi_c2(0, K=1, H=100, n=1000)
+    elif case == "mppi_batch":
+        p, parts, xg, eps = W.mppi_batch_inputs(0, K=1, H=100, n=1000)
         u = eps[0].astype(np.float64)
         cap = 1200
         checkpoints = [25, 50, 100]
@@ -192,7 +192,7 @@ def test_fp32_within_model_sensitivity(ora, case):
 
 def test_fp64_merging_and_gate(ora):
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(3, K=4, H=60, n=300)
+    p, field, xg0, eps = W.mppi_batch_inputs(3, K=4, H=60, n=300)
     for over in (dict(n_wake_max=330), dict(shed_gate=2), dict(shed_gate=1, alpha_crit=0.05)):
         q = dict(p, **over)
         res = _run_gpu(V, torch, q, field, xg0, eps, V.FP64, 300 + 2 * 60)
@@ -233,7 +233,7 @@ def test_batch_invariance_and_per_launch_form():
     """A rollout's result does not depend on the batch it runs in, and the one-rollout-per-
     launch form computes the same numbers bitwise."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(1, K=64, H=20, n=500)
+    p, field, xg0, eps = W.mppi_batch_inputs(1, K=64, H=20, n=500)
     st = V.State(p, field, xg0, 540)
     c = torch.tensor(eps, device="cuda")
     full = st.rollout_batch(c)
@@ -252,7 +252,7 @@ def test_paced_launch_matches_unpaced_launches(monkeypatch):
     default, every launch are not paced. The pacing changes timing only: the results are the
     same bits."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(2, K=1024, H=6, n=300)
+    p, field, xg0, eps = W.mppi_batch_inputs(2, K=1024, H=6, n=300)
     st = V.State(p, field, xg0, 320)
     c = torch.tensor(eps, device="cuda")
     monkeypatch.setenv("VPM_PACE", "1")
@@ -273,7 +273,7 @@ def test_two_wave_batch_matches_single_launches():
     resident at once). Each rollout's costs, final glider state, trajectory and field are the
     same bits as in a launch of its own."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(5, K=2048, H=4, n=300)
+    p, field, xg0, eps = W.mppi_batch_inputs(5, K=2048, H=4, n=300)
     st = V.State(p, field, xg0, 310)
     c = torch.tensor(eps, device="cuda")
     full = st.rollout_batch(c, want_traj=True, want_field=True)
@@ -292,7 +292,7 @@ def test_rollout_batch_replays_from_a_cuda_graph():
     """A rollout batch captured into a CUDA graph (its pair-sum scratch and pacing table are
     allocated stream-ordered inside the capture) gives the eager launch's bits on replay."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(4, K=1024, H=5, n=400)
+    p, field, xg0, eps = W.mppi_batch_inputs(4, K=1024, H=5, n=400)
     st = V.State(p, field, xg0, 420)
     c = torch.tensor(eps, device="cuda")
     eager = st.rollout_batch(c)
@@ -320,7 +320,7 @@ def test_full_size_batch_properties(ora):
     bitwise; a step taken from a sampled rollout's final state matches the oracle's step from
     that same state."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(0, K=1024, H=100, n=1000)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=1024, H=100, n=1000)
     st = V.State(p, field, xg0, 1200)
     c = torch.tensor(eps, device="cuda")
     out = st.rollout_batch(c, want_field=True)
@@ -350,7 +350,7 @@ def test_2000_particle_batch_properties(ora):
     16 rows): counts and costs, sampled rollouts rerun alone bitwise, and a step from a sampled
     final state against the oracle's step from that state."""
     torch, V = cuda()
-    p, field, xg0, eps = W.mppi_c2(0, K=1024, H=100, n=1900)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=1024, H=100, n=1900)
     st = V.State(p, field, xg0, 2100)
     c = torch.tensor(eps, device="cuda")
     out = st.rollout_batch(c, want_field=True)
@@ -400,8 +400,8 @@ def test_fp64_cluster_path_matches_one_block_bitwise(case):
     rollouts through both paths give the same bits."""
     torch, V = cuda()
     if case == "plate":
-        p = W.plate_c1_params()
-        field, xg, cap = W.plate_c1_initial(2, 60)
+        p = W.fixed_plate_params()
+        field, xg, cap = W.fixed_plate_initial(2, 60)
         ctrl = np.zeros((10, 60), np.float32)
     else:
         p = dict(W.glider_params(), n_wake_max=150)

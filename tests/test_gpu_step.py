@@ -18,20 +18,20 @@ pytestmark = pytest.mark.gpu
 
 
 def _cases():
-    c2 = W.glider_params()
-    c1 = W.plate_c1_params()
+    gl = W.glider_params()
+    fp = W.fixed_plate_params()
     return {
-        "c2_ungated": (c2, W.background_field(0, 1000), np.array(W.GLIDER_X0), [0, 1, 25, 60, 99]),
-        "c2_lev_gated": (dict(c2, shed_gate=2), W.background_field(1, 700), np.array(W.GLIDER_X0), [0, 5, 40]),
-        "c2_both_gated": (dict(c2, shed_gate=1, alpha_crit=math.radians(3)), W.background_field(2, 400),
+        "glider_ungated": (gl, W.background_field(0, 1000), np.array(W.GLIDER_X0), [0, 1, 25, 60, 99]),
+        "glider_lev_gated": (dict(gl, shed_gate=2), W.background_field(1, 700), np.array(W.GLIDER_X0), [0, 5, 40]),
+        "glider_both_gated": (dict(gl, shed_gate=1, alpha_crit=math.radians(3)), W.background_field(2, 400),
                           np.array(W.GLIDER_X0), [0, 10, 30]),
-        "c2_merging": (dict(c2, n_wake_max=450), W.background_field(3, 440), np.array(W.GLIDER_X0), [0, 3, 20]),
-        "c1_gaussian": (c1, *W.plate_c1_initial(0)[:2], [0, 1, 80, 160, 199]),
-        "nb2": (dict(c2, n_b=2), W.background_field(4, 300), np.array(W.GLIDER_X0), [0, 7, 30]),
-        "nb32": (dict(c2, n_b=32), W.background_field(5, 300), np.array(W.GLIDER_X0), [0, 7, 30]),
-        "empty_wake": (c2, np.zeros((0, 3)), np.array(W.GLIDER_X0), [0, 1, 2]),
+        "glider_merging": (dict(gl, n_wake_max=450), W.background_field(3, 440), np.array(W.GLIDER_X0), [0, 3, 20]),
+        "fixed_plate_gaussian": (fp, *W.fixed_plate_initial(0)[:2], [0, 1, 80, 160, 199]),
+        "nb2": (dict(gl, n_b=2), W.background_field(4, 300), np.array(W.GLIDER_X0), [0, 7, 30]),
+        "nb32": (dict(gl, n_b=32), W.background_field(5, 300), np.array(W.GLIDER_X0), [0, 7, 30]),
+        "empty_wake": (gl, np.zeros((0, 3)), np.array(W.GLIDER_X0), [0, 1, 2]),
         # the perch benchmark's shape (Table I): clean start, merging above 60 particles
-        "table1_merging": (dict(c2, n_wake_max=60), np.zeros((0, 3)), np.array(W.GLIDER_X0),
+        "table1_merging": (dict(gl, n_wake_max=60), np.zeros((0, 3)), np.array(W.GLIDER_X0),
                            [0, 29, 30, 31, 55, 79]),
     }
 

@@ -31,8 +31,8 @@ def _crosses(p0, p1, a, b):
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_pair_removed_at_first_crossing(ora, seed):
-    p = W.plate_c1_params()
-    pair, xg, cap = W.plate_c1_initial(seed)
+    p = W.fixed_plate_params()
+    pair, xg, cap = W.fixed_plate_initial(seed)
     a = ora.State(p, np.zeros((0, 3)), xg, cap)
     a.inject_pair(*pair[0], *pair[1])
     b = a.copy()

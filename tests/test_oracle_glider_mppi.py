@@ -220,7 +220,7 @@ def test_mppi_update_convex_combination(ora):
 
 
 def test_rollout_matches_stepping(ora):
-    p, field, xg0, eps = W.mppi_c2(0, K=2, H=12, n=100)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=2, H=12, n=100)
     out = ora.rollout(p, field, xg0, eps[0].astype(np.float64), want_traj=True, want_field=True)
     s = ora.State(p, field, xg0, 100 + 24)
     for k in range(12):

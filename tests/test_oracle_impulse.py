@@ -59,7 +59,7 @@ def test_tev_only_load_is_impulse_rate(ora, deg):
     impulse force within 5 % over the first half chord of travel (steps 2-49, the impulsive start,
     where the one-step backward differences of Eq. 13 lag the central difference of the impulse)
     and within 2 % over the next 2.5 chords."""
-    p = dict(W.plate_c1_params(), shed_gate=2, alpha_crit=math.radians(20.0))
+    p = dict(W.fixed_plate_params(), shed_gate=2, alpha_crit=math.radians(20.0))
     fn, fi = _loads_and_impulse_force(ora, p, math.radians(deg), 300)
     assert fn[2:50].mean() == pytest.approx(fi[2:50].mean(), rel=0.05)
     assert fn[50:298].mean() == pytest.approx(fi[50:298].mean(), rel=0.02)
@@ -71,7 +71,7 @@ def test_lev_shedding_load_follows_impulse(ora, deg):
     (steps 2-49) the mean Bernoulli normal force has the impulse force's sign and lies within 25 %
     of it. The remaining difference comes from the discretisation: vortices born 0.02 c from
     the edge collocation points, and a whole LEV formed within each step."""
-    p = dict(W.plate_c1_params(), shed_gate=0)
+    p = dict(W.fixed_plate_params(), shed_gate=0)
     fn, fi = _loads_and_impulse_force(ora, p, math.radians(deg), 52)
     a, b = fn[2:50].mean(), fi[2:50].mean()
     assert b > 0 and a > 0

@@ -95,7 +95,7 @@ def test_rigid_motion_invariance(ora):
 
 
 def test_zero_incidence_no_wake_is_unloaded(ora):
-    p = dict(W.plate_c1_params(), wake_kernel=1)
+    p = dict(W.fixed_plate_params(), wake_kernel=1)
     s = ora.State(p, np.zeros((0, 3)), np.array([0.0, 0.0, 0.0, 0, 0, 0, 0]), 10)
     out = s.step()
     assert np.abs(out["gamma_s"]).max() < 1e-15
@@ -103,7 +103,7 @@ def test_zero_incidence_no_wake_is_unloaded(ora):
 
 
 def test_mirror_incidence_antisymmetric(ora):
-    p = W.plate_c1_params()
+    p = W.fixed_plate_params()
     ga = ora.State(p, np.zeros((0, 3)), np.array([0, 0, 0.3, 0, 0, 0, 0.0]), 10).step()
     gb = ora.State(p, np.zeros((0, 3)), np.array([0, 0, -0.3, 0, 0, 0, 0.0]), 10).step()
     assert np.allclose(ga["gamma_s"], -gb["gamma_s"], atol=1e-14)
@@ -114,7 +114,7 @@ def test_wagner_indicial_lift(ora):
     normal force follows Wagner's function (Jones' fit) toward the thin-airfoil value
     2 pi sin(alpha) q c; the centre of pressure sits ahead of mid-chord (nose-up moment)."""
     deg = 3.0
-    p = dict(W.plate_c1_params(), shed_gate=2, alpha_crit=math.radians(20.0))
+    p = dict(W.fixed_plate_params(), shed_gate=2, alpha_crit=math.radians(20.0))
     al = math.radians(deg)
     s = ora.State(p, np.zeros((0, 3)), np.array([0, 0, al, 0, 0, 0, 0.0]), 900)
     q = 0.5 * p["rho"] * 1.0 ** 2 * p["chord"] * p["span"]
@@ -133,7 +133,7 @@ def test_wagner_indicial_lift(ora):
 
 
 def test_gate_mode1_sheds_nothing_below_alpha_crit(ora):
-    p = dict(W.plate_c1_params(), shed_gate=1, alpha_crit=math.radians(10), wake_kernel=1)
+    p = dict(W.fixed_plate_params(), shed_gate=1, alpha_crit=math.radians(10), wake_kernel=1)
     wake = np.array([[1.5, 0.3, 0.2], [2.0, -0.4, -0.1]])
     xg = np.array([0, 0, math.radians(5), 0, 0, 0, 0.0])
     s = ora.State(p, wake, xg, 10)
@@ -147,7 +147,7 @@ def test_gate_mode1_sheds_nothing_below_alpha_crit(ora):
 
 
 def test_gate_mode2_sheds_tev_only(ora):
-    p = dict(W.plate_c1_params(), shed_gate=2, alpha_crit=math.radians(10), wake_kernel=1)
+    p = dict(W.fixed_plate_params(), shed_gate=2, alpha_crit=math.radians(10), wake_kernel=1)
     xg = np.array([0, 0, math.radians(5), 0, 0, 0, 0.0])
     s = ora.State(p, np.zeros((0, 3)), xg, 10)
     out = s.step()
@@ -157,7 +157,7 @@ def test_gate_mode2_sheds_tev_only(ora):
 
 
 def test_merging_keeps_circulation(ora):
-    p = dict(W.plate_c1_params(), n_wake_max=20, wake_kernel=1)
+    p = dict(W.fixed_plate_params(), n_wake_max=20, wake_kernel=1)
     wake = W.background_field(2, 19)
     wake[:, 0] += 3.0
     s = ora.State(p, wake, np.array([0, 0, 0.4, 0, 0, 0, 0.0]), 40)
@@ -173,7 +173,7 @@ def test_merging_keeps_circulation(ora):
 
 
 def test_merge_position_is_mean(ora):
-    p = dict(W.plate_c1_params(), n_wake_max=3, wake_kernel=1)
+    p = dict(W.fixed_plate_params(), n_wake_max=3, wake_kernel=1)
     wake = np.array([[10.0, 0.0, 0.1], [12.0, 2.0, 0.2]])
     s = ora.State(p, wake, np.array([0, 0, 0.4, 0, 0, 0, 0.0]), 10)
     out = s.step()

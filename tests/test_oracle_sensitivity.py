@@ -21,13 +21,13 @@ def _spread(ora, p, field, xg0, u, rel, seed=1):
 
 
 def test_ungated_workload_amplifies_rounding(ora):
-    p, field, xg0, eps = W.mppi_c2(0, K=1, H=100, n=1000)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=1, H=100, n=1000)
     u = eps[0].astype(np.float64)
     assert _spread(ora, p, field, xg0, u, 1e-7) > 1e-2
     assert _spread(ora, p, field, xg0, u, 1e-13) < 1e-3
 
 
 def test_lev_gated_variant_is_mildly_sensitive(ora):
-    p, field, xg0, eps = W.mppi_c2(0, K=1, H=100, n=1000)
+    p, field, xg0, eps = W.mppi_batch_inputs(0, K=1, H=100, n=1000)
     p = dict(p, shed_gate=2)
     assert _spread(ora, p, field, xg0, eps[0].astype(np.float64), 1e-7) < 1e-4

@@ -21,7 +21,7 @@ def _worker(rank, world, port, q):
     r, w, _ = bench.dist_setup(world, backend="gloo")
     bench.barrier(w)
     t = bench.max_over_ranks(10.0 * (r + 1), w)
-    field = W.mppi_c2(r, K=1, H=1, n=50)[1]
+    field = W.mppi_batch_inputs(r, K=1, H=1, n=50)[1]
     q.put((r, w, t, bench.job_throughput(100.0, w, t), float(field[:, 0].sum())))
     dist.destroy_process_group()
 

@@ -50,8 +50,8 @@ def glider_params(**over) -> dict:
 GLIDER_X0 = (0.0, 0.0, 0.0, 0.0, 7.0, 0.0, 0.0)  # initial glider state, §IV-A
 
 
-# --------------------------------------------------------------------------- config 1
-def plate_c1_params() -> dict:
+# --------------------------------------------------------------------------- fixed plate
+def fixed_plate_params() -> dict:
     """Fixed flat plate at 45 degrees incidence in a uniform stream of speed 1.
 
     The plate is held at theta = 45 deg with its centre at the origin and the stream
@@ -64,8 +64,8 @@ def plate_c1_params() -> dict:
     )
 
 
-def plate_c1_initial(seed: int, steps: int = 200):
-    """Disturbance pair of config 1 and the fixed plate's glider state.
+def fixed_plate_initial(seed: int, steps: int = 200):
+    """Disturbance pair of the fixed-plate case and the fixed plate's glider state.
 
     Two opposite vortices of strength 0.5 spaced 0.5 c apart are centred 2 c upstream
     (+x, since the stream flows in -x) with a vertical offset uniform in +-0.2 c. The
@@ -79,7 +79,7 @@ def plate_c1_initial(seed: int, steps: int = 200):
     return parts, glider, 2 + 2 * steps
 
 
-# --------------------------------------------------------------------------- config 2
+# --------------------------------------------------------------------------- MPPI batch
 BOX = (-1.0, 5.0, -1.5, 1.5)  # x0, x1, z0, z1: the 6c x 3c background box
 
 
@@ -116,8 +116,8 @@ def mppi_noise(seed: int, K: int, H: int, sigma: float) -> np.ndarray:
 MPPI_SIGMA_U = 0.1 / 0.01  # 0.1 rad of elevator deflection per 0.01 s step, as a rate
 
 
-def mppi_c2(seed: int = 0, K: int = 1024, H: int = 100, n: int = 1000):
-    """MPPI batch of config 2: root field, glider x0 and control noise."""
+def mppi_batch_inputs(seed: int = 0, K: int = 1024, H: int = 100, n: int = 1000):
+    """MPPI batch of 1000-particle root fields: root field, glider x0 and control noise."""
     p = glider_params()
     field = background_field(seed, n)
     eps = mppi_noise(seed + 1000, K, H, MPPI_SIGMA_U)
@@ -130,14 +130,14 @@ def costs_synthetic(seed: int, K: int, scale: float = 50.0) -> np.ndarray:
     return (scale * r.chisquare(3, K)).astype(np.float32)
 
 
-# --------------------------------------------------------------------------- config 3
+# --------------------------------------------------------------------------- uneven batches
 def uneven_counts(seed: int, R: int = 4096, lo: int = 64, hi: int = 8192) -> np.ndarray:
     """Particle counts log-uniform in [lo, hi]."""
     u = _rng(seed).uniform(math.log(lo), math.log(hi), R)
     return np.clip(np.rint(np.exp(u)), lo, hi).astype(np.int64)
 
 
-# --------------------------------------------------------------------------- config 4
+# --------------------------------------------------------------------------- large free field
 def blob_field(seed: int, n: int, n_blobs: int = 64, sigma: float = 0.1, extent: float = 10.0,
                gamma_std: float = 1e-3) -> np.ndarray:
     """Seeded sum of Gaussian blobs: centres uniform in [0, extent]^2, each particle
@@ -155,7 +155,7 @@ def sample_indices(seed: int, n: int, m: int) -> np.ndarray:
     return np.sort(_rng(seed).choice(n, size=min(m, n), replace=False)).astype(np.int64)
 
 
-# --------------------------------------------------------------------------- config 5
+# --------------------------------------------------------------------------- serving
 def serving_scenarios(seed: int, n_scen: int = 16, n_lo: int = 500, n_hi: int = 5000):
     """Resident field sizes and fields of the serving scenarios (box field + pair)."""
     r = _rng(seed)
