@@ -142,8 +142,8 @@ def test_unknown_disturbance_moves_the_plant_off_the_nominal(ora):
 def test_projection_is_the_policy_rollout_from_the_observed_state(ora, L):
     """Under an unknown disturbance each replan starts from the tracking instance with the
     observed glider state and projects L steps under the policy in effect at that step: the
-    plan's first nominal state is the policy rollout of the oracle's closed-loop rollout from
-    that snapshot."""
+    plan's first nominal state is where the closed-loop policy rollout (oracle/policy.py) from
+    that snapshot ends."""
     N = 32
     r, _ = _run(_cfg(N, 10, L), pair=RING)
     assert len(r["snapshots"]) == len(r["plans"]) - 1 >= 2
