@@ -10,6 +10,11 @@ and form the reweighted control sequence. A replan is three iterations.
 Metric: Biot-Savart pair interactions per second (every evaluated target-source pair of
 Eqs. 12 and 16 counted once), plus replan p50/p99 latency in ms.
 
+The default line also carries, as entries of their own: the replan latency on ~2000-particle
+fields next to the one-rollout-per-launch form, the serving loop at two arrival rates, the
+uneven batch (4096 rollouts of 64-8192 particles, autotuned persistent launches), the 2^20
+free field (two Heun steps, error on 4096 sampled targets) and the FP64 oracle on the host.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--replans R] [--impl reference]
 """
 from __future__ import annotations
@@ -472,6 +477,13 @@ def run_gpu(args):
                    "seconds_of_arrivals": args.serve_line_seconds, "runs": serving,
                    "clocks": clk_sv.summary()}
 
+    # the uneven batch and the large free field, each measured as its own workload would be
+    uneven = freefield = None
+    if world == 1 and args.uneven_line_steps > 0:
+        uneven = uneven_result(V, torch, args.rollouts_uneven, args.uneven_line_steps, args.sample)
+    if world == 1 and args.ff_line_steps > 0:
+        freefield = freefield_result(V, torch, args.n, args.ff_line_steps)
+
     if rank != 0:
         return
     clocks = clk.summary()
@@ -518,6 +530,10 @@ def run_gpu(args):
         line["replan2000_ms"] = replan2000
     if serving is not None:
         line["serving"] = serving
+    if uneven is not None:
+        line["uneven_batch"] = uneven
+    if freefield is not None:
+        line["free_field"] = freefield
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"], line["error_vs_fp64_oracle"] = cpu_baseline(V=V)
     print(json.dumps(line), flush=True)
@@ -546,15 +562,11 @@ def run_profile_case(args):
 
 
 # ------------------------------------------------------------------ extra workloads
-def run_freefield(args):
-    """Large free field: N = 2^20 regularised vortices (64 Gaussian blobs, core 1e-3), 10 Heun
-    steps in binary32 with compensated tile sums, one evaluation per particle pair; error of the
-    final velocities against the FP64 oracle on 4096 sampled targets."""
-    import torch
-    import paper_2509_16079_b300 as V
-    from paper_2509_16079_b300 import build
-    build.build()
-    n, steps, dt, rc = args.n, args.ff_steps, 1e-3, 1e-3
+def freefield_result(V, torch, n: int, steps: int, targets: int = 4096) -> dict:
+    """Large free field: n regularised vortices (64 Gaussian blobs, core 1e-3), `steps` Heun
+    steps in binary32 with one evaluation per particle pair; error of the final velocities
+    against the FP64 oracle on `targets` sampled targets, which also times the oracle."""
+    rc, dt = 1e-3, 1e-3
     P = W.blob_field(0, n)
     a = np.zeros((n, 4), np.float32)
     a[:, :3] = P
@@ -580,7 +592,7 @@ def run_freefield(args):
     from concurrent.futures import ThreadPoolExecutor
     oracle.build()
     Pf = d[:, :3].double().cpu().numpy()
-    idx = W.sample_indices(1, n, 4096)
+    idx = W.sample_indices(1, n, targets)
     chunks = np.array_split(idx, os.cpu_count() or 1)
     t_ora = time.perf_counter()
     with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
@@ -592,13 +604,16 @@ def run_freefield(args):
     err = np.linalg.norm(got - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max()
     achieved = n * float(n) * FLOPS_PER_PAIR / (kern_ms / 1e3) / 1e12
     peak = fp32_peak_tflops()
-    print(json.dumps({
+    return {
         "metric": "Biot-Savart pair-interactions/s", "value": pairs / (ms / 1e3),
         "unit": "pair-interactions/s", "n_gpus": 1, "steps": steps, "ms_per_step": ms / steps,
         "higher_is_better": True, "dtype": "f32 (Kahan-compensated tile sums)", "data": "synthetic",
         "config": {"workload": "free field N=%d, 64 Gaussian blobs sigma 0.1 in a 10x10 box, "
-                               "Vatistas core 1e-3, Heun dt=1e-3" % n, "pairs_per_step": 2 * n * n},
-        "error_vs_fp64_oracle": {"normwise_velocity": err, "targets": int(len(idx))},
+                               "Vatistas core 1e-3, Heun dt=1e-3" % n, "pairs_per_step": 2 * n * n,
+                   "l2": "not flushed: the %d MB field stays L2-resident across the Heun steps of "
+                         "one call; each evaluation is ALU-bound (%d x %d pairs)" % (16 * n >> 20, n, n)},
+        "error_vs_fp64_oracle": {"normwise_velocity": err, "targets": int(len(idx)),
+                                 "tolerance": 1e-5},
         "cpu_baseline": {"value": ora_pairs / t_ora, "unit": "pair-interactions/s",
                          "cores": len(chunks), "kind": "oracle",
                          "per_core": ora_pairs / t_ora / len(chunks), "cpu_model": cpu_model(),
@@ -611,7 +626,16 @@ def run_freefield(args):
                      "traffic": profiled_traffic("freefield_kernel_2pow20.md", "vpm_freefield.cu"),
                      "pipes": profiled_pipes("freefield_kernel_2pow20.md", "vpm_freefield.cu"),
                      "launch_ms": kern_ms},
-        "clocks": clk.summary()}), flush=True)
+        "clocks": clk.summary()}
+
+
+def run_freefield(args):
+    """The large free field alone: N = 2^20 by default, 10 Heun steps."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    print(json.dumps(freefield_result(V, torch, args.n, args.ff_steps)), flush=True)
 
 
 def run_alu(args):
@@ -938,22 +962,19 @@ def run_replan2000(args):
                       "higher_is_better": False, **r, "clocks": clk.summary()}), flush=True)
 
 
-def run_uneven(args):
-    """Uneven batching: 4096 rollouts with particle counts log-uniform in [64, 8192], H = 50,
+def uneven_result(V, torch, R: int, steps: int, sample: int) -> dict:
+    """Uneven batching: R rollouts with particle counts log-uniform in [64, 8192], H = 50,
     binary32, persistent launches (class launches side by side or one merged launch) with
-    autotuned block and diagonal-unit sizes, the horizon replayed from a
-    CUDA graph; against one launch per rollout (timed on a systematic sample of the rollouts
-    sorted by size and scaled to all of them: the launches are serial on one stream)."""
-    import torch
-    import paper_2509_16079_b300 as V
-    from paper_2509_16079_b300 import build
-    build.build()
-    R, Hh = args.rollouts_uneven, 50
+    autotuned block and diagonal-unit sizes, the horizon replayed from a CUDA graph, L2 flushed
+    between timed horizons; against one launch per rollout (timed on a systematic sample of the
+    rollouts sorted by size and scaled to all of them: the launches are serial on one stream)."""
+    Hh = 50
     counts = W.uneven_counts(0, R, 64, 8192)
     fields = [W.background_field(10_000 + i, int(n)) for i, n in enumerate(counts)]
     gliders = np.tile(np.array(W.GLIDER_X0), (R, 1))
     p = W.glider_params()
     controls = torch.tensor(W.mppi_noise(11, R, Hh, W.MPPI_SIGMA_U), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     b = V.Batch(p, fields, gliders, Hh)
     b.tune(controls)
     out = b.rollout(controls, use_graph=True)
@@ -961,20 +982,25 @@ def run_uneven(args):
     b.status()
     times = []
     with ClockSampler(0) as clk:
-        for _ in range(args.steps):
+        for j in range(steps):
+            flush.fill_(float(j))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             b.rollout(controls, use_graph=True, out=out)
             e1.record()
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+    b.status()
+    schedule, modes = b.schedule(), b.tuned_modes()
+    b.close()
+    del flush
     pairs = sum(pairs_per_rollout(int(n), Hh) for n in counts)
     ms = float(np.median(times))
     # one launch per rollout, systematic sample
     order = np.argsort(counts)
-    sample = order[len(order) // (2 * args.sample) :: max(1, len(order) // args.sample)][: args.sample]
+    picked = order[len(order) // (2 * sample) :: max(1, len(order) // sample)][: sample]
     single_ms = []
-    for i in sample:
+    for i in picked:
         st = V.State(p, fields[i], gliders[i], int(counts[i]) + 2 * Hh, V.FP32)
         c = controls[i:i + 1].contiguous()
         st.rollout_batch(c, want_final=False)
@@ -986,17 +1012,27 @@ def run_uneven(args):
         e1.synchronize()
         single_ms.append(e0.elapsed_time(e1))
         st.close()
-    per_launch_ms = float(np.sum(single_ms)) * R / len(sample)
-    print(json.dumps({
+    per_launch_ms = float(np.sum(single_ms)) * R / len(picked)
+    return {
         "metric": "Biot-Savart pair-interactions/s", "value": pairs / (ms / 1e3),
-        "unit": "pair-interactions/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": ms,
+        "unit": "pair-interactions/s", "n_gpus": 1, "steps": steps, "ms_per_step": ms,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "uneven batch: %d rollouts, counts log-uniform in [64, 8192], H=50" % R,
                    "pairs_per_step": pairs, "max_count": int(counts.max()),
-                   "schedule": b.schedule(), "tuner_whole_batch_3_steps": b.tuned_modes(), "graph": True},
-        "one_launch_per_rollout": {"ms_scaled": per_launch_ms, "sampled_rollouts": int(len(sample)),
+                   "schedule": schedule, "tuner_whole_batch_3_steps": modes, "graph": True,
+                   "l2": "flushed between timed horizons (256 MB write outside the events)"},
+        "one_launch_per_rollout": {"ms_scaled": per_launch_ms, "sampled_rollouts": int(len(picked)),
                                    "pairs_per_s": pairs / (per_launch_ms / 1e3)},
-        "speedup": per_launch_ms / ms, "clocks": clk.summary()}), flush=True)
+        "speedup": per_launch_ms / ms, "clocks": clk.summary()}
+
+
+def run_uneven(args):
+    """The uneven batch alone: 4096 rollouts by default."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    print(json.dumps(uneven_result(V, torch, args.rollouts_uneven, args.steps, args.sample)), flush=True)
 
 
 SERVE_H = 100
@@ -1173,6 +1209,10 @@ def main():
     ap.add_argument("--sample", type=int, default=64, help="rollouts timed one launch each (uneven)")
     ap.add_argument("--n", type=int, default=1 << 20, help="free-field particle count")
     ap.add_argument("--ff-steps", type=int, default=10)
+    ap.add_argument("--ff-line-steps", type=int, default=2,
+                    help="Heun steps of the free-field entry in the default line (0: leave it out)")
+    ap.add_argument("--uneven-line-steps", type=int, default=5,
+                    help="timed horizons of the uneven-batch entry in the default line (0: leave it out)")
     ap.add_argument("--n0", type=int, default=1900, help="root field size of the ~2000-particle replans")
     ap.add_argument("--per-launch-subset", type=int, default=16)
     ap.add_argument("--replan2000-replans", type=int, default=200,
