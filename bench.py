@@ -1019,7 +1019,7 @@ def uneven_result(V, torch, R: int, steps: int, sample: int) -> dict:
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "uneven batch: %d rollouts, counts log-uniform in [64, 8192], H=50" % R,
                    "pairs_per_step": pairs, "max_count": int(counts.max()),
-                   "schedule": schedule, "tuner_whole_batch_3_steps": modes, "graph": True,
+                   "schedule": schedule, "tuner_whole_batch_ms": modes, "graph": True,
                    "l2": "flushed between timed horizons (256 MB write outside the events)"},
         "one_launch_per_rollout": {"ms_scaled": per_launch_ms, "sampled_rollouts": int(len(picked)),
                                    "pairs_per_s": pairs / (per_launch_ms / 1e3)},

@@ -424,9 +424,15 @@ vpm_status vpm_batch_rollout(vpm_batch *batch, int H, const float *d_controls, f
  * one persistent launch sized for the largest field, is timed alone over min(H, 3) steps for
  * each block size that fits (128, 256, 512 threads) and each diagonal pair-unit size (32, 64 or
  * 128 targets, i.e. 1, 2 or 4 per lane; Vatistas kernel only, others keep 2), keeping its
- * fastest. Then the whole batch is timed as the class launches side by side and as the one
- * merged launch, and the faster is kept. Rollouts use one block (CTA) each. It changes speed
- * only, never results. Synchronises `stream`.
+ * fastest. A class whose fields can exceed 2300 particles (Vatistas kernel) is then timed at
+ * that shape with each rollout spread over a thread-block cluster of 2 and of 4 CTAs (every CTA
+ * holds the field; the step's pair units are split between them and the advected records are
+ * exchanged through distributed shared memory), and keeps the fastest of 1, 2 and 4 CTAs per
+ * rollout; cluster choices are kept only if the whole batch of class launches runs faster with
+ * them than with one CTA per rollout (a class alone can leave SMs idle that clusters fill; side
+ * by side the classes fill the GPU anyway). Then the whole batch is timed as the class launches
+ * side by side and as the one merged launch, over the whole horizon H, and the faster is kept. It
+ * changes speed only, never results. Synchronises `stream`.
  */
 vpm_status vpm_batch_tune(vpm_batch *batch, int H, const float *d_controls, cudaStream_t stream);
 
@@ -438,7 +444,7 @@ vpm_status vpm_batch_schedule(const vpm_batch *batch, int *h_nclasses, int *h_ca
                               int *h_items, float *h_tuned_ms, int *h_diag_t, int *h_ctas,
                               int *h_merged);
 
-/* The tuner's times (ms, min(H, 3) steps of the whole batch) of the class launches side by side
+/* The tuner's times (ms, H steps of the whole batch) of the class launches side by side
  * and of the one merged launch (0 before tuning or with a single class). */
 vpm_status vpm_batch_tuned_modes(const vpm_batch *batch, float *h_split_ms, float *h_merged_ms);
 
@@ -447,6 +453,15 @@ vpm_status vpm_batch_tuned_modes(const vpm_batch *batch, float *h_split_ms, floa
  * targets per lane (1, 2, 4; 2 unless the wake kernel is Vatistas; binary64 batches: 128 and
  * 2). Results do not depend on it. Errors: VPM_ERR_INVALID (a size that does not fit). */
 vpm_status vpm_batch_set_schedule(vpm_batch *batch, int merged, int cls, int nt, int diag_t);
+
+/* Sets CTAs per rollout by hand for launch `cls` of the schedule selected by `merged` (as in
+ * vpm_batch_set_schedule): 1, or a cluster of 2 or 4 CTAs per rollout (binary32 batches with the
+ * Vatistas kernel of Eq. 5 only), keeping the launch's threads and diagonal-unit size. The
+ * batch rollout over a cluster is the same computation as on one CTA (§III-A steps; Eq. 16's
+ * pair sums split between the CTAs by unit), so results are the same bits. Errors:
+ * VPM_ERR_INVALID (another count, another precision or kernel, or a cluster that does not fit
+ * the launch's shared memory and threads). */
+vpm_status vpm_batch_set_ctas(vpm_batch *batch, int merged, int cls, int ctas);
 
 /* Reads and clears the batch's device error word (synchronises `stream`). */
 vpm_status vpm_batch_status(vpm_batch *batch, cudaStream_t stream);

@@ -114,6 +114,7 @@ _SIGNATURES = {
     "vpm_batch_rollout": ([_VP, _I, _VP, _VP, _VP, _VP, _I, _VP], _I),
     "vpm_batch_tune": ([_VP, _I, _VP, _VP], _I),
     "vpm_batch_set_schedule": ([_VP, _I, _I, _I, _I], _I),
+    "vpm_batch_set_ctas": ([_VP, _I, _I, _I], _I),
     "vpm_batch_tuned_modes": ([_VP, C.POINTER(_F), C.POINTER(_F)], _I),
     "vpm_batch_schedule": ([_VP, C.POINTER(_I), _VP, _VP, _VP, _VP, _VP, _VP, C.POINTER(_I)], _I),
     "vpm_batch_status": ([_VP, _VP], _I),
@@ -518,6 +519,9 @@ class Batch:
 
     def set_schedule(self, merged: bool, cls: int, threads: int, diag_t: int):
         check(lib().vpm_batch_set_schedule(self._h, int(bool(merged)), int(cls), int(threads), int(diag_t)))
+
+    def set_ctas(self, merged: bool, cls: int, ctas: int):
+        check(lib().vpm_batch_set_ctas(self._h, int(bool(merged)), int(cls), int(ctas)))
 
     def status(self, stream=None):
         check(lib().vpm_batch_status(self._h, stream_handle(stream)))

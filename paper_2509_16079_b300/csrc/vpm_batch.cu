@@ -1,6 +1,7 @@
 // Batches of rollouts from many different roots (uneven particle counts) in persistent
 // launches: host-side grouping into shared-memory classes, longest-first ordering, the
-// autotuner (block size, diagonal-unit size, class launches or one launch for all), and
+// autotuner (block size, diagonal-unit size, CTAs per rollout, class launches or one launch
+// for all), and
 // capture of a whole horizon into a CUDA graph.
 #include <math.h>
 #include <stdarg.h>
@@ -54,7 +55,9 @@ struct BatchClass {
     int cap = 0;                 // largest capacity in the class (shared-memory size)
     int nt = 128;                // threads per block (autotuned)
     int dt = 2;                  // targets per lane of the diagonal pair units (autotuned)
-    int grid = 0;                // persistent blocks for nt (resident blocks per SM x SMs)
+    int ctas = 1;                // CTAs per rollout: 1, or a cluster of 2 or 4 (autotuned)
+    int grid = 0;                // persistent CTAs (resident blocks per SM x SMs, or resident
+                                 // clusters x ctas)
     float tuned_ms = 0.f;
     std::vector<int> items;      // rollout indices, largest first
     int *d_order = nullptr;
@@ -242,15 +245,22 @@ static void batch_args(const vpm_batch *b, int H, const float *ctrl, float *cost
     a.status = b->d_status;
 }
 
-// Persistent grid of class c for nt threads per block; also sets the kernel's shared-memory
-// limit, so it runs before any capture.
-static cudaError_t prepare_class(vpm_batch *b, int c, int nt, int dt)
+// Persistent grid of class c for nt threads per block and `ctas` CTAs per rollout; also sets
+// the kernel's shared-memory limit, so it runs before any capture.
+static cudaError_t prepare_class(vpm_batch *b, int c, int nt, int dt, int ctas)
 {
     BatchClass &k = b->cls[c];
     const size_t smem = rollout_smem_bytes(b->params.precision, k.cap);
-    const int per_sm = uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, dt, smem);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    k.grid = std::min<int>((int)k.items.size(), per_sm * b->sms);
+    if (ctas > 1) {
+        const int clusters = uneven_max_clusters(b->params.precision, b->params.wake_kernel, nt, dt,
+                                                 ctas, smem);
+        if (clusters < 1) return cudaErrorInvalidConfiguration;
+        k.grid = std::min<int>((int)k.items.size(), clusters) * ctas;
+    } else {
+        const int per_sm = uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, dt, smem);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        k.grid = std::min<int>((int)k.items.size(), per_sm * b->sms);
+    }
     // scratch for the grid's blocks; a captured graph that holds the old buffer is dropped
     const long long slots = rollout_rev_slots(b->params.precision, k.cap);
     if (slots > 0 && (size_t)k.grid > k.rev_blocks) {
@@ -278,7 +288,7 @@ static bool runs_class(const vpm_batch *b, int c, bool merged)
 static cudaError_t enqueue_classes(vpm_batch *b, int H, const float *ctrl, float *costs,
                                    int *count, double *final_glider, cudaStream_t s,
                                    int only_class = -1, int nt_override = 0, int dt_override = 0,
-                                   int merged = -1)
+                                   int merged = -1, int ctas_override = 0)
 {
     const bool mg = merged < 0 ? b->merged : merged != 0;
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * (kNumClasses + 1), s);
@@ -288,6 +298,7 @@ static cudaError_t enqueue_classes(vpm_batch *b, int H, const float *ctrl, float
         if (only_class >= 0 ? (c != only_class || k.items.empty()) : !runs_class(b, c, mg)) continue;
         const int nt = nt_override ? nt_override : k.nt;
         const int dt = dt_override ? dt_override : k.dt;
+        const int ctas = ctas_override ? ctas_override : k.ctas;
         const int grid = k.grid;
         RolloutArgs a;
         batch_args(b, H, ctrl, costs, count, final_glider, a);
@@ -298,7 +309,8 @@ static cudaError_t enqueue_classes(vpm_batch *b, int H, const float *ctrl, float
         a.rev = k.d_rev;
         a.rev_stride = rollout_rev_slots(b->params.precision, k.cap);
         e = cudaStreamWaitEvent(k.stream, b->fork, 0);
-        if (!e) e = launch_uneven(b->params.precision, a, grid, nt, dt, k.stream);
+        if (!e) e = ctas > 1 ? launch_uneven_cluster(a, grid / ctas, nt, dt, ctas, k.stream)
+                             : launch_uneven(b->params.precision, a, grid, nt, dt, k.stream);
         if (!e) e = cudaEventRecord(k.done, k.stream);
         if (!e) e = cudaStreamWaitEvent(s, k.done, 0);
     }
@@ -313,7 +325,8 @@ extern "C" vpm_status vpm_batch_rollout(vpm_batch *b, int H, const float *d_cont
     if (!b || !d_controls || !d_costs) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: null argument");
     if (H < 1 || H > b->max_h) return bfail(VPM_ERR_INVALID, "vpm_batch_rollout: need 1 <= H <= %d", b->max_h);
     for (int c = 0; c <= kNumClasses; ++c)
-        if (runs_class(b, c, b->merged)) BTRY(prepare_class(b, c, b->cls[c].nt, b->cls[c].dt), "prepare class");
+        if (runs_class(b, c, b->merged))
+            BTRY(prepare_class(b, c, b->cls[c].nt, b->cls[c].dt, b->cls[c].ctas), "prepare class");
     if (!use_graph) {
         cudaError_t e = enqueue_classes(b, H, d_controls, d_costs, d_count, d_final_glider, stream);
         if (e) return bcuda(e, "vpm_batch_rollout");
@@ -343,11 +356,11 @@ extern "C" vpm_status vpm_batch_rollout(vpm_batch *b, int H, const float *d_cont
 // Times one enqueue of the batch (or of one class) over Ht steps after one warm-up enqueue.
 static cudaError_t time_enqueue(vpm_batch *b, int Ht, const float *ctrl, float *costs, cudaStream_t s,
                                 cudaEvent_t t0, cudaEvent_t t1, float &ms, int only_class, int nt,
-                                int dt, int merged)
+                                int dt, int merged, int ctas = 0)
 {
-    cudaError_t e = enqueue_classes(b, Ht, ctrl, costs, nullptr, nullptr, s, only_class, nt, dt, merged);
+    cudaError_t e = enqueue_classes(b, Ht, ctrl, costs, nullptr, nullptr, s, only_class, nt, dt, merged, ctas);
     if (!e) e = cudaEventRecord(t0, s);
-    if (!e) e = enqueue_classes(b, Ht, ctrl, costs, nullptr, nullptr, s, only_class, nt, dt, merged);
+    if (!e) e = enqueue_classes(b, Ht, ctrl, costs, nullptr, nullptr, s, only_class, nt, dt, merged, ctas);
     if (!e) e = cudaEventRecord(t1, s);
     if (!e) e = cudaEventSynchronize(t1);
     if (!e) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -358,9 +371,19 @@ static cudaError_t time_enqueue(vpm_batch *b, int Ht, const float *ctrl, float *
 // rollouts in one persistent launch), one launch of the class alone over min(H, 3) steps is timed
 // for each block size that fits (128, 256, 512 threads) and each diagonal-unit size (32, 64 or
 // 128 targets: 1, 2 or 4 per lane; the Vatistas kernel only, others keep 2); each keeps its
-// fastest. Then the whole batch is timed as concurrent class launches and as the one merged
-// launch, and the faster schedule is kept. A rollout's result depends on none of these choices,
-// so tuning changes speed only. Synchronises `stream`.
+// fastest. A class of fields above kClusterMinCap particles (Vatistas kernel) is then timed at
+// that shape with each rollout spread over a cluster of 2 and of 4 CTAs, and keeps the fastest
+// of 1, 2 and 4 CTAs per rollout. A class alone may leave SMs idle that clusters fill, while the
+// classes side by side fill the GPU anyway, so cluster choices are kept only if the whole batch
+// of class launches runs faster with them than with one CTA per rollout. Then the whole batch is
+// timed as concurrent class launches and as the one merged launch, and the faster schedule is
+// kept. The whole-batch timings run the whole horizon H: over 3 or 10 steps the class launches
+// of the 4096-rollout batch looked 3-5 % faster than the merged launch and were 1-2 % slower over
+// its 50 steps.
+// A rollout's result depends on none of these choices, so tuning changes speed only.
+// Synchronises `stream`.
+static const int kClusterMinCap = 2300;
+
 extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_controls,
                                      cudaStream_t stream)
 {
@@ -388,27 +411,63 @@ extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_control
                 if (dt != 2 && !vat) continue;
                 if (uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, dt, smem) < 1) continue;
                 float ms = 0.f;
-                cudaError_t e = prepare_class(b, c, nt, dt);
-                if (!e) e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, ms, c, nt, dt, -1);
+                cudaError_t e = prepare_class(b, c, nt, dt, 1);
+                if (!e) e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, ms, c, nt, dt, -1, 1);
                 if (e) { st = bcuda(e, "vpm_batch_tune"); break; }
                 if (ms < best) { best = ms; best_nt = nt; best_dt = dt; }
             }
             if (st != VPM_OK) break;
         }
+        int best_ctas = 1;
+        for (int ctas : {2, 4}) {
+            if (st != VPM_OK || !vat || k.cap <= kClusterMinCap) break;
+            if (uneven_max_clusters(b->params.precision, b->params.wake_kernel, best_nt, best_dt, ctas, smem) < 1)
+                continue;
+            float ms = 0.f;
+            cudaError_t e = prepare_class(b, c, best_nt, best_dt, ctas);
+            if (!e) e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, ms, c, best_nt, best_dt, -1, ctas);
+            if (e) { st = bcuda(e, "vpm_batch_tune"); break; }
+            if (ms < best) { best = ms; best_ctas = ctas; }
+        }
         k.nt = best_nt;
         k.dt = best_dt;
+        k.ctas = best_ctas;
         k.tuned_ms = best;
         if (st == VPM_OK) {
-            cudaError_t e = prepare_class(b, c, best_nt, best_dt);
+            cudaError_t e = prepare_class(b, c, best_nt, best_dt, best_ctas);
             if (e) st = bcuda(e, "vpm_batch_tune");
         }
     }
-    // class launches side by side against the one merged launch
+    const int Hw = H;
     b->merged = false;
+    // cluster choices made class by class, against one CTA per rollout for the whole batch
+    bool clustered = false;
+    for (int c = 0; c < kNumClasses; ++c) clustered |= !b->cls[c].items.empty() && b->cls[c].ctas > 1;
+    if (st == VPM_OK && nonempty >= 2 && clustered) {
+        float with = 0.f, without = 0.f;
+        int chosen[kNumClasses];
+        for (int c = 0; c < kNumClasses; ++c) chosen[c] = b->cls[c].ctas;
+        cudaError_t e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, with, -1, 0, 0, 0);
+        for (int c = 0; c < kNumClasses && !e; ++c) {
+            if (b->cls[c].items.empty() || chosen[c] == 1) continue;
+            b->cls[c].ctas = 1;
+            e = prepare_class(b, c, b->cls[c].nt, b->cls[c].dt, 1);
+        }
+        if (!e) e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, without, -1, 0, 0, 0);
+        if (!e && with < without) {
+            for (int c = 0; c < kNumClasses && !e; ++c) {
+                if (b->cls[c].items.empty() || chosen[c] == 1) continue;
+                b->cls[c].ctas = chosen[c];
+                e = prepare_class(b, c, b->cls[c].nt, b->cls[c].dt, chosen[c]);
+            }
+        }
+        if (e) st = bcuda(e, "vpm_batch_tune");
+    }
+    // class launches side by side against the one merged launch
     if (st == VPM_OK && nonempty >= 2) {
         float split = 0.f, one = 0.f;
-        cudaError_t e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, split, -1, 0, 0, 0);
-        if (!e) e = time_enqueue(b, Ht, d_controls, costs, stream, t0, t1, one, -1, 0, 0, 1);
+        cudaError_t e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, split, -1, 0, 0, 0);
+        if (!e) e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, one, -1, 0, 0, 1);
         if (e) st = bcuda(e, "vpm_batch_tune");
         else { b->merged = one < split; b->split_ms = split; b->merged_ms = one; }
     }
@@ -435,7 +494,7 @@ extern "C" vpm_status vpm_batch_schedule(const vpm_batch *b, int *h_nclasses, in
         if (h_items) h_items[m] = (int)k.items.size();
         if (h_tuned_ms) h_tuned_ms[m] = k.tuned_ms;
         if (h_diag_t) h_diag_t[m] = k.dt;
-        if (h_ctas) h_ctas[m] = 1;
+        if (h_ctas) h_ctas[m] = k.ctas;
         ++m;
     }
     *h_nclasses = m;
@@ -469,9 +528,34 @@ extern "C" vpm_status vpm_batch_set_schedule(vpm_batch *b, int merged, int cls, 
     const size_t smem = rollout_smem_bytes(b->params.precision, b->cls[target].cap);
     if (uneven_blocks_per_sm(b->params.precision, b->params.wake_kernel, nt, diag_t, smem) < 1)
         return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: %d threads do not fit the class", nt);
+    const int ctas = b->cls[target].ctas;
+    if (ctas > 1 && uneven_max_clusters(b->params.precision, b->params.wake_kernel, nt, diag_t, ctas, smem) < 1)
+        return bfail(VPM_ERR_INVALID, "vpm_batch_set_schedule: %d threads do not fit a cluster of %d", nt, ctas);
     b->merged = merged != 0;
     b->cls[target].nt = nt;
     b->cls[target].dt = diag_t;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    return VPM_OK;
+}
+
+extern "C" vpm_status vpm_batch_set_ctas(vpm_batch *b, int merged, int cls, int ctas)
+{
+    if (!b) return bfail(VPM_ERR_INVALID, "vpm_batch_set_ctas: null batch");
+    if (ctas != 1 && ctas != 2 && ctas != 4) return bfail(VPM_ERR_INVALID, "vpm_batch_set_ctas: ctas must be 1, 2 or 4");
+    if (ctas > 1 && (b->params.precision != VPM_FP32 || b->params.wake_kernel != VPM_KERNEL_VATISTAS))
+        return bfail(VPM_ERR_INVALID, "vpm_batch_set_ctas: clusters need a binary32 batch with the Vatistas kernel");
+    int m = 0, target = -1;
+    for (int c = 0; c <= kNumClasses; ++c) {
+        if (!runs_class(b, c, merged != 0)) continue;
+        if (m++ == cls) target = c;
+    }
+    if (target < 0) return bfail(VPM_ERR_INVALID, "vpm_batch_set_ctas: class %d does not exist in that schedule", cls);
+    BatchClass &k = b->cls[target];
+    const size_t smem = rollout_smem_bytes(b->params.precision, k.cap);
+    if (ctas > 1 && uneven_max_clusters(b->params.precision, b->params.wake_kernel, k.nt, k.dt, ctas, smem) < 1)
+        return bfail(VPM_ERR_INVALID, "vpm_batch_set_ctas: a cluster of %d CTAs of %d threads does not fit", ctas, k.nt);
+    b->merged = merged != 0;
+    k.ctas = ctas;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     return VPM_OK;
 }

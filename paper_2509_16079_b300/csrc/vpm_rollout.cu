@@ -826,7 +826,9 @@ __device__ void old_pairs_f32(const DevParams &p, Work &w, const float4 *part, f
 }
 
 // The old-old sum of target i < n: its diagonal sum (in vel), then its row's forward sum and
-// the reverse sums of the earlier rows (scratch).
+// the reverse sums of the earlier rows (scratch). CL: the scratch was written by other CTAs of
+// a cluster, so it is read from L2 (ld.global.cg), past this SM's L1.
+template <bool CL = false>
 __device__ __forceinline__ float2 old_sum(const float2 *vel, const float2 *scr, int cap32,
                                           int rows_off, int i)
 {
@@ -835,12 +837,16 @@ __device__ __forceinline__ float2 old_sum(const float2 *vel, const float2 *scr, 
     if (row == 0 && rows_off == 0) return v;
     float cu = 0.f, cw = 0.f;
     if (row < rows_off) {
-        const float4 f = reinterpret_cast<const float4 *>(scr)[fwd_index(i)];
+        const float4 *fp = reinterpret_cast<const float4 *>(scr) + fwd_index(i);
+        float4 f;
+        if constexpr (CL) f = __ldcg(fp); else f = *fp;
         kahan_add(v.x, cu, f.x - f.z);
         kahan_add(v.y, cw, f.y - f.w);
     }
     for (int a = 0; a < row; ++a) {
-        const float2 r = scr[rev_slot(a, i, cap32)];
+        const float2 *rp = scr + rev_slot(a, i, cap32);
+        float2 r;
+        if constexpr (CL) r = __ldcg(rp); else r = *rp;
         kahan_add(v.x, cu, r.x);
         kahan_add(v.y, cw, r.y);
     }
@@ -916,8 +922,9 @@ __device__ void fresh_velocities_f32(const DevParams &p, Work &w, const float4 *
 // then advected by explicit Euler (double-length positions) and decayed exactly,
 // Gamma <- Gamma exp(-gamma dt) (Eq. 17). The record is read and written by the thread that
 // owns it, so no barrier separates the velocity from the advection. `bad` collects non-finite
-// velocities.
-template <int KER>
+// velocities. CL (a CTA of a cluster that runs one rollout): the scratch is read from L2 and
+// the advected record is written into the field of every CTA of the cluster.
+template <int KER, bool CL = false>
 __device__ __forceinline__ void finalize_one(const DevParams &p, const Work &w, float4 *part,
                                              const float2 *vel, const float2 *scr, int cap32,
                                              int rows_off, int n, int nf, int i, double *probe_vel,
@@ -933,7 +940,7 @@ __device__ __forceinline__ void finalize_one(const DevParams &p, const Work &w, 
     float xl, zl;
     if (i < n) {
         q = part[i];
-        const float2 raw = old_sum(vel, scr, cap32, rows_off, i);
+        const float2 raw = old_sum<CL>(vel, scr, cap32, rows_off, i);
         unpack_lo(q.w, xl, zl);
         float bu = 0.f, bw = 0.f;
         bound_terms_f32(p, w, q.x, q.y, xl, zl, bu, bw);
@@ -961,7 +968,13 @@ __device__ __forceinline__ void finalize_one(const DevParams &p, const Work &w, 
     q.y = sz;
     q.z = fmaf(q.z, dcl, q.z * dch);
     q.w = pack_lo(ex, ez);
-    part[i] = q;
+    if constexpr (CL) {
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        const int C = (int)cl.num_blocks();
+        for (int r = 0; r < C; ++r) *cl.map_shared_rank(part + i, r) = q;
+    } else {
+        part[i] = q;
+    }
 }
 
 // Phase C completion and phase D for every particle of the step, by the whole block.
@@ -1440,6 +1453,143 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_kernel(const Ro
     }
 }
 
+// ------------------------------------------------------------------ binary32 rollouts over a cluster
+
+// One binary32 rollout spread over a thread-block cluster of C CTAs (2 or 4; a schedule of the
+// uneven batch for large fields). Every CTA holds the whole field in its shared memory and runs
+// the plate warp's serial work (geometry, plate sums, solve, loads, glider, shedding) from
+// identical data, so every CTA has the same plate state, particle count and shed particles.
+// The step's pair units are split by index: unit u goes to CTA u mod C, and the CTA's warps claim
+// its units in order. Rows write their partial sums to the cluster's scratch in global memory;
+// diagonal units write their targets' sums into their CTA's vel. After a cluster barrier (release
+// and acquire at cluster scope) a particle is completed and advected by the CTA that ran its
+// diagonal unit (the freshly shed particles by CTA 0), which writes the new record into the field
+// of every CTA through distributed shared memory; a second cluster barrier ends the step, and
+// termination and merging then run on every CTA from identical fields. Every partial sum is
+// formed by one warp in the same order as on the one-CTA path and combined per particle in the
+// same order, so the results are the same bits whatever C.
+template <int KER, int DT>
+__device__ void old_pairs_f32_cl(const DevParams &p, Work &w, const float4 *part, float2 *vel,
+                                 float2 *scr, int cap32, int n, const PairPlan &pp, int claim_base,
+                                 int rank, int C, int nl)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(&w.chunk_next, 1) - claim_base;
+        li = __shfl_sync(0xffffffffu, li, 0);
+        if (li >= nl) break;
+        const int c = rank + C * li;
+        if (c < pp.rows_off) {
+            offdiag_row<KER>(p, part, scr, cap32, n, c);
+        } else if (pp.pair_diag) {
+            const int g = c - pp.rows_off;
+            if (kRow * (g + 1) <= n) diag_row_pairs<KER, true>(p, part, vel, n, g);
+            else diag_row_pairs<KER, false>(p, part, vel, n, g);
+        } else {
+            const int g = c - pp.rows_off, t0 = 32 * DT * g, r0 = (t0 / kRow) * kRow;
+            old_pairs_chunk<KER, DT>(p, part, vel, r0, min(r0 + kRow, n), t0, n);
+        }
+    }
+}
+
+template <int KER, int DT>
+__device__ void step_once_cl(const DevParams &p, Work &w, float4 *part, float2 *vel, double u_ctrl,
+                             const RolloutArgs &a, float2 *scr, int rank, int C, int &n,
+                             int &claim_base)
+{
+    namespace cg = cooperative_groups;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == plate_warp()) {
+        const int lane = tid & 31;
+        plate_geometry(p, w);
+        prefetch_solve_rows(p, w.geo);
+        if (lane < p.n_b) bound_point_f32(p, w, lane);
+        plate_sums_f32<KER>(p, w, part, n);
+        __syncwarp();
+        const int m = plate_solve<float>(p, w, part, n, u_ctrl, 1);
+        if (lane == 0) w.n = m;
+        fresh_velocities_f32<KER>(p, w, part, n, m);
+    }
+    const PairPlan pp = pair_plan<DT, true>(n);
+    const int cap32 = (a.cap + 31) & ~31;
+    const int nl = pp.nunits > rank ? (pp.nunits - rank + C - 1) / C : 0;
+    old_pairs_f32_cl<KER, DT>(p, w, part, vel, scr, cap32, n, pp, claim_base, rank, C, nl);
+    claim_base += nl + (int)(blockDim.x >> 5);
+    cg::this_cluster().sync();       // every CTA's partial sums written; plate results in place
+    int n1 = w.n;
+    const int nf = n1 - n, gsz = pp.pair_diag ? kRow : 32 * DT;
+    bool bad = false;
+    for (int i = tid; i < n1; i += (int)blockDim.x) {
+        const int owner = i < n ? (pp.rows_off + i / gsz) % C : 0;
+        if (owner == rank)
+            finalize_one<KER, true>(p, w, part, vel, scr, cap32, pp.rows_off, n, nf, i, nullptr, bad);
+    }
+    if (bad) atomicOr(&w.flag, (int)kStNonFinite);
+    cg::this_cluster().sync();       // the advected field is complete in every CTA
+    if (w.ndist == 2) n1 = terminate_pair<float>(p, w, part, n1);
+    n = merge_oldest<float>(p, part, n1, w.ndist);
+}
+
+template <int KER, int DT>
+__device__ void run_rollout_cl(const RolloutArgs &a, Work &w, float4 *part, float2 *vel, float2 *scr,
+                               int rid, int rank, int C)
+{
+    namespace cg = cooperative_groups;
+    load_state<float>(a, w, part, rid);
+    int n = w.n, claim_base = 0;
+    for (int k = 0; k < a.H; ++k) {
+        double u = a.controls ? (double)a.controls[(size_t)rid * a.ctrl_stride + a.step0 + k]
+                              : a.u_const;
+        if (a.pol_gains && (int)(threadIdx.x >> 5) == plate_warp()) {
+            const size_t j = (size_t)a.pol_offset + k;
+            double fb = (double)a.pol_ubar[j];
+            for (int c = 0; c < 7; ++c)
+                fb -= a.pol_gains[j * 7 + c] * (w.xg[c] - a.pol_xbar[j * 7 + c]);
+            u = (a.controls ? u : 0.0) + fb;
+        }
+        step_once_cl<KER, DT>(a.p, w, part, vel, u, a, scr, rank, C, n, claim_base);
+        if (rank == 0 && a.traj && threadIdx.x < 7)
+            a.traj[((size_t)rid * a.H + k) * 7 + threadIdx.x] = w.xg[threadIdx.x];
+    }
+    if (threadIdx.x == 0) {
+        w.n = n;
+        if (rank != 0 && w.flag) atomicOr(cg::this_cluster().map_shared_rank(&w.flag, 0), w.flag);
+    }
+    cg::this_cluster().sync();
+    if (rank == 0) {
+        if (a.out_part) store_state<float>(a, w, part, rid);
+        finish<float>(a, w, part, rid);
+    }
+}
+
+// Persistent cluster form of uneven_kernel: CTA 0 of each cluster claims the next rollout of
+// a.order and hands its index to the other CTAs; the cluster's scratch is slot blockIdx.x / C.
+template <int KER, int NT, int DT>
+__global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_cluster_kernel(const RolloutArgs a)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *part = reinterpret_cast<float4 *>(smem);
+    float2 *vel = reinterpret_cast<float2 *>(smem + sizeof(float4) * (size_t)a.cap);
+    __shared__ Work w;
+    __shared__ int s_item;
+    float2 *scr = a.rev ? a.rev + (size_t)(blockIdx.x / C) * a.rev_stride : nullptr;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int q = atomicAdd(a.counter, 1);
+            for (int r = 0; r < C; ++r) *cl.map_shared_rank(&s_item, r) = q;
+        }
+        cl.sync();
+        const int q = s_item;
+        if (q >= a.n_items) break;
+        run_rollout_cl<KER, DT>(a, w, part, vel, scr, a.order[q], rank, C);
+        cl.sync();                   // every CTA is done with this rollout and with s_item
+    }
+}
+
 // ------------------------------------------------------------------ host-side launch helpers
 
 // Raises a kernel's dynamic shared-memory limit to at least smem, once per size increase (the
@@ -1736,6 +1886,102 @@ int uneven_blocks_per_sm(int precision, int kernel, int nt, int dt, size_t smem)
     if (kernel == VPM_KERNEL_SINGULAR) { VPM_OCC(VPM_KERNEL_SINGULAR) }
     VPM_OCC(VPM_KERNEL_VATISTAS)
 #undef VPM_OCC
+}
+
+// Cluster launches of the binary32 persistent kernel (Vatistas kernel of Eq. 5, the workloads'
+// kernel): `clusters` clusters of `ctas` CTAs of nt threads, diagonal units of 32 dt targets.
+template <int NT, int DT>
+static cudaLaunchConfig_t cluster_cfg_u(int clusters, int ctas, size_t smem, cudaStream_t s,
+                                        cudaLaunchAttribute &at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(clusters * ctas);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = ctas; at.val.clusterDim.y = 1; at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <int NT, int DT>
+static std::atomic<size_t> &granted_uc()
+{
+    static std::atomic<size_t> g{0};
+    return g;
+}
+
+template <int NT, int DT>
+static int clusters_uc(int ctas, size_t smem)
+{
+    auto k = uneven_cluster_kernel<VPM_KERNEL_VATISTAS, NT, DT>;
+    if (grant_smem(k, granted_uc<NT, DT>(), smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchAttribute at;
+    cudaLaunchConfig_t cfg = cluster_cfg_u<NT, DT>(1, ctas, smem, nullptr, at);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <int NT, int DT>
+static cudaError_t launch_uc(const RolloutArgs &a, int clusters, int ctas, size_t smem, cudaStream_t s)
+{
+    auto k = uneven_cluster_kernel<VPM_KERNEL_VATISTAS, NT, DT>;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusNone) {         // under capture the batch raised it before
+        const cudaError_t e = grant_smem(k, granted_uc<NT, DT>(), smem);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchAttribute at;
+    const cudaLaunchConfig_t cfg = cluster_cfg_u<NT, DT>(clusters, ctas, smem, s, at);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+int uneven_max_clusters(int precision, int kernel, int nt, int dt, int ctas, size_t smem)
+{
+    if (precision != VPM_FP32 || kernel != VPM_KERNEL_VATISTAS || (ctas != 2 && ctas != 4)) return 0;
+#define VPM_UC(NT_)                                                   \
+    if (nt == NT_) {                                                  \
+        if (dt == 1) return clusters_uc<NT_, 1>(ctas, smem);          \
+        if (dt == 4) return clusters_uc<NT_, 4>(ctas, smem);          \
+        return clusters_uc<NT_, 2>(ctas, smem);                       \
+    }
+    VPM_UC(512)
+    VPM_UC(256)
+    VPM_UC(128)
+#undef VPM_UC
+    return 0;
+}
+
+cudaError_t launch_uneven_cluster(const RolloutArgs &a, int clusters, int nt, int dt, int ctas,
+                                  cudaStream_t s)
+{
+    if (a.p.kernel != VPM_KERNEL_VATISTAS || (ctas != 2 && ctas != 4) || clusters < 1 ||
+        (rev_slots(a.cap) > 0 && (!a.rev || a.rev_stride < rev_slots(a.cap))))
+        return cudaErrorInvalidValue;
+    const size_t smem = rollout_smem_bytes(VPM_FP32, a.cap);
+#define VPM_UC(NT_)                                                         \
+    if (nt == NT_) {                                                        \
+        if (dt == 1) return launch_uc<NT_, 1>(a, clusters, ctas, smem, s);  \
+        if (dt == 4) return launch_uc<NT_, 4>(a, clusters, ctas, smem, s);  \
+        return launch_uc<NT_, 2>(a, clusters, ctas, smem, s);               \
+    }
+    VPM_UC(512)
+    VPM_UC(256)
+    VPM_UC(128)
+#undef VPM_UC
+    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ one binary64 rollout per cluster

@@ -86,6 +86,13 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
 cudaError_t launch_uneven(int precision, const RolloutArgs &a, int grid, int nt, int dt, cudaStream_t s);
 // Resident blocks per SM of the persistent kernel for this configuration (0 if it cannot run).
 int uneven_blocks_per_sm(int precision, int kernel, int nt, int dt, size_t smem);
+// The persistent launch with one rollout per cluster of `ctas` CTAs (2 or 4; binary32, Vatistas
+// kernel only): `clusters` clusters claim rollouts; a.rev holds one scratch area per cluster.
+// Results are the same bits as launch_uneven's.
+cudaError_t launch_uneven_cluster(const RolloutArgs &a, int clusters, int nt, int dt, int ctas,
+                                  cudaStream_t s);
+// Clusters of `ctas` CTAs that can be resident at once for this configuration (0: it cannot run).
+int uneven_max_clusters(int precision, int kernel, int nt, int dt, int ctas, size_t smem);
 // Throughput probe of the binary32 pair loop (Vatistas kernel, core radius r_core): `grid`
 // blocks of 128 threads each load the n records of d_src into shared memory and form every
 // target's sum over all n sources `reps` times with t targets per lane (1, 2 or 4); block b

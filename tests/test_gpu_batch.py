@@ -70,7 +70,8 @@ def test_graph_replay_and_tuning_do_not_change_results():
     b.tune(controls)
     sched = b.schedule()
     assert all(s["threads"] in (128, 256, 512) and s["tuned_ms"] > 0 and s["diag_t"] in (1, 2, 4)
-               and s["ctas"] == 1 for s in sched)
+               and s["ctas"] in (1, 2, 4) for s in sched)
+    assert all(s["ctas"] == 1 for s in sched if s["cap"] <= 2300)
     tuned = b.rollout(controls)
     torch.cuda.synchronize()
     for k in base:
@@ -107,6 +108,64 @@ def test_every_schedule_gives_the_same_bits():
                     checked += 1
     assert checked >= 20
     b.status()
+
+
+def test_cluster_schedules_give_the_same_bits():
+    """Each launch of both schedules with every rollout spread over a cluster of 2 and of 4 CTAs,
+    at every block and diagonal-unit size that fits, gives the bits of one CTA per rollout. The
+    fields cover a single row (up to 128 particles), ragged last rows, the once-per-target and
+    once-per-pair diagonal units (below and from 1300 particles) and the 512-thread classes."""
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 4
+    counts = [90, 127, 600, 1299, 1400, 2500, 2999, 4100, 6000, 8100, 0, 33]
+    fields, gliders = _roots(counts, 5)
+    controls = torch.tensor(W.mppi_noise(13, len(counts), H, W.MPPI_SIGMA_U), device="cuda")
+    b = V.Batch(p, fields, gliders, H)
+    base = {k: v.clone() for k, v in b.rollout(controls).items()}
+    checked = set()
+    for merged in (False, True):
+        nl = 1 if merged else len(b.schedule())
+        assert nl >= (1 if merged else 5)
+        for cls in range(nl):
+            for threads in (128, 256, 512):
+                for diag_t in (1, 2, 4):
+                    for ctas in (2, 4):
+                        try:
+                            b.set_ctas(merged, cls, 1)
+                            b.set_schedule(merged, cls, threads, diag_t)
+                            b.set_ctas(merged, cls, ctas)
+                        except V.VpmError:
+                            continue                # does not fit this class
+                        out = b.rollout(controls)
+                        torch.cuda.synchronize()
+                        s = b.schedule()[cls]
+                        assert (s["ctas"], s["threads"], s["diag_t"], s["merged"]) == \
+                            (ctas, threads, diag_t, merged)
+                        for k in base:
+                            assert torch.equal(out[k], base[k]), (merged, cls, threads, diag_t, ctas, k)
+                        checked.add((merged, cls, ctas))
+            b.set_ctas(merged, cls, 1)
+    # every class launch (5) and the merged launch ran on clusters of both sizes
+    assert len(checked) == 2 * 6, sorted(checked)
+    b.status()
+
+
+def test_cluster_ctas_rejected_where_they_cannot_run():
+    torch, V = cuda()
+    p = W.glider_params()
+    fields, gliders = _roots([300, 2600], 1)
+    b = V.Batch(p, fields, gliders, 2)
+    for bad in (0, 3, 8):
+        with pytest.raises(V.VpmError):
+            b.set_ctas(False, 0, bad)
+    with pytest.raises(V.VpmError):
+        b.set_ctas(False, 5, 2)                     # no such launch
+    b64 = V.Batch(p, fields, gliders, 2, precision=V.FP64)
+    with pytest.raises(V.VpmError):
+        b64.set_ctas(False, 0, 2)                   # clusters are a binary32 schedule
+    b.set_ctas(False, 1, 2)
+    assert b.schedule()[1]["ctas"] == 2
 
 
 def test_batch_fp64_against_oracle(ora):
