@@ -431,7 +431,8 @@ vpm_status vpm_batch_rollout(vpm_batch *batch, int H, const float *d_controls, f
  * rollout; cluster choices are kept only if the whole batch of class launches runs faster with
  * them than with one CTA per rollout (a class alone can leave SMs idle that clusters fill; side
  * by side the classes fill the GPU anyway). Then the whole batch is timed as the class launches
- * side by side and as the one merged launch, over the whole horizon H, and the faster is kept. It
+ * side by side and as the one merged launch, each over the whole horizon H as a captured CUDA
+ * graph (median of three replays), and the faster is kept. It
  * changes speed only, never results. Synchronises `stream`.
  */
 vpm_status vpm_batch_tune(vpm_batch *batch, int H, const float *d_controls, cudaStream_t stream);
@@ -444,7 +445,7 @@ vpm_status vpm_batch_schedule(const vpm_batch *batch, int *h_nclasses, int *h_ca
                               int *h_items, float *h_tuned_ms, int *h_diag_t, int *h_ctas,
                               int *h_merged);
 
-/* The tuner's times (ms, H steps of the whole batch) of the class launches side by side
+/* The tuner's times (ms, H steps of the whole batch, graph replay) of the class launches side by side
  * and of the one merged launch (0 before tuning or with a single class). */
 vpm_status vpm_batch_tuned_modes(const vpm_batch *batch, float *h_split_ms, float *h_merged_ms);
 

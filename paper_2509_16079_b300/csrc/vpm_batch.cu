@@ -367,6 +367,36 @@ static cudaError_t time_enqueue(vpm_batch *b, int Ht, const float *ctrl, float *
     return e;
 }
 
+// Median time of three replays of the whole batch over Ht steps in the schedule `merged`, captured
+// into a CUDA graph as vpm_batch_rollout runs it (concurrent class launches vary from run to run,
+// and their eager and graph forms differ by a few per cent).
+static cudaError_t time_graph(vpm_batch *b, int Ht, const float *ctrl, float *costs, cudaStream_t s,
+                              cudaEvent_t t0, cudaEvent_t t1, bool merged, float &ms)
+{
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e) return e;
+    e = enqueue_classes(b, Ht, ctrl, costs, nullptr, nullptr, b->capture_stream, -1, 0, 0, merged ? 1 : 0);
+    const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
+    if (!e) e = e2;
+    if (!e) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    float t[3] = {0.f, 0.f, 0.f};
+    if (!e) e = cudaGraphLaunch(ge, s);              // warm-up
+    for (int r = 0; r < 3 && !e; ++r) {
+        e = cudaEventRecord(t0, s);
+        if (!e) e = cudaGraphLaunch(ge, s);
+        if (!e) e = cudaEventRecord(t1, s);
+        if (!e) e = cudaEventSynchronize(t1);
+        if (!e) e = cudaEventElapsedTime(&t[r], t0, t1);
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    std::sort(t, t + 3);
+    ms = t[1];
+    return e;
+}
+
 // Autotuner over the launch shape: for every class (and for the merged class that runs all
 // rollouts in one persistent launch), one launch of the class alone over min(H, 3) steps is timed
 // for each block size that fits (128, 256, 512 threads) and each diagonal-unit size (32, 64 or
@@ -377,9 +407,10 @@ static cudaError_t time_enqueue(vpm_batch *b, int Ht, const float *ctrl, float *
 // classes side by side fill the GPU anyway, so cluster choices are kept only if the whole batch
 // of class launches runs faster with them than with one CTA per rollout. Then the whole batch is
 // timed as concurrent class launches and as the one merged launch, and the faster schedule is
-// kept. The whole-batch timings run the whole horizon H: over 3 or 10 steps the class launches
-// of the 4096-rollout batch looked 3-5 % faster than the merged launch and were 1-2 % slower over
-// its 50 steps.
+// kept. The whole-batch timings run the whole horizon H as a CUDA graph (median of three
+// replays): over 3 or 10 steps the class launches of the 4096-rollout batch looked 3-5 % faster
+// than the merged launch and were 1-2 % slower over its 50 steps, and one eager timing of them
+// came out 6 % below their graph replay.
 // A rollout's result depends on none of these choices, so tuning changes speed only.
 // Synchronises `stream`.
 static const int kClusterMinCap = 2300;
@@ -447,13 +478,13 @@ extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_control
         float with = 0.f, without = 0.f;
         int chosen[kNumClasses];
         for (int c = 0; c < kNumClasses; ++c) chosen[c] = b->cls[c].ctas;
-        cudaError_t e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, with, -1, 0, 0, 0);
+        cudaError_t e = time_graph(b, Hw, d_controls, costs, stream, t0, t1, false, with);
         for (int c = 0; c < kNumClasses && !e; ++c) {
             if (b->cls[c].items.empty() || chosen[c] == 1) continue;
             b->cls[c].ctas = 1;
             e = prepare_class(b, c, b->cls[c].nt, b->cls[c].dt, 1);
         }
-        if (!e) e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, without, -1, 0, 0, 0);
+        if (!e) e = time_graph(b, Hw, d_controls, costs, stream, t0, t1, false, without);
         if (!e && with < without) {
             for (int c = 0; c < kNumClasses && !e; ++c) {
                 if (b->cls[c].items.empty() || chosen[c] == 1) continue;
@@ -466,8 +497,8 @@ extern "C" vpm_status vpm_batch_tune(vpm_batch *b, int H, const float *d_control
     // class launches side by side against the one merged launch
     if (st == VPM_OK && nonempty >= 2) {
         float split = 0.f, one = 0.f;
-        cudaError_t e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, split, -1, 0, 0, 0);
-        if (!e) e = time_enqueue(b, Hw, d_controls, costs, stream, t0, t1, one, -1, 0, 0, 1);
+        cudaError_t e = time_graph(b, Hw, d_controls, costs, stream, t0, t1, false, split);
+        if (!e) e = time_graph(b, Hw, d_controls, costs, stream, t0, t1, true, one);
         if (e) st = bcuda(e, "vpm_batch_tune");
         else { b->merged = one < split; b->split_ms = split; b->merged_ms = one; }
     }
