@@ -220,7 +220,12 @@ vpm_status vpm_rollout_scratch_slot(int capacity, int kind, int row, int particl
 /*
  * K independent rollouts of H steps from the root model, which is not modified. Rollout i
  * applies elevator rates d_controls[i*H + k] (binary32, K x H row-major). One thread block
- * holds one rollout's field in shared memory for the whole horizon. Outputs (device):
+ * holds one rollout's field in shared memory for the whole horizon. Binary32 launches of a few
+ * rollouts whose fields can exceed 2300 particles (Vatistas kernel, H > 1) instead spread each
+ * rollout over a thread-block cluster of C CTAs, the largest C in {4, 2} with K C <= the SM count
+ * (every CTA holds the field; the pair work is split between them): the same bits, faster when
+ * K alone would leave SMs idle; VPM_ROLLOUT_CLUSTERS=0 in the environment keeps one block per
+ * rollout. Outputs (device):
  *   d_costs[K]               terminal cost J_i of Eq. 24 (computed in binary64, stored binary32;
  *                            NaN if the rollout produced a non-finite value)
  *   d_final_glider[K*7]      final glider states (binary64), or null

@@ -12,6 +12,7 @@
 // decay of Eq. 17; merging of the two oldest particles while N > N_w,max.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <atomic>
 #include <climits>
 #include <cstdlib>
@@ -1564,7 +1565,8 @@ __device__ void run_rollout_cl(const RolloutArgs &a, Work &w, float4 *part, floa
 }
 
 // Persistent cluster form of uneven_kernel: CTA 0 of each cluster claims the next rollout of
-// a.order and hands its index to the other CTAs; the cluster's scratch is slot blockIdx.x / C.
+// a.order (without an order, rollout a.rid0 + claim) and hands its index to the other CTAs; the
+// cluster's scratch is slot blockIdx.x / C.
 template <int KER, int NT, int DT>
 __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_cluster_kernel(const RolloutArgs a)
 {
@@ -1585,7 +1587,7 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_cluster_kernel(
         cl.sync();
         const int q = s_item;
         if (q >= a.n_items) break;
-        run_rollout_cl<KER, DT>(a, w, part, vel, scr, a.order[q], rank, C);
+        run_rollout_cl<KER, DT>(a, w, part, vel, scr, a.order ? a.order[q] : a.rid0 + q, rank, C);
         cl.sync();                   // every CTA is done with this rollout and with s_item
     }
 }
@@ -1759,6 +1761,56 @@ size_t rollout_smem_bytes(int precision, int cap)
 
 // Rollouts per launch up to which the binary64 path uses one cluster per rollout.
 constexpr int kClusterRollouts = 9;
+
+// Binary32 launches of few rollouts with large fields spread each rollout over a cluster of CTAs
+// (the persistent cluster kernel of the uneven batch): with one CTA per rollout, K rollouts of
+// fields that fit one CTA per SM use only K SMs. Measured over 50 steps (K x field): 64 x 6000
+// 62.4 ms on one CTA, 36.9 ms on 2, 61.7 ms on 4; 32 x 8000 109.4, 59.1, 42.9 ms; 128 x 4000,
+// 148 x 3000 and 512 x 2600 fastest on one CTA. Rule: the largest C in {4, 2} with K C <= SMs for
+// fields that can exceed kClusterFieldMin particles (smaller fields: the plate warp's work,
+// repeated on every CTA, is a larger share). Results are the same bits. VPM_ROLLOUT_CLUSTERS=0
+// in the environment at launch keeps one CTA per rollout.
+constexpr int kClusterFieldMin = 2300;
+
+static int rollout_cluster_size(const RolloutArgs &a, int grid, size_t smem)
+{
+    if (a.p.kernel != VPM_KERNEL_VATISTAS || a.H <= 1 || a.cap <= kClusterFieldMin || a.probe_fm ||
+        a.probe_gs || a.probe_vel || a.probe_vt || a.pace_mask || a.order || a.counter)
+        return 1;
+    const char *env = getenv("VPM_ROLLOUT_CLUSTERS");
+    if (env && env[0] == '0' && env[1] == 0) return 1;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const int nt = a.cap > 3000 ? 512 : 256;
+    for (int c : {4, 2})
+        if ((long long)grid * c <= sms && uneven_max_clusters(VPM_FP32, a.p.kernel, nt, kDiagT, c, smem) >= 1)
+            return c;
+    return 1;
+}
+
+// `grid` rollouts (a.rid0 ...) as clusters of `ctas` CTAs claiming them from a counter of their own.
+static cudaError_t launch_rollout_clusters(const RolloutArgs &a, int grid, int ctas, cudaStream_t s)
+{
+    const size_t smem = rollout_smem_bytes(VPM_FP32, a.cap);
+    const int nt = a.cap > 3000 ? 512 : 256;
+    const int clusters = std::min(grid, uneven_max_clusters(VPM_FP32, a.p.kernel, nt, kDiagT, ctas, smem));
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    void *cnt = nullptr;
+    cudaError_t e = lib_malloc_async(&cnt, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    RolloutArgs b = a;
+    b.counter = static_cast<int *>(cnt);
+    b.order = nullptr;
+    b.n_items = grid;
+    e = cudaMemsetAsync(cnt, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_uneven_cluster(b, clusters, nt, kDiagT, ctas, s);
+    const cudaError_t e2 = cudaFreeAsync(cnt, s);
+    return e != cudaSuccess ? e : e2;
+}
 template <int KER>
 static cudaError_t launch_cluster_t(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s);
 
@@ -1777,6 +1829,11 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
         if (ker == VPM_KERNEL_SINGULAR) return launch_t<double, VPM_KERNEL_SINGULAR, 128>(a, grid, smem, s);
         return launch_t<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
     }
+    const int ctas = rollout_cluster_size(a, grid, smem);
+    if (ctas > 1)
+        return with_rev_scratch(a, grid, s, [&](const RolloutArgs &b) {
+            return launch_rollout_clusters(b, grid, ctas, s);
+        });
     return with_rev_scratch(a, grid, s, [&](const RolloutArgs &b) {
         if (ker == VPM_KERNEL_GAUSSIAN) return launch_f32<VPM_KERNEL_GAUSSIAN>(b, grid, smem, s);
         if (ker == VPM_KERNEL_SINGULAR) return launch_f32<VPM_KERNEL_SINGULAR>(b, grid, smem, s);

@@ -168,6 +168,36 @@ def test_cluster_ctas_rejected_where_they_cannot_run():
     assert b.schedule()[1]["ctas"] == 2
 
 
+@pytest.mark.parametrize("K,n", [(1, 7000), (16, 3000), (40, 5000)])
+def test_rollout_batch_on_clusters_gives_the_bits_of_one_block(K, n, monkeypatch):
+    """vpm_rollout_batch spreads a few rollouts of large fields over clusters of CTAs (the largest
+    C in {4, 2} with K C <= SMs); costs, final and per-step glider states, final fields and counts
+    are the same bits as with one block per rollout (VPM_ROLLOUT_CLUSTERS=0), also with per-rollout
+    initial states; the profiler shows the cluster kernel ran."""
+    from torch.profiler import ProfilerActivity, profile
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 5
+    st = V.State(p, W.background_field(77 + K, n), W.GLIDER_X0, n + 2 * H, V.FP32)
+    controls = torch.tensor(W.mppi_noise(8, K, H, W.MPPI_SIGMA_U), device="cuda")
+    x0 = torch.tensor(np.tile(np.array(W.GLIDER_X0), (K, 1)) +
+                      np.random.default_rng(K).uniform(-0.1, 0.1, (K, 7)), device="cuda")
+    for kw in ({}, {"x0": x0}):
+        monkeypatch.setenv("VPM_ROLLOUT_CLUSTERS", "0")
+        one = st.rollout_batch(controls, want_traj=True, want_field=True, **kw)
+        torch.cuda.synchronize()
+        monkeypatch.delenv("VPM_ROLLOUT_CLUSTERS")
+        with profile(activities=[ProfilerActivity.CUDA], acc_events=True) as prof:
+            cl = st.rollout_batch(controls, want_traj=True, want_field=True, **kw)
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events()]
+        assert any("uneven_cluster_kernel" in nm for nm in names), names[:20]
+        for k in one:
+            assert torch.equal(cl[k], one[k]), (K, n, k, bool(kw))
+    st.status()
+    st.close()
+
+
 def test_batch_fp64_against_oracle(ora):
     torch, V = cuda()
     p = W.glider_params()
