@@ -62,6 +62,8 @@ def test_host_side_rejections(vlib):
     assert vlib.mppi_weights(None, 4, 1.0, None, None) == V.VPM_ERR_INVALID
     assert vlib.vpm_rollout_batch(None, 1, 1, None, None, None, None, None, None, None) == V.VPM_ERR_INVALID
     assert b"null" in vlib.vpm_last_error()
+    assert vlib.vpm_batch_set_ctas(None, 0, 0, 2) == V.VPM_ERR_INVALID
+    assert vlib.vpm_batch_set_schedule(None, 0, 0, 128, 2) == V.VPM_ERR_INVALID
     r = C.c_double(0.0)
     assert vlib.vpm_probe_rate(99, 1, C.byref(r)) == V.VPM_ERR_INVALID
     assert vlib.vpm_probe_rate(V.PROBE_PAIRS_SYM + 1, 1, C.byref(r)) == V.VPM_ERR_INVALID
