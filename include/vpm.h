@@ -225,7 +225,9 @@ vpm_status vpm_rollout_scratch_slot(int capacity, int kind, int row, int particl
  * rollout over a thread-block cluster of C CTAs, the largest C in {4, 2} with K C <= the SM count
  * (every CTA holds the field; the pair work is split between them): the same bits, faster when
  * K alone would leave SMs idle; VPM_ROLLOUT_CLUSTERS=0 in the environment keeps one block per
- * rollout. Outputs (device):
+ * rollout. A launch made while `stream` is being captured into a CUDA graph uses clusters only
+ * for a launch shape (field capacity, and the cluster size the rule picks) that an earlier launch
+ * outside capture has used, and one block per rollout otherwise. Outputs (device):
  *   d_costs[K]               terminal cost J_i of Eq. 24 (computed in binary64, stored binary32;
  *                            NaN if the rollout produced a non-finite value)
  *   d_final_glider[K*7]      final glider states (binary64), or null

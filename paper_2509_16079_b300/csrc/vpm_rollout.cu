@@ -1769,35 +1769,73 @@ constexpr int kClusterRollouts = 9;
 // 148 x 3000 and 512 x 2600 fastest on one CTA. Rule: the largest C in {4, 2} with K C <= SMs for
 // fields that can exceed kClusterFieldMin particles (smaller fields: the plate warp's work,
 // repeated on every CTA, is a larger share). Results are the same bits. VPM_ROLLOUT_CLUSTERS=0
-// in the environment at launch keeps one CTA per rollout.
+// in the environment at launch keeps one CTA per rollout, and so does a launch made during stream
+// capture for a launch shape no earlier launch has used (below).
 constexpr int kClusterFieldMin = 2300;
 
-static int rollout_cluster_size(const RolloutArgs &a, int grid, size_t smem)
+// Resident clusters and the SM count by launch shape, remembered from launches made outside stream
+// capture: a launch made while its stream is being captured must not query occupancy or raise a
+// kernel's shared-memory limit (either invalidates the capture), so it uses clusters only for a
+// shape an earlier launch has seen, and one block per rollout otherwise (the same bits).
+struct ClusterShape { int nt, ctas; size_t smem; int clusters; };
+static std::mutex g_cshape_mutex;
+static ClusterShape g_cshapes[64];
+static int g_ncshapes = 0;
+static std::atomic<int> g_sms{0};
+
+static int cached_clusters(int nt, int ctas, size_t smem, bool capturing)
 {
+    {
+        std::lock_guard<std::mutex> lock(g_cshape_mutex);
+        for (int i = 0; i < g_ncshapes; ++i)
+            if (g_cshapes[i].nt == nt && g_cshapes[i].ctas == ctas && g_cshapes[i].smem == smem)
+                return g_cshapes[i].clusters;
+    }
+    if (capturing) return 0;
+    const int c = uneven_max_clusters(VPM_FP32, VPM_KERNEL_VATISTAS, nt, kDiagT, ctas, smem);
+    std::lock_guard<std::mutex> lock(g_cshape_mutex);
+    if (g_ncshapes < 64) g_cshapes[g_ncshapes++] = ClusterShape{nt, ctas, smem, c};
+    return c;
+}
+
+static int rollout_cluster_size(const RolloutArgs &a, int grid, size_t smem, cudaStream_t s, bool &capturing)
+{
+    capturing = false;
     if (a.p.kernel != VPM_KERNEL_VATISTAS || a.H <= 1 || a.cap <= kClusterFieldMin || a.probe_fm ||
         a.probe_gs || a.probe_vel || a.probe_vt || a.pace_mask || a.order || a.counter)
         return 1;
     const char *env = getenv("VPM_ROLLOUT_CLUSTERS");
     if (env && env[0] == '0' && env[1] == 0) return 1;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
+    capturing = cs != cudaStreamCaptureStatusNone;
+    int sms = g_sms.load(std::memory_order_acquire);
+    if (!sms) {
+        int dev = 0;
+        if (capturing) return 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        g_sms.store(sms, std::memory_order_release);
+    }
     const int nt = a.cap > 3000 ? 512 : 256;
     for (int c : {4, 2})
-        if ((long long)grid * c <= sms && uneven_max_clusters(VPM_FP32, a.p.kernel, nt, kDiagT, c, smem) >= 1)
-            return c;
+        if ((long long)grid * c <= sms && cached_clusters(nt, c, smem, capturing) >= 1) return c;
     return 1;
 }
 
 // `grid` rollouts (a.rid0 ...) as clusters of `ctas` CTAs claiming them from a counter of their own.
-static cudaError_t launch_rollout_clusters(const RolloutArgs &a, int grid, int ctas, cudaStream_t s)
+static cudaError_t launch_rollout_clusters(const RolloutArgs &a, int grid, int ctas, bool capturing,
+                                          cudaStream_t s)
 {
     const size_t smem = rollout_smem_bytes(VPM_FP32, a.cap);
     const int nt = a.cap > 3000 ? 512 : 256;
-    const int clusters = std::min(grid, uneven_max_clusters(VPM_FP32, a.p.kernel, nt, kDiagT, ctas, smem));
+    const int clusters = std::min(grid, cached_clusters(nt, ctas, smem, capturing));
     if (clusters < 1) return cudaErrorInvalidConfiguration;
     void *cnt = nullptr;
     cudaError_t e = lib_malloc_async(&cnt, sizeof(int), s);
@@ -1829,10 +1867,11 @@ cudaError_t launch_rollout(int precision, const RolloutArgs &a, int grid, cudaSt
         if (ker == VPM_KERNEL_SINGULAR) return launch_t<double, VPM_KERNEL_SINGULAR, 128>(a, grid, smem, s);
         return launch_t<double, VPM_KERNEL_VATISTAS, 128>(a, grid, smem, s);
     }
-    const int ctas = rollout_cluster_size(a, grid, smem);
+    bool capturing = false;
+    const int ctas = rollout_cluster_size(a, grid, smem, s, capturing);
     if (ctas > 1)
         return with_rev_scratch(a, grid, s, [&](const RolloutArgs &b) {
-            return launch_rollout_clusters(b, grid, ctas, s);
+            return launch_rollout_clusters(b, grid, ctas, capturing, s);
         });
     return with_rev_scratch(a, grid, s, [&](const RolloutArgs &b) {
         if (ker == VPM_KERNEL_GAUSSIAN) return launch_f32<VPM_KERNEL_GAUSSIAN>(b, grid, smem, s);

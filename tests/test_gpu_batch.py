@@ -198,6 +198,44 @@ def test_rollout_batch_on_clusters_gives_the_bits_of_one_block(K, n, monkeypatch
     st.close()
 
 
+def test_rollout_batch_on_clusters_under_graph_capture():
+    """A few rollouts of a large field captured into a CUDA graph (torch.cuda.graph, global capture
+    mode) and replayed give the bits of the eager launch. A launch shape that ran eagerly before
+    the capture replays on clusters; a shape first seen during capture keeps one block per rollout
+    (the library makes no occupancy query while a capture is open)."""
+    from torch.profiler import ProfilerActivity, profile
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 4
+    for n, K, eager_first in ((3000, 4, True), (5200, 2, False)):
+        st = V.State(p, W.background_field(300 + n, n), W.GLIDER_X0, n + 2 * H, V.FP32)
+        controls = torch.tensor(W.mppi_noise(21, K, H, W.MPPI_SIGMA_U), device="cuda")
+        if eager_first:
+            eager = st.rollout_batch(controls, want_traj=True)
+            torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cap = st.rollout_batch(controls, want_traj=True)
+        with profile(activities=[ProfilerActivity.CUDA], acc_events=True) as prof:
+            g.replay()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events()]
+        on_clusters = any("uneven_cluster_kernel" in nm for nm in names)
+        assert on_clusters == eager_first, names[:20]
+        if not eager_first:
+            eager = st.rollout_batch(controls, want_traj=True)
+            torch.cuda.synchronize()
+        for k in eager:
+            assert torch.equal(cap[k], eager[k]), (n, k)
+        g.replay()
+        torch.cuda.synchronize()
+        for k in eager:
+            assert torch.equal(cap[k], eager[k]), (n, k)
+        del g
+        st.status()
+        st.close()
+
+
 def test_batch_fp64_against_oracle(ora):
     torch, V = cuda()
     p = W.glider_params()
