@@ -1035,6 +1035,45 @@ def run_uneven(args):
     print(json.dumps(uneven_result(V, torch, args.rollouts_uneven, args.steps, args.sample)), flush=True)
 
 
+def run_clusters(args):
+    """A few rollouts of large fields through vpm_rollout_batch, one block per rollout
+    (VPM_ROLLOUT_CLUSTERS=0) against the automatic choice of a 2- or 4-CTA cluster per rollout;
+    the same bits either way (checked here on the costs and final glider states)."""
+    import torch
+    import paper_2509_16079_b300 as V
+    from paper_2509_16079_b300 import build
+    build.build()
+    p = W.glider_params()
+    Hh = args.cluster_horizon
+    rows = []
+    with ClockSampler(0) as clk:
+        for case in args.cluster_cases:
+            K, n = (int(x) for x in case.split("x"))
+            st = V.State(p, W.background_field(5 + K, n), W.GLIDER_X0, n + 2 * Hh, V.FP32)
+            c = torch.tensor(W.mppi_noise(2, K, Hh, W.MPPI_SIGMA_U), device="cuda")
+            row, outs = {"K": K, "n": n}, {}
+            for mode in ("0", "1"):
+                os.environ["VPM_ROLLOUT_CLUSTERS"] = mode
+                outs[mode] = st.rollout_batch(c)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(max(1, args.steps)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    st.rollout_batch(c)
+                    e1.record()
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                row["one_block_ms" if mode == "0" else "auto_ms"] = float(np.median(ts))
+            os.environ.pop("VPM_ROLLOUT_CLUSTERS", None)
+            row["same_bits"] = all(torch.equal(outs["0"][k], outs["1"][k]) for k in outs["0"])
+            rows.append(row)
+            st.close()
+    print(json.dumps({"workload": "vpm_rollout_batch, few rollouts of large fields, H=%d, binary32, "
+                                  "Vatistas core 0.05c" % Hh, "cases": rows, "clocks": clk.summary()}),
+          flush=True)
+
+
 SERVE_H = 100
 SERVE_MAX_WAIT_MS = 4000.0   # least-work-first admission: a request queued this long goes first
 SERVE_SMALL_ROLLOUTS = 256   # and requests of up to this many rollouts take the high-priority lane
@@ -1198,7 +1237,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: K rollouts x --horizon steps, one timed iteration")
     ap.add_argument("--horizon", type=int, default=H)
-    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "replan2000", "uneven", "serving", "alu", "table1", "policy", "nmpc", "plate"])
+    ap.add_argument("--workload", default="mppi", choices=["mppi", "freefield", "replan2000", "uneven", "serving", "alu", "table1", "policy", "nmpc", "plate", "clusters"])
+    ap.add_argument("--cluster-cases", nargs="*", default=["1x8000", "8x6000", "32x8000", "64x6000", "74x4000", "128x4000"],
+                    help="K x field-size cases of the clusters workload")
+    ap.add_argument("--cluster-horizon", type=int, default=50)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0, 1.5, 2.0, 3.0],
                     help="total request rates (Hz) of the serving workload's sustainable-rate sweep")
@@ -1244,6 +1286,8 @@ def main():
         run_policy(args)
     elif args.workload == "nmpc":
         run_nmpc(args)
+    elif args.workload == "clusters":
+        run_clusters(args)
     elif args.workload == "plate":
         run_plate(args)
     else:
