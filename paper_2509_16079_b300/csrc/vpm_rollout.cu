@@ -1600,6 +1600,7 @@ __global__ void __launch_bounds__(NT, min_blocks_for(NT)) uneven_cluster_kernel(
     __shared__ Work w;
     __shared__ int s_item;
     float2 *scr = a.rev ? a.rev + (size_t)(blockIdx.x / C) * a.rev_stride : nullptr;
+    cl.sync();                       // every CTA of the cluster has started before any remote write
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) {
             const int q = atomicAdd(a.counter, 1);
