@@ -172,6 +172,28 @@ def test_tuner_spreads_few_large_rollouts_over_clusters():
     b.status()
 
 
+def test_clusters_at_the_largest_field_one_cta_holds():
+    """Fields that fill a CTA's shared memory (9200 + 2H particles: about 224 of 227 KB) on clusters of 2
+    and 4 CTAs give the bits of one CTA per rollout."""
+    torch, V = cuda()
+    p = W.glider_params()
+    H = 3
+    counts = [9200, 9290 - 2 * H]
+    fields, gliders = _roots(counts, 4)
+    controls = torch.tensor(W.mppi_noise(19, len(counts), H, W.MPPI_SIGMA_U), device="cuda")
+    b = V.Batch(p, fields, gliders, H)
+    base = {k: v.clone() for k, v in b.rollout(controls).items()}
+    assert len(b.schedule()) == 1 and b.schedule()[0]["cap"] == 9290
+    for ctas in (2, 4):
+        b.set_ctas(False, 0, ctas)
+        out = b.rollout(controls)
+        torch.cuda.synchronize()
+        assert b.schedule()[0]["ctas"] == ctas
+        for k in base:
+            assert torch.equal(out[k], base[k]), (ctas, k)
+    b.status()
+
+
 def test_cluster_ctas_rejected_where_they_cannot_run():
     torch, V = cuda()
     p = W.glider_params()
